@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the blockwise (Schur-complement) inversion on GB300.
+
+One step = one full inversion of the workload matrix through the library's
+C ABI: every pivot-block inverse, row panel and Schur update of the p
+elimination steps (Eq. (a) applied once per diagonal block, in place), plus
+the device copy of the pristine input into the work buffer. Inputs are
+seeded synthetic matrices resident in HBM before the timed region; each is
+512 MiB, larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank inverts its
+own matrix (independent problems, no collective on the data path); the step
+time is the max over ranks and `value` counts the work of all ranks.
+
+--impl reference times the CPU FP64 oracle (plain C, all host cores) on a
+bounded sample of the same workload (order 4096, same block order and
+distribution) and prints the same line with "impl": "reference".
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective TFLOP/s & inverses/s at resid≤1e-12 vs FP64 GPU path; p50/p99 latency"
+RHO_GATE = 1e-12
+
+# FP64 ALU peak from unit counts: 2 DFMA/clock/SM x 2 flop x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+
+WORKLOADS = {
+    "f64_8192": dict(n=8192, block=256, sigma=1.5, seed=2, mode="f64",
+                     desc="8192x8192 FP64, 32x32 grid of 256x256 blocks, N(0,1)/sqrt(n)+1.5I, seed 2, plain FP64 GPU path"),
+    "f64_256": dict(n=256, block=64, sigma=None, seed=1, mode="f64",
+                    desc="256x256 FP64, 4x4 grid of 64x64 blocks, U[-1,1]+256I, seed 1"),
+}
+CPU_SAMPLE_N = 4096
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel source
+# it was measured on; reported as null once that source changes.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="f64_8192")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe-peaks", action="store_true",
+                    help="measure library GEMM rates (FP64, FP32, TF32, BF16, FP16, FP8, INT8) and exit")
+    return ap.parse_args()
+
+
+def probe_peaks():
+    """Library (cuBLAS) GEMM throughput per dtype, best of N with CUDA events:
+    the denominators that the measured peak file does not carry."""
+    import torch
+    out = {}
+
+    def best(fn, flops, iters):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        b = 1e30
+        for _ in range(iters):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            b = min(b, s.elapsed_time(e) / 1e3)
+        return flops / b / 1e12
+
+    n = 8192
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for name, dt, it in [("f64", torch.float64, 3), ("f32_simt", torch.float32, 5),
+                         ("bf16", torch.bfloat16, 10), ("f16", torch.float16, 10)]:
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        out[name] = best(lambda: a @ b, 2 * n ** 3, it)
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = True
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    out["tf32"] = best(lambda: a @ b, 2 * n ** 3, 10)
+    a8 = a.to(torch.float8_e4m3fn)
+    b8 = b.to(torch.float8_e4m3fn).t()
+    one = torch.tensor(1.0, device="cuda")
+    out["fp8_e4m3"] = best(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16),
+                           2 * n ** 3, 10)
+    ai = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+    bi8 = torch.randint(-8, 8, (n, n), device="cuda", dtype=torch.int8)
+    out["int8"] = best(lambda: torch._int_mm(ai, bi8), 2 * n ** 3, 10)
+    print(json.dumps({"probe": "library GEMM TFLOP/s, 8192^3", **out}))
+
+
+def make_input(w):
+    from paper_2305_11103_gb300 import inputs
+    if w["sigma"] is None:
+        return inputs.diag_dominant_uniform(w["n"], w["seed"], shift=w["n"])
+    return inputs.gaussian_shifted(w["n"], w["seed"], sigma=w["sigma"])
+
+
+def partition(n, b):
+    sizes = [b] * (n // b)
+    if n % b:
+        sizes.append(n % b)
+    return sizes
+
+
+def config_of(w, extra=None):
+    c = {"workload": w["desc"], "n": w["n"], "block": w["block"], "mode": w["mode"],
+         "l2": "inputs larger than L2 (no flush)" if w["n"] * w["n"] * 8 > 129 * 2**20 else "fits L2"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------- clocks ------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
+        mx = max((float(r[1]) for r in rows if r[1].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# -------------------------------------------------------------- oracle -----
+def time_oracle(n, block, sigma, seed, repeats=1):
+    """Seconds per inversion of the CPU oracle (all host cores) at order n."""
+    import oracle
+    from paper_2305_11103_gb300 import inputs
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    A = inputs.gaussian_shifted(n, seed, sigma=sigma) if sigma else inputs.diag_dominant_uniform(n, seed, shift=n)
+    sizes = partition(n, block)
+    ts = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.block_inverse(A, sizes)
+        ts.append(time.perf_counter() - t0)
+    return sum(ts) / len(ts), oracle.max_threads()
+
+
+def cpu_baseline(w):
+    n = min(w["n"], CPU_SAMPLE_N)
+    sec, cores = time_oracle(n, w["block"], w["sigma"], w["seed"])
+    return {"value": 2.0 * n ** 3 / sec / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"one inversion at order {n} ({n // w['block']} blocks of {w['block']}, same distribution), "
+                      f"{sec:.2f} s, scaled as 2n^3/t"}
+
+
+# ---------------------------------------------------------- distributed ----
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2305_11103_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------- our arm -------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2305_11103_gb300 import blockinv as bi
+    from paper_2305_11103_gb300 import build as libbuild
+    if rank == 0:
+        libbuild.build()
+    barrier(world)
+    bi.lib()
+    w = WORKLOADS[args.workload]
+    n, sizes, mode = w["n"], partition(w["n"], w["block"]), w["mode"]
+    A = make_input(w)
+    dev = torch.device("cuda", local)
+    dA = torch.from_numpy(A).to(dev)
+    dX = torch.empty_like(dA)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        dX.copy_(dA)
+        st = bi.blockinv_invert(n, sizes, dX.data_ptr(), n, mode, stream)
+        if st != bi.OK:
+            raise bi.BlockinvError(st, bi.blockinv_last_error_detail()[1], "blockinv_invert")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    bi.blockinv_trace_enable(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    bi.blockinv_trace_enable(False)
+    clk = clocks.stop()
+    trace = bi.blockinv_trace_summary()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    flops = 2.0 * n ** 3
+    value = world * flops / (ms / 1e3) / 1e12
+    rho = bi.residual(dA, dX)
+
+    top = max(trace.items(), key=lambda kv: kv[1]["ms"])
+    kname, kt = top
+    achieved = kt["flops"] / (kt["ms"] / 1e3) / 1e12
+    traffic = None
+    rec = NCU_TRAFFIC.get((kname, args.workload))
+    if rec and rec["src"] == src_hash("k_update_f64.cu"):
+        traffic = rec["bytes_per_launch"]
+    total_ms = sum(v["ms"] for v in trace.values())
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kname,
+                "peak_source": "FP64 unit counts: 2 DFMA/clk/SM x 2 x 152 SMs x 2.07 GHz (not in MEASURED_PEAKS.json)",
+                "algorithmic_flops_per_launch": kt["flops"] / kt["launches"],
+                "share_of_kernel_time": kt["ms"] / total_ms if total_ms else None}
+    launches = sum(v["launches"] for v in trace.values())
+
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.from_numpy(A).pin_memory()
+        hX = torch.empty_like(hA).pin_memory()
+        tot = 0.0
+        for it in range(args.warmup + args.steps):
+            hX.copy_(hA)
+            t0 = time.perf_counter()
+            st = bi.blockinv_invert_host(n, sizes, hX.data_ptr(), n, mode, stream)
+            t1 = time.perf_counter()
+            if st != bi.OK:
+                raise bi.BlockinvError(st, -1, "blockinv_invert_host")
+            if it >= args.warmup:
+                tot += t1 - t0
+        e2e_s = max_over_ranks(tot / args.steps, world)
+        e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
+               "api": "blockinv_invert_host (pinned host buffer, copies inside the timed region)"}
+        del hA, hX
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "inverses_per_s": world * 1e3 / ms, "rho": rho, "rho_gate": RHO_GATE,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches, "kernels": trace,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------ reference arm ------
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    n = min(w["n"], CPU_SAMPLE_N)
+    for _ in range(args.warmup):
+        time_oracle(n, w["block"], w["sigma"], w["seed"])
+    tot, cores = 0.0, 1
+    for _ in range(args.steps):
+        sec, cores = time_oracle(n, w["block"], w["sigma"], w["seed"])
+        tot += sec
+    sec = tot / args.steps
+    value = 2.0 * n ** 3 / sec / 1e12
+    sample = (f"one inversion per step at order {n} ({n // w['block']} blocks of {w['block']}, same distribution), "
+              f"scaled as 2n^3/t")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.probe_peaks:
+        probe_peaks()
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,141 @@
+/*
+ * blockinv.h - C ABI of libblockinv.so, GB300 (sm_103a) blockwise matrix inversion.
+ *
+ * The library inverts a square matrix partitioned into a p x p grid of square
+ * diagonal blocks (orders m_0..m_{p-1}, sum n) by repeated Schur-complement
+ * elimination: Eq. (a) of R. Thiru Senthil, "Blockwise inversion and
+ * algorithms for inverting large partitioned matrices" (arXiv 2305.11103),
+ * applied once per diagonal block, in place, as the paper's
+ * `invertor_inplace_by_a` procedure (Sec. 4.2) generalised from 2 x 2 to
+ * p x p blocks. At elimination step k, with P the current diagonal block k:
+ *
+ *   1. P^-1                                   (pivot-block inverse, the paper's diamond op)
+ *   2. V_j = P^-1 X[k, j] for every j != k    (row panel, the paper's right-arrow op)
+ *   3. X[i, j] -= X[i, k] V_j  for i, j != k  (Schur complement S_A = D - C A^-1 B)
+ *   4. X[i, k] = -X[i, k] P^-1, X[k, j] = V_j, X[k, k] = P^-1   (in-place assembly)
+ *
+ * After the last step X holds A^-1. The method needs every pivot block (the
+ * leading diagonal block and each successive Schur complement) to be
+ * invertible (Sec. 3, the condition stated with Eq. (a)); there is no
+ * pivoting across blocks. Inside a pivot block, Gauss-Jordan elimination
+ * with partial (row) pivoting is used.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are FP64, row-major, with a leading dimension (elements) >= n.
+ *    A column-major caller gets A^-1 in column-major too, since
+ *    (A^T)^-1 = (A^-1)^T and the partition is symmetric.
+ *  - Device pointers are CUDA device memory of the current device (for
+ *    example allocated by PyTorch). The caller owns every buffer it passes;
+ *    the library never frees them. Workspace is allocated by the library in
+ *    stream order (cudaMallocAsync) and released before the call returns.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - Argument errors are reported synchronously and leave the matrix
+ *    untouched. Numerical errors (a singular or non-finite pivot block) are
+ *    reported by the blocking entry points after a stream synchronisation; the
+ *    matrix contents are then unspecified (partly eliminated).
+ *  - blockinv_last_error_detail() gives the failing block index of the last
+ *    SINGULAR / NONFINITE status returned on the calling host thread.
+ */
+#ifndef BLOCKINV_H
+#define BLOCKINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Arithmetic mode.
+ *  BLOCKINV_F64        every step in FP64 on the GPU.
+ *  BLOCKINV_MIXED_TF32 elimination on an FP32 copy with the Schur-update
+ *                      products on TF32 tensor cores (FP32 accumulation),
+ *                      then Newton-Schulz refinement X <- X + X (I - A X) with
+ *                      an FP64-accurate residual until rho <= tol.
+ *  BLOCKINV_MIXED_BF16 the same with BF16 tensor-core products. */
+typedef enum {
+  BLOCKINV_F64 = 0,
+  BLOCKINV_MIXED_TF32 = 1,
+  BLOCKINV_MIXED_BF16 = 2
+} blockinv_mode;
+
+/* Status codes. */
+enum {
+  BLOCKINV_OK = 0,
+  BLOCKINV_PENDING = 1,              /* blockinv_poll: request not finished          */
+  BLOCKINV_ERR_INVALID = -1,         /* bad argument (n, lda, partition, pointer)    */
+  BLOCKINV_ERR_SINGULAR = -2,        /* a pivot block has an exact zero pivot        */
+  BLOCKINV_ERR_NONFINITE = -3,       /* a pivot block holds NaN or Inf               */
+  BLOCKINV_ERR_NOMEM = -4,           /* device workspace allocation failed           */
+  BLOCKINV_ERR_BUDGET = -5,          /* serving: request larger than the HBM budget  */
+  BLOCKINV_ERR_NOT_CONVERGED = -6,   /* refinement did not reach the tolerance       */
+  BLOCKINV_ERR_TIMEOUT = -7,         /* a bounded device wait gave up                */
+  BLOCKINV_ERR_CUDA = -8             /* a CUDA runtime call failed                   */
+};
+
+/* Largest diagonal block order the GPU pivot-block kernel accepts. */
+#define BLOCKINV_MAX_BLOCK 512
+
+/* Invert the n x n FP64 matrix A in place (blocking).
+ *  n            order, 1 <= n.
+ *  p            number of diagonal blocks, 1 <= p <= n; 0 means "choose":
+ *               blocks of order 256 (the last one takes the remainder), or the
+ *               paper's rule of Table 2 (orders 2..4, N_k = 2^(int(log2 n)-1)
+ *               blocks) when n <= 16.
+ *  block_sizes  host array of p positive orders summing to n (Eq. (blocking),
+ *               Sec. 5.1: the only restriction is that the orders sum to n);
+ *               ignored when p == 0. Each order <= BLOCKINV_MAX_BLOCK.
+ *  A            device pointer; overwritten by A^-1.
+ *  lda          leading dimension of A in elements, >= n.
+ *  mode         a blockinv_mode.
+ *  stream       cudaStream_t or NULL.
+ * Returns BLOCKINV_OK or an error status. Synchronises `stream`. */
+int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A,
+                    int64_t lda, int mode, void* stream);
+
+/* Stream-ordered form of blockinv_invert: enqueues the work and returns
+ * without synchronising. Argument errors are returned at once. The numerical
+ * status (a BLOCKINV_* code) and the failing block index are written to
+ * status_dev[0] and status_dev[1] (device memory, two int32) when the work
+ * completes. */
+int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, double* A,
+                          int64_t lda, int mode, void* stream, int32_t* status_dev);
+
+/* Host-buffer form: A_host (host memory, pinned or pageable) is copied to the
+ * device, inverted, and copied back into A_host. Blocking. */
+int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
+                         int64_t lda, int mode, void* stream);
+
+/* rho = ||A X - I||_F / (||A||_F ||X||_F), computed on the GPU with FP64
+ * products and sums (device pointers, row-major). The normwise residual used
+ * as the acceptance gate for every result. Blocking; the result goes to
+ * *rho_out (host). */
+int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X,
+                      int64_t ldx, double* rho_out, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* blockinv_status_str(int status);
+
+/* Failing block index of the last SINGULAR / NONFINITE status returned on this
+ * host thread (-1 if none); also returns that status. */
+int blockinv_last_error_detail(int64_t* failing_block);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int blockinv_version(void);
+
+/* Kernel tracing (the library's own profiling hook; not part of the paper's
+ * method). blockinv_trace_enable(1) clears and starts recording: every kernel
+ * launch of the library is then bracketed by two CUDA events on its stream
+ * and tagged with its algorithmic flops and bytes. blockinv_trace_enable(0)
+ * stops recording. blockinv_trace_summary() waits for the recorded events,
+ * writes a JSON object {"kernel": {"launches", "ms", "flops", "bytes"}, ...}
+ * into buf (truncated to buflen - 1 characters, NUL-terminated), clears the
+ * record and returns the length needed including the NUL. */
+int blockinv_trace_enable(int on);
+int64_t blockinv_trace_summary(char* buf, int64_t buflen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLOCKINV_H */

@@ -1,0 +1,174 @@
+"""Thin ctypes binding of libblockinv.so (include/blockinv.h), same entry-point names.
+
+Argument marshalling only: every step of the inversion runs in the library's
+CUDA kernels. PyTorch tensors are accepted for convenience (device memory and
+streams); the C ABI itself sees plain pointers and sizes. The library must be
+built first (``__graft_entry__.build()``); loading fails loudly otherwise, and
+there is no CPU fallback.
+"""
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libblockinv.so")
+
+F64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+MODES = {"f64": F64, "tf32": MIXED_TF32, "bf16": MIXED_BF16}
+
+OK, PENDING = 0, 1
+ERR_INVALID, ERR_SINGULAR, ERR_NONFINITE, ERR_NOMEM = -1, -2, -3, -4
+ERR_BUDGET, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -5, -6, -7, -8
+
+_lock = threading.Lock()
+_lib = None
+
+_i64, _i32, _int, _vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); the declarations of include/blockinv.h
+SIGNATURES = {
+    "blockinv_invert": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
+    "blockinv_invert_async": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp]),
+    "blockinv_invert_host": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
+    "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "blockinv_status_str": (ctypes.c_char_p, [_int]),
+    "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "blockinv_version": (_int, []),
+    "blockinv_trace_enable": (_int, [_int]),
+    "blockinv_trace_summary": (ctypes.c_int64, [ctypes.c_char_p, ctypes.c_int64]),
+}
+
+
+class BlockinvError(RuntimeError):
+    def __init__(self, status, failing_block=-1, what=""):
+        name = lib().blockinv_status_str(status).decode() if _lib else str(status)
+        super().__init__(f"{what}: {name} (status {status}, block {failing_block})")
+        self.status = status
+        self.failing_block = failing_block
+
+
+def lib():
+    """Load libblockinv.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+        return _lib
+
+
+def _sizes(block_sizes):
+    if block_sizes is None:
+        return 0, None, None
+    arr = (ctypes.c_int32 * len(block_sizes))(*[int(v) for v in block_sizes])
+    return len(block_sizes), arr, arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _mode(mode):
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+# ------------------------------------------------------------- raw C ABI ---
+def blockinv_invert(n, block_sizes, A_ptr, lda, mode=F64, stream=None):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_invert(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream))
+
+
+def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_ptr):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_invert_async(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream),
+                                       status_dev_ptr)
+
+
+def blockinv_invert_host(n, block_sizes, A_host_ptr, lda, mode=F64, stream=None):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_invert_host(n, p, arr, A_host_ptr, lda, _mode(mode), _stream_ptr(stream))
+
+
+def blockinv_residual(n, A_ptr, lda, X_ptr, ldx, stream=None):
+    rho = ctypes.c_double(0.0)
+    st = lib().blockinv_residual(n, A_ptr, lda, X_ptr, ldx, ctypes.byref(rho), _stream_ptr(stream))
+    return st, rho.value
+
+
+def blockinv_status_str(status):
+    return lib().blockinv_status_str(status).decode()
+
+
+def blockinv_last_error_detail():
+    blk = ctypes.c_int64(-1)
+    st = lib().blockinv_last_error_detail(ctypes.byref(blk))
+    return st, blk.value
+
+
+def blockinv_version():
+    return lib().blockinv_version()
+
+
+def blockinv_trace_enable(on):
+    return lib().blockinv_trace_enable(1 if on else 0)
+
+
+def blockinv_trace_summary():
+    """Per-kernel {launches, ms, flops, bytes} recorded since tracing was enabled."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    need = lib().blockinv_trace_summary(buf, len(buf))
+    if need > len(buf):
+        raise RuntimeError("trace summary truncated")
+    return json.loads(buf.value.decode())
+
+
+# ---------------------------------------------------- tensor conveniences ---
+def _check_matrix(t):
+    import torch
+    if t.dtype != torch.float64 or t.dim() != 2 or t.shape[0] != t.shape[1] or t.stride(1) != 1:
+        raise ValueError("expected a square float64 matrix with unit column stride")
+
+
+def invert_(A, block_sizes=None, mode="f64", stream=None):
+    """Invert the square float64 CUDA tensor A in place; raises BlockinvError."""
+    _check_matrix(A)
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor (use invert_host_ for host memory)")
+    n = A.shape[0]
+    st = blockinv_invert(n, block_sizes, A.data_ptr(), A.stride(0), mode, stream)
+    if st != OK:
+        raise BlockinvError(st, blockinv_last_error_detail()[1], "blockinv_invert")
+    return A
+
+
+def invert_host_(A, block_sizes=None, mode="f64", stream=None):
+    """Invert a host float64 matrix (torch CPU tensor, pinned or not) in place via the GPU."""
+    _check_matrix(A)
+    n = A.shape[0]
+    st = blockinv_invert_host(n, block_sizes, A.data_ptr(), A.stride(0), mode, stream)
+    if st != OK:
+        raise BlockinvError(st, blockinv_last_error_detail()[1], "blockinv_invert_host")
+    return A
+
+
+def residual(A, X, stream=None):
+    """rho = ||A X - I||_F / (||A||_F ||X||_F) on the GPU (float64 CUDA tensors)."""
+    _check_matrix(A)
+    _check_matrix(X)
+    st, rho = blockinv_residual(A.shape[0], A.data_ptr(), A.stride(0), X.data_ptr(), X.stride(0), stream)
+    if st != OK:
+        raise BlockinvError(st, -1, "blockinv_residual")
+    return rho

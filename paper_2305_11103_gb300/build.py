@@ -1,0 +1,90 @@
+"""Build libblockinv.so in-tree with nvcc for sm_103a (GB300).
+
+Each CUDA translation unit is compiled in parallel, then linked into
+``paper_2305_11103_gb300/_build/libblockinv.so`` against the shared CUDA
+runtime (the same one PyTorch loads). Rebuilds only what changed.
+"""
+import concurrent.futures
+import glob
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+ROOT = os.path.dirname(HERE)
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libblockinv.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                     "--expt-relaxed-constexpr", "-I", INCLUDE]
+
+
+def nvcc():
+    exe = shutil.which("nvcc")
+    if exe:
+        return exe
+    cand = "/usr/local/cuda/bin/nvcc"
+    if os.path.exists(cand):
+        return cand
+    raise RuntimeError("nvcc not found")
+
+
+def _deps():
+    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+
+
+def _stale(target, sources):
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(s) > t for s in sources)
+
+
+def _compile(src, obj, ptxas_verbose):
+    cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    if ptxas_verbose:
+        cmd += ["-Xptxas", "-v"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(obj + ".tmp", obj)
+    return r.stderr
+
+
+def build(force=False, ptxas_verbose=False, jobs=None):
+    """Compile and link libblockinv.so; returns its path."""
+    os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    deps = _deps()
+    todo = []
+    objs = []
+    for src in sources:
+        obj = os.path.join(BUILD, "obj", os.path.basename(src)[:-3] + ".o")
+        objs.append(obj)
+        if force or ptxas_verbose or _stale(obj, [src] + deps):
+            todo.append((src, obj))
+    logs = {}
+    if todo:
+        with concurrent.futures.ThreadPoolExecutor(jobs or min(8, len(todo))) as ex:
+            futs = {ex.submit(_compile, s, o, ptxas_verbose): s for s, o in todo}
+            for f in concurrent.futures.as_completed(futs):
+                logs[futs[f]] = f.result()
+    if force or todo or _stale(LIB, objs):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + [
+            "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(LIB + ".tmp", LIB)
+    if ptxas_verbose:
+        for src, log in sorted(logs.items()):
+            print(f"== {os.path.basename(src)}\n{log}")
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+    print(build(force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv))

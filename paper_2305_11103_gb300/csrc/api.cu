@@ -1,0 +1,363 @@
+// C ABI entry points of libblockinv.so (declared in include/blockinv.h):
+// argument checks, the partition plan, stream-ordered workspace, and the
+// per-step kernel sequence of the blockwise inversion (Eq. (a) applied once
+// per diagonal block, in place).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace blockinv {
+
+namespace {
+
+thread_local int g_last_status = BLOCKINV_OK;
+thread_local int64_t g_last_block = -1;
+
+int record(int status, int64_t block) {
+  g_last_status = status;
+  g_last_block = block;
+  return status;
+}
+
+constexpr int kDefaultBlock = 256;
+
+// ------------------------------------------------------------- tracing ----
+// When enabled, every kernel launch of the library is bracketed by two CUDA
+// events on its stream and tagged with its algorithmic flops and bytes (what
+// the step must compute and move at minimum, not what the kernel happens to
+// touch). blockinv_trace_summary() waits for the events and reports, per
+// kernel, launches, total device time, flops and bytes.
+struct TraceRec {
+  const char* name;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec> g_trace;
+
+struct TraceScope {
+  TraceRec rec{nullptr, nullptr, nullptr, 0, 0};
+  cudaStream_t s;
+  TraceScope(const char* name, double flops, double bytes, cudaStream_t stream) : s(stream) {
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    if (!g_trace_on) return;
+    rec.name = name;
+    rec.flops = flops;
+    rec.bytes = bytes;
+    if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess) {
+      rec.name = nullptr;
+      return;
+    }
+    cudaEventRecord(rec.a, s);
+  }
+  ~TraceScope() {
+    if (!rec.name) return;
+    cudaEventRecord(rec.b, s);
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    g_trace.push_back(rec);
+  }
+};
+
+struct Plan {
+  int n = 0;
+  std::vector<int> sizes;
+  std::vector<int> offs;
+  int bmax = 0;
+};
+
+// Default partition when the caller passes p == 0. Small orders follow the
+// paper's rule (Table 2: N_k = 2^(int(log2 n) - 1) blocks of order 2..4, the
+// remainder handed to the last blocks); larger ones use blocks of order 256
+// with the last block taking the remainder.
+void default_partition(int n, std::vector<int>* out) {
+  out->clear();
+  if (n <= 3) {
+    out->push_back(n);
+    return;
+  }
+  if (n <= 16) {
+    int e = 0;
+    while ((2 << e) <= n) ++e;  // e = floor(log2 n)
+    const int nk = 1 << (e - 1);
+    out->assign(nk, 2);
+    int r = n - 2 * nk;
+    int pos = nk - 1;
+    while (r-- > 0) {
+      (*out)[pos] += 1;
+      pos = (pos == 0) ? nk - 1 : pos - 1;
+    }
+    return;
+  }
+  const int p = (n + kDefaultBlock - 1) / kDefaultBlock;
+  out->assign(p, kDefaultBlock);
+  out->back() = n - kDefaultBlock * (p - 1);
+}
+
+bool valid_mode(int mode) {
+  return mode == BLOCKINV_F64 || mode == BLOCKINV_MIXED_TF32 || mode == BLOCKINV_MIXED_BF16;
+}
+
+int make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* plan) {
+  if (n < 1 || n > (int64_t)1 << 20 || lda < n || p < 0 || p > n) return BLOCKINV_ERR_INVALID;
+  plan->n = (int)n;
+  if (p == 0) {
+    default_partition((int)n, &plan->sizes);
+  } else {
+    if (!block_sizes) return BLOCKINV_ERR_INVALID;
+    plan->sizes.assign(block_sizes, block_sizes + p);
+  }
+  int64_t sum = 0;
+  plan->offs.clear();
+  plan->bmax = 0;
+  for (int b : plan->sizes) {
+    if (b < 1 || b > BLOCKINV_MAX_BLOCK) return BLOCKINV_ERR_INVALID;
+    plan->offs.push_back((int)sum);
+    sum += b;
+    if (b > plan->bmax) plan->bmax = b;
+  }
+  if (sum != n) return BLOCKINV_ERR_INVALID;
+  PivotPlan pp;
+  if (!plan_pivot(plan->bmax, 8, &pp)) return BLOCKINV_ERR_INVALID;
+  return BLOCKINV_OK;
+}
+
+// Stream-ordered device allocation that is released when the scope ends
+// (the release is itself stream-ordered, so it is safe with pending work).
+struct AsyncBuf {
+  void* ptr = nullptr;
+  cudaStream_t s = nullptr;
+  cudaError_t alloc(size_t bytes, cudaStream_t stream) {
+    s = stream;
+    return cudaMallocAsync(&ptr, bytes ? bytes : 16, stream);
+  }
+  ~AsyncBuf() {
+    if (ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BLOCKINV_OK;
+  if (e == cudaErrorMemoryAllocation) return BLOCKINV_ERR_NOMEM;
+  return BLOCKINV_ERR_CUDA;
+}
+
+// Enqueue the FP64 elimination of the whole matrix on stream s.
+int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStream_t s) {
+  const int n = pl.n;
+  AsyncBuf pinv, ubuf;
+  cudaError_t e = pinv.alloc(sizeof(double) * (size_t)pl.bmax * pl.bmax, s);
+  if (e == cudaSuccess) e = ubuf.alloc(sizeof(double) * (size_t)n * pl.bmax, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  double* Pinv = static_cast<double*>(pinv.ptr);
+  double* U = static_cast<double*>(ubuf.ptr);
+  for (size_t k = 0; k < pl.sizes.size(); ++k) {
+    const int o = pl.offs[k], b = pl.sizes[k];
+    const double bd = b, nd = n, rest = (double)(n - b);
+    {
+      TraceScope t("pivot_inverse_f64", 2.0 * bd * bd * bd, 16.0 * bd * bd, s);
+      e = launch_pivot_inverse<double>(A + (int64_t)o * lda + o, lda, b, Pinv, b, status, (int)k, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t("row_panel_f64", 2.0 * bd * bd * rest, 8.0 * (2.0 * bd * nd + bd * bd + 2.0 * rest * bd), s);
+      e = launch_row_panel_f64(A, lda, n, o, b, Pinv, U, status, s);
+    }
+    if (e == cudaSuccess && n > b) {
+      TraceScope t("schur_update_f64", 2.0 * bd * rest * nd, 8.0 * (2.0 * rest * nd + rest * bd + bd * nd), s);
+      e = launch_schur_update_f64(A, lda, n, o, b, U, status, s);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return BLOCKINV_OK;
+}
+
+int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s) {
+  switch (mode) {
+    case BLOCKINV_F64:
+      return enqueue_f64(pl, A, lda, status, s);
+    default:
+      return BLOCKINV_ERR_INVALID;
+  }
+}
+
+// Wait for the stream and turn the device status word into a return code.
+int finish(const int32_t* status_dev, cudaStream_t s) {
+  int32_t host[2] = {0, -1};
+  cudaError_t e = cudaMemcpyAsync(host, status_dev, sizeof(host), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  return record(host[0], host[0] == BLOCKINV_OK ? -1 : host[1]);
+}
+
+}  // namespace
+}  // namespace blockinv
+
+using namespace blockinv;
+
+extern "C" {
+
+int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, double* A,
+                          int64_t lda, int mode, void* stream, int32_t* status_dev) {
+  Plan pl;
+  int st = make_plan(n, p, block_sizes, lda, &pl);
+  if (st != BLOCKINV_OK) return record(st, -1);
+  if (!A || !status_dev || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int32_t), s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  return record(enqueue(pl, A, lda, mode, status_dev, s), -1);
+}
+
+int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
+                    int mode, void* stream) {
+  Plan pl;
+  int st = make_plan(n, p, block_sizes, lda, &pl);
+  if (st != BLOCKINV_OK) return record(st, -1);
+  if (!A || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  AsyncBuf sbuf;
+  cudaError_t e = sbuf.alloc(2 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  int32_t* status = static_cast<int32_t*>(sbuf.ptr);
+  st = enqueue(pl, A, lda, mode, status, s);
+  if (st != BLOCKINV_OK) {
+    cudaStreamSynchronize(s);
+    return record(st, -1);
+  }
+  return finish(status, s);
+}
+
+int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
+                         int64_t lda, int mode, void* stream) {
+  Plan pl;
+  int st = make_plan(n, p, block_sizes, lda, &pl);
+  if (st != BLOCKINV_OK) return record(st, -1);
+  if (!A_host || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  AsyncBuf dbuf, sbuf;
+  const size_t row = sizeof(double) * (size_t)n;
+  cudaError_t e = dbuf.alloc(row * (size_t)n, s);
+  if (e == cudaSuccess) e = sbuf.alloc(2 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(dbuf.ptr, row, A_host, sizeof(double) * (size_t)lda, row, (size_t)n,
+                          cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  int32_t* status = static_cast<int32_t*>(sbuf.ptr);
+  st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s);
+  if (st != BLOCKINV_OK) {
+    cudaStreamSynchronize(s);
+    return record(st, -1);
+  }
+  e = cudaMemcpy2DAsync(A_host, sizeof(double) * (size_t)lda, dbuf.ptr, row, row, (size_t)n,
+                        cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  return finish(status, s);
+}
+
+int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx,
+                      double* rho_out, void* stream) {
+  if (n < 1 || n > (int64_t)1 << 20 || lda < n || ldx < n || !A || !X || !rho_out)
+    return record(BLOCKINV_ERR_INVALID, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  AsyncBuf sums;
+  cudaError_t e = sums.alloc(3 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums.ptr, 0, 3 * sizeof(double), s);
+  if (e == cudaSuccess) e = launch_residual_f64((int)n, A, lda, X, ldx, static_cast<double*>(sums.ptr), s);
+  double h[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sums.ptr, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  *rho_out = std::sqrt(h[0]) / (std::sqrt(h[1]) * std::sqrt(h[2]));
+  return record(BLOCKINV_OK, -1);
+}
+
+const char* blockinv_status_str(int status) {
+  switch (status) {
+    case BLOCKINV_OK: return "ok";
+    case BLOCKINV_PENDING: return "pending";
+    case BLOCKINV_ERR_INVALID: return "invalid argument";
+    case BLOCKINV_ERR_SINGULAR: return "singular pivot block";
+    case BLOCKINV_ERR_NONFINITE: return "non-finite pivot block";
+    case BLOCKINV_ERR_NOMEM: return "out of device memory";
+    case BLOCKINV_ERR_BUDGET: return "request exceeds the memory budget";
+    case BLOCKINV_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case BLOCKINV_ERR_TIMEOUT: return "device wait timed out";
+    case BLOCKINV_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+int blockinv_last_error_detail(int64_t* failing_block) {
+  if (failing_block) *failing_block = g_last_block;
+  return g_last_status;
+}
+
+int blockinv_version(void) { return 100; }
+
+int blockinv_trace_enable(int on) {
+  std::vector<TraceRec> old;
+  {
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    g_trace_on = (on != 0);
+    if (on) old.swap(g_trace);
+  }
+  for (auto& r : old) {
+    cudaEventSynchronize(r.b);
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  return BLOCKINV_OK;
+}
+
+int64_t blockinv_trace_summary(char* buf, int64_t buflen) {
+  std::vector<TraceRec> recs;
+  {
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    recs.swap(g_trace);
+  }
+  struct Agg {
+    int64_t launches = 0;
+    double ms = 0, flops = 0, bytes = 0;
+  };
+  std::map<std::string, Agg> agg;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    Agg& a = agg[r.name];
+    a.launches += 1;
+    a.ms += ms;
+    a.flops += r.flops;
+    a.bytes += r.bytes;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char line[256];
+    snprintf(line, sizeof(line), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+             first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms,
+             kv.second.flops, kv.second.bytes);
+    out += line;
+    first = false;
+  }
+  out += "}";
+  if (buf && buflen > 0) {
+    size_t m = std::min((size_t)buflen - 1, out.size());
+    memcpy(buf, out.data(), m);
+    buf[m] = 0;
+  }
+  return (int64_t)out.size() + 1;
+}
+
+}  // extern "C"

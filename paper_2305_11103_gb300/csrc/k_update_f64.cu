@@ -1,0 +1,275 @@
+// FP64 kernels of one elimination step (Eq. (a), block form; in-place
+// assembly as in the paper's `invertor_inplace_by_a`, Sec. 4.2):
+//
+//  K2 row panel   X[k, j] <- P^-1 X[k, j] for every block column j != k
+//                 (the paper's right-arrow op, -A^-1 B up to sign), and
+//                 X[k, k] <- P^-1. The block column k (rows outside block k)
+//                 is copied to U first, since K3 overwrites it.
+//  K3 Schur update X[i, j] <- X[i, j] - U[i] X[k, j] for i, j != k (S_A =
+//                 D - C A^-1 B for the trailing blocks, and the top-left
+//                 update A^-1 + A^-1 B S_A^-1 C A^-1 for the rows already
+//                 eliminated), fused with the column assembly
+//                 X[i, k] <- -U[i] P^-1: block column k is treated as zero
+//                 on input and row panel k holds P^-1 there.
+//
+// FP64 on GB300 issues at about 2 DFMA per clock per SM, so both kernels are
+// bound by the FP64 pipe, not by memory: K3 moves 16 bytes of X per 2b flops.
+// They are register-tiled SIMT kernels sized to keep that pipe busy.
+#include "internal.h"
+
+namespace blockinv {
+
+namespace {
+
+__device__ __forceinline__ bool failed(const int32_t* status) {
+  return *(volatile const int32_t*)status != 0;
+}
+
+// ---------------------------------------------------------------- K2 ------
+// One CTA owns a 32-column strip of row panel k (all b rows), so the strip
+// can be read completely before it is overwritten in place. Thread (g, c)
+// holds rows g, g + 8, g + 16, ... of column c.
+constexpr int kPanelCols = 32;
+constexpr int kPanelK = 8;
+
+template <int MAXB>
+__global__ void __launch_bounds__(256)
+row_panel_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                     const double* __restrict__ Pinv, double* __restrict__ U,
+                     const int32_t* status, int col_tiles) {
+  if (failed(status)) return;
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x >= col_tiles) {
+    // Copy block column k, rows outside block k, into U (n x b, ld b).
+    const int64_t total = (int64_t)n * b;
+    const int64_t stride = (int64_t)(gridDim.x - col_tiles) * blockDim.x;
+    for (int64_t e = (int64_t)(blockIdx.x - col_tiles) * blockDim.x + tid; e < total; e += stride) {
+      const int i = (int)(e / b);
+      const int l = (int)(e - (int64_t)i * b);
+      if (i >= o && i < o + b) continue;
+      U[e] = X[(int64_t)i * ldx + o + l];
+    }
+    return;
+  }
+  constexpr int RPT = MAXB / 8;  // rows per thread
+  __shared__ double Ps[kPanelK][MAXB];
+  __shared__ double Xs[kPanelK][kPanelCols];
+  const int c = tid & 31;
+  const int g = tid >> 5;
+  const int j0 = blockIdx.x * kPanelCols;
+  const int j = j0 + c;
+  double acc[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) acc[q] = 0.0;
+
+  for (int kc = 0; kc < b; kc += kPanelK) {
+    for (int e = tid; e < b * kPanelK; e += 256) {
+      const int r = e / kPanelK;
+      const int kk = e - r * kPanelK;
+      Ps[kk][r] = (kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.0;
+    }
+    {
+      const int kk = tid >> 5;  // 8 rows x 32 columns
+      const int jj = j0 + (tid & 31);
+      Xs[kk][tid & 31] = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kPanelK; ++kk) {
+      const double x = Xs[kk][c];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
+    }
+    __syncthreads();
+  }
+  if (j >= n) return;
+  const bool pivot_col = (j >= o && j < o + b);
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = g + 8 * q;
+    if (r < b) X[(int64_t)(o + r) * ldx + j] = pivot_col ? Pinv[(int64_t)r * b + (j - o)] : acc[q];
+  }
+}
+
+// ---------------------------------------------------------------- K3 ------
+constexpr int kTile = 64;
+constexpr int kTileK = 8;
+
+__global__ void __launch_bounds__(256)
+schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                        const double* __restrict__ U, const int32_t* status) {
+  const int i0 = blockIdx.y * kTile;
+  const int j0 = blockIdx.x * kTile;
+  if (i0 >= o && i0 + kTile <= o + b) return;  // tile lies inside the pivot rows
+  if (failed(status)) return;
+  __shared__ __align__(16) double Us[kTileK][kTile];
+  __shared__ __align__(16) double Vs[kTileK][kTile];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;
+  const int ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) acc[a][d] = 0.0;
+
+  for (int kc = 0; kc < b; kc += kTileK) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * 256;
+      // U tile: 64 rows x 8 k
+      const int ui = e >> 3, uk = e & 7;
+      const int gi = i0 + ui;
+      Us[uk][ui] = (gi < n && kc + uk < b) ? U[(int64_t)gi * b + kc + uk] : 0.0;
+      // V tile: 8 k x 64 columns of row panel k
+      const int vk = e >> 6, vj = e & 63;
+      const int gj = j0 + vj;
+      Vs[vk][vj] = (gj < n && kc + vk < b) ? X[(int64_t)(o + kc + vk) * ldx + gj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTileK; ++kk) {
+      double u[4], v[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) u[a] = Us[kk][ty * 4 + a];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) v[d] = Vs[kk][tx * 4 + d];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[a][d] = fma(u[a], v[d], acc[a][d]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+    if (i >= n || (i >= o && i < o + b)) continue;
+    double* row = X + (int64_t)i * ldx;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int j = j0 + tx * 4 + d;
+      if (j >= n) continue;
+      const double base = (j >= o && j < o + b) ? 0.0 : row[j];
+      row[j] = base - acc[a][d];
+    }
+  }
+}
+
+// --------------------------------------------------------- residual -------
+// Partial sums of ||A X - I||_F^2 (sums3[0]), ||A||_F^2 (sums3[1]) and
+// ||X||_F^2 (sums3[2]). The product tile is formed in FP64 and reduced in
+// the epilogue, so no n x n temporary is needed.
+__global__ void __launch_bounds__(256)
+residual_f64_kernel(int n, const double* __restrict__ A, int64_t lda,
+                    const double* __restrict__ X, int64_t ldx, double* sums3) {
+  const int i0 = blockIdx.y * kTile;
+  const int j0 = blockIdx.x * kTile;
+  __shared__ __align__(16) double As[kTileK][kTile];
+  __shared__ __align__(16) double Xs[kTileK][kTile];
+  __shared__ double red[3][8];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;
+  const int ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) acc[a][d] = 0.0;
+  for (int kc = 0; kc < n; kc += kTileK) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * 256;
+      const int ai = e >> 3, ak = e & 7;
+      As[ak][ai] = (i0 + ai < n && kc + ak < n) ? A[(int64_t)(i0 + ai) * lda + kc + ak] : 0.0;
+      const int xk = e >> 6, xj = e & 63;
+      Xs[xk][xj] = (kc + xk < n && j0 + xj < n) ? X[(int64_t)(kc + xk) * ldx + j0 + xj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTileK; ++kk) {
+      double u[4], v[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) u[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) v[d] = Xs[kk][tx * 4 + d];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[a][d] = fma(u[a], v[d], acc[a][d]);
+    }
+    __syncthreads();
+  }
+  double r2 = 0.0, a2 = 0.0, x2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty * 4 + a;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const int j = j0 + tx * 4 + d;
+      if (i < n && j < n) {
+        const double e = acc[a][d] - (i == j ? 1.0 : 0.0);
+        r2 = fma(e, e, r2);
+        const double av = A[(int64_t)i * lda + j];
+        const double xv = X[(int64_t)i * ldx + j];
+        a2 = fma(av, av, a2);
+        x2 = fma(xv, xv, x2);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, off);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = r2;
+    red[1][tid >> 5] = a2;
+    red[2][tid >> 5] = x2;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[tid][w];
+    atomicAdd(&sums3[tid], s);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_row_panel_f64(double* X, int64_t ldx, int n, int o, int b,
+                                 const double* Pinv, double* U, const int32_t* status,
+                                 cudaStream_t s) {
+  const int col_tiles = (n + kPanelCols - 1) / kPanelCols;
+  const int copy_ctas = (n > b) ? 64 : 0;
+  dim3 grid(col_tiles + copy_ctas);
+  if (b <= 64)
+    row_panel_f64_kernel<64><<<grid, 256, 0, s>>>(X, ldx, n, o, b, Pinv, U, status, col_tiles);
+  else if (b <= 128)
+    row_panel_f64_kernel<128><<<grid, 256, 0, s>>>(X, ldx, n, o, b, Pinv, U, status, col_tiles);
+  else if (b <= 256)
+    row_panel_f64_kernel<256><<<grid, 256, 0, s>>>(X, ldx, n, o, b, Pinv, U, status, col_tiles);
+  else if (b <= 512)
+    row_panel_f64_kernel<512><<<grid, 256, 0, s>>>(X, ldx, n, o, b, Pinv, U, status, col_tiles);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schur_update_f64(double* X, int64_t ldx, int n, int o, int b,
+                                    const double* U, const int32_t* status, cudaStream_t s) {
+  if (n == b) return cudaSuccess;
+  const int t = (n + kTile - 1) / kTile;
+  schur_update_f64_kernel<<<dim3(t, t), 256, 0, s>>>(X, ldx, n, o, b, U, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_f64(int n, const double* A, int64_t lda, const double* X,
+                                int64_t ldx, double* sums3, cudaStream_t s) {
+  const int t = (n + kTile - 1) / kTile;
+  residual_f64_kernel<<<dim3(t, t), 256, 0, s>>>(n, A, lda, X, ldx, sums3);
+  return cudaGetLastError();
+}
+
+}  // namespace blockinv

@@ -1,0 +1,73 @@
+"""The C ABI: libblockinv.so builds, loads, and exports every symbol that
+include/blockinv.h declares. No GPU work is done here: the calls below fail
+argument validation on the host before any CUDA call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2305_11103_gb300 import blockinv
+from paper_2305_11103_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(blockinv_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return blockinv.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert "blockinv_invert" in names and "blockinv_residual" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", libbuild.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (blockinv_\w+)", out))
+    missing = names - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    for n in names:
+        getattr(lib, n)
+
+
+def test_binding_matches_header():
+    assert set(blockinv.SIGNATURES) <= declared_symbols()
+
+
+def test_status_strings_and_version(lib):
+    assert blockinv.blockinv_version() >= 100
+    assert blockinv.blockinv_status_str(0) == "ok"
+    assert "singular" in blockinv.blockinv_status_str(-2)
+
+
+@pytest.mark.parametrize("n,sizes,lda", [
+    (0, None, 0),            # empty order
+    (4, [2, 1], 4),          # sizes do not sum to n
+    (4, [4, 0], 4),          # zero block
+    (4, [4], 3),             # lda < n
+    (600, [600], 600),       # block above the pivot-kernel limit
+    (-3, None, 4),
+])
+def test_argument_errors_are_synchronous(lib, n, sizes, lda):
+    st = blockinv.blockinv_invert(n, sizes, 0x1000, lda, 0, None)
+    assert st == blockinv.ERR_INVALID
+    assert blockinv.blockinv_last_error_detail() == (blockinv.ERR_INVALID, -1)
+
+
+def test_null_pointer_rejected(lib):
+    assert blockinv.blockinv_invert(8, None, None, 8, 0, None) == blockinv.ERR_INVALID
+
+
+def test_unknown_mode_rejected_before_gpu_work(lib):
+    assert blockinv.blockinv_invert(8, [8], 0x1000, 8, 7, None) == blockinv.ERR_INVALID
