@@ -39,6 +39,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 WORKLOADS = {
     "f64_8192": dict(n=8192, block=256, sigma=1.5, seed=2, mode="f64",
                      desc="8192x8192 FP64, 32x32 grid of 256x256 blocks, N(0,1)/sqrt(n)+1.5I, seed 2, plain FP64 GPU path"),
+    "f64_6144": dict(n=6144, block=256, sigma=1.5, seed=2, mode="f64",
+                     desc="6144x6144 FP64, 24x24 grid of 256x256 blocks, N(0,1)/sqrt(n)+1.5I, seed 2 (profiling case)"),
     "f64_256": dict(n=256, block=64, sigma=None, seed=1, mode="f64",
                     desc="256x256 FP64, 4x4 grid of 64x64 blocks, U[-1,1]+256I, seed 1"),
 }
@@ -47,7 +49,13 @@ CPU_SAMPLE_N = 4096
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel source
 # it was measured on; reported as null once that source changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 6144 capture: 537.1 MB per launch (303.1 read + 234.0 write) for 5888 x 6144
+    # updated elements; scaled by units to 7936 x 8192 elements per launch at 8192.
+    ("schur_update_f64", "f64_8192"): {"bytes_per_launch": 537.1e6 * (7936 * 8192) / (5888 * 6144),
+                                       "src": "45a7462097825344"},
+    ("schur_update_f64", "f64_6144"): {"bytes_per_launch": 537.1e6, "src": "45a7462097825344"},
+}
 
 
 def parse():
