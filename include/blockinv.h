@@ -106,6 +106,39 @@ int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, doub
 int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
                          int64_t lda, int mode, void* stream);
 
+/* Options and per-call report for blockinv_invert_ex. */
+typedef struct {
+  double tol;          /* refinement target for rho (mixed modes); <= 0 means 1e-12     */
+  int32_t max_refine;  /* Newton-Schulz iteration cap (mixed modes); < 0 means 5;      */
+                       /* 0 returns the low-precision elimination unrefined           */
+  int32_t fallback;    /* mixed modes: 1 = rerun in FP64 if refinement fails (default) */
+  int32_t reserved[4];
+} blockinv_options;
+
+typedef struct {
+  int32_t status;         /* the returned status                                       */
+  int32_t refine_iters;   /* Newton-Schulz updates applied                             */
+  int64_t failing_block;  /* block index for SINGULAR / NONFINITE, else -1             */
+  double rho;             /* final rho measured on the GPU (mixed modes), else -1      */
+  double rho_initial;     /* rho of the unrefined low-precision inverse, else -1       */
+  int32_t used_fallback;  /* 1 if the FP64 path produced the result after a failed     */
+                          /* refinement                                                */
+  int32_t reserved[7];
+} blockinv_info;
+
+/* blockinv_invert with options and a report (either pointer may be NULL). */
+int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
+                       int mode, void* stream, const blockinv_options* opt, blockinv_info* info);
+
+/* Diagnostic: C[M x N] (FP32, row-major, ldc) = A[M x K] B[N x K]^T on the
+ * tcgen05 tensor-core GEMM used by the mixed path, with A and B row-major
+ * (K contiguous, leading dimensions lda / ldb in elements, rows 16-byte
+ * aligned). kind 0: BF16 operands; 1: FP32 storage read as TF32; 2: FP8 E4M3.
+ * Device pointers; blocking. Not part of the paper's method: it exists to
+ * check the tensor-core path in isolation. */
+int blockinv_diag_gemm(int kind, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, float* C, int64_t ldc, void* stream);
+
 /* rho = ||A X - I||_F / (||A||_F ||X||_F), computed on the GPU with FP64
  * products and sums (device pointers, row-major). The normwise residual used
  * as the acceptance gate for every result. Blocking; the result goes to

@@ -35,9 +35,25 @@ SIGNATURES = {
     "blockinv_status_str": (ctypes.c_char_p, [_int]),
     "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_version": (_int, []),
+    "blockinv_invert_ex": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp, _vp]),
+    "blockinv_diag_gemm": (_int, [_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "blockinv_trace_enable": (_int, [_int]),
     "blockinv_trace_summary": (ctypes.c_int64, [ctypes.c_char_p, ctypes.c_int64]),
 }
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("fallback", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("refine_iters", ctypes.c_int32), ("failing_block", ctypes.c_int64),
+                ("rho", ctypes.c_double), ("rho_initial", ctypes.c_double), ("used_fallback", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class BlockinvError(RuntimeError):
@@ -94,6 +110,20 @@ def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_p
     p, arr, _ = _sizes(block_sizes)
     return lib().blockinv_invert_async(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream),
                                        status_dev_ptr)
+
+
+def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1):
+    """Returns (status, Info)."""
+    p, arr, _ = _sizes(block_sizes)
+    opt = Options(tol=tol, max_refine=max_refine, fallback=fallback)
+    info = Info()
+    st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
+                                  ctypes.byref(info))
+    return st, info
+
+
+def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None):
+    return lib().blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, _stream_ptr(stream))
 
 
 def blockinv_invert_host(n, block_sizes, A_host_ptr, lda, mode=F64, stream=None):

@@ -43,35 +43,6 @@ std::mutex g_trace_mu;
 bool g_trace_on = false;
 std::vector<TraceRec> g_trace;
 
-struct TraceScope {
-  TraceRec rec{nullptr, nullptr, nullptr, 0, 0};
-  cudaStream_t s;
-  TraceScope(const char* name, double flops, double bytes, cudaStream_t stream) : s(stream) {
-    std::lock_guard<std::mutex> g(g_trace_mu);
-    if (!g_trace_on) return;
-    rec.name = name;
-    rec.flops = flops;
-    rec.bytes = bytes;
-    if (cudaEventCreate(&rec.a) != cudaSuccess || cudaEventCreate(&rec.b) != cudaSuccess) {
-      rec.name = nullptr;
-      return;
-    }
-    cudaEventRecord(rec.a, s);
-  }
-  ~TraceScope() {
-    if (!rec.name) return;
-    cudaEventRecord(rec.b, s);
-    std::lock_guard<std::mutex> g(g_trace_mu);
-    g_trace.push_back(rec);
-  }
-};
-
-struct Plan {
-  int n = 0;
-  std::vector<int> sizes;
-  std::vector<int> offs;
-  int bmax = 0;
-};
 
 // Default partition when the caller passes p == 0. Small orders follow the
 // paper's rule (Table 2: N_k = 2^(int(log2 n) - 1) blocks of order 2..4, the
@@ -178,10 +149,59 @@ int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStr
   return BLOCKINV_OK;
 }
 
-int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s) {
+struct Options {
+  double tol = 1e-12;
+  int max_refine = 5;
+  bool fallback = true;
+};
+
+Options resolve(const blockinv_options* o) {
+  Options r;
+  if (o) {
+    if (o->tol > 0) r.tol = o->tol;
+    if (o->max_refine >= 0) r.max_refine = o->max_refine;
+    r.fallback = o->fallback != 0;
+  }
+  return r;
+}
+
+// Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
+// of the low-precision inverse).
+int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* status, cudaStream_t s) {
+  const int n = pl.n;
+  const int64_t ld32 = (n + 31) / 32 * 32;
+  const int kpad = mixed_kpad(pl.bmax);
+  const size_t eb = bf16 ? 2 : 4;
+  AsyncBuf x32, pinv, u, vt;
+  cudaError_t e = x32.alloc(sizeof(float) * (size_t)n * ld32, s);
+  if (e == cudaSuccess) e = pinv.alloc(sizeof(float) * (size_t)pl.bmax * pl.bmax, s);
+  if (e == cudaSuccess) e = u.alloc(eb * (size_t)n * kpad, s);
+  if (e == cudaSuccess) e = vt.alloc(eb * (size_t)n * kpad, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  float* X32 = static_cast<float*>(x32.ptr);
+  {
+    TraceScope t("cast_f64_to_f32", 0, 12.0 * n * (double)n, s);
+    e = launch_cast_f64_to_f32(A, lda, X32, ld32, n, s);
+  }
+  if (e == cudaSuccess)
+    e = mixed_elimination(pl, bf16, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, status, s);
+  if (e == cudaSuccess) {
+    TraceScope t("cast_f32_to_f64", 0, 12.0 * n * (double)n, s);
+    e = launch_cast_f32_to_f64(X32, ld32, A, lda, n, s);
+  }
+  return cuda_status(e);
+}
+
+int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s,
+            const Options& opt) {
   switch (mode) {
     case BLOCKINV_F64:
       return enqueue_f64(pl, A, lda, status, s);
+    case BLOCKINV_MIXED_TF32:
+    case BLOCKINV_MIXED_BF16:
+      if (opt.max_refine == 0)
+        return enqueue_mixed_elim(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s);
+      return BLOCKINV_ERR_NOT_CONVERGED;  // refinement is enqueued by invert_ex
     default:
       return BLOCKINV_ERR_INVALID;
   }
@@ -197,6 +217,28 @@ int finish(const int32_t* status_dev, cudaStream_t s) {
 }
 
 }  // namespace
+
+TraceScope::TraceScope(const char* name, double flops, double bytes, cudaStream_t s) : s_(s) {
+  std::lock_guard<std::mutex> g(g_trace_mu);
+  if (!g_trace_on) return;
+  if (cudaEventCreate(&a_) != cudaSuccess) return;
+  if (cudaEventCreate(&b_) != cudaSuccess) {
+    cudaEventDestroy(a_);
+    return;
+  }
+  name_ = name;
+  flops_ = flops;
+  bytes_ = bytes;
+  cudaEventRecord(a_, s_);
+}
+
+TraceScope::~TraceScope() {
+  if (!name_) return;
+  cudaEventRecord(b_, s_);
+  std::lock_guard<std::mutex> g(g_trace_mu);
+  g_trace.push_back(TraceRec{name_, a_, b_, flops_, bytes_});
+}
+
 }  // namespace blockinv
 
 using namespace blockinv;
@@ -212,27 +254,48 @@ int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
-  return record(enqueue(pl, A, lda, mode, status_dev, s), -1);
+  return record(enqueue(pl, A, lda, mode, status_dev, s, Options()), -1);
 }
 
-int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
-                    int mode, void* stream) {
+int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int mode,
+                       void* stream, const blockinv_options* options, blockinv_info* info) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->failing_block = -1;
+    info->rho = -1;
+    info->rho_initial = -1;
+  }
   Plan pl;
   int st = make_plan(n, p, block_sizes, lda, &pl);
-  if (st != BLOCKINV_OK) return record(st, -1);
-  if (!A || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  if (st == BLOCKINV_OK && (!A || !valid_mode(mode))) st = BLOCKINV_ERR_INVALID;
+  if (st != BLOCKINV_OK) {
+    if (info) info->status = st;
+    return record(st, -1);
+  }
+  const Options opt = resolve(options);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   AsyncBuf sbuf;
   cudaError_t e = sbuf.alloc(2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
-  st = enqueue(pl, A, lda, mode, status, s);
+  st = enqueue(pl, A, lda, mode, status, s, opt);
   if (st != BLOCKINV_OK) {
     cudaStreamSynchronize(s);
+    if (info) info->status = st;
     return record(st, -1);
   }
-  return finish(status, s);
+  st = finish(status, s);
+  if (info) {
+    info->status = st;
+    info->failing_block = g_last_block;
+  }
+  return st;
+}
+
+int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int mode,
+                    void* stream) {
+  return blockinv_invert_ex(n, p, block_sizes, A, lda, mode, stream, nullptr, nullptr);
 }
 
 int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
@@ -252,7 +315,7 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
                           cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
-  st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s);
+  st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s, Options());
   if (st != BLOCKINV_OK) {
     cudaStreamSynchronize(s);
     return record(st, -1);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/blockinv.h"
 
 namespace blockinv {
@@ -15,6 +17,30 @@ namespace blockinv {
 struct DevStatus {
   int32_t code;
   int32_t block;
+};
+
+// Validated partition of an order-n matrix into diagonal blocks.
+struct Plan {
+  int n = 0;
+  std::vector<int> sizes;
+  std::vector<int> offs;
+  int bmax = 0;
+};
+
+// RAII kernel tracer: when tracing is on, brackets the enclosed launch with two
+// CUDA events on stream s and records its algorithmic flops and bytes.
+class TraceScope {
+ public:
+  TraceScope(const char* name, double flops, double bytes, cudaStream_t s);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  const char* name_ = nullptr;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  double flops_ = 0, bytes_ = 0;
+  cudaStream_t s_ = nullptr;
 };
 
 // Host-side choice of the pivot-kernel cluster shape for a block of order b.
@@ -48,5 +74,15 @@ cudaError_t launch_schur_update_f64(double* X, int64_t ldx, int n, int o, int b,
 // Residual pieces (FP64): partial sums of ||A X - I||_F^2, ||A||_F^2, ||X||_F^2.
 cudaError_t launch_residual_f64(int n, const double* A, int64_t lda, const double* X,
                                 int64_t ldx, double* sums3, cudaStream_t s);
+
+// Mixed-precision elimination (k_mixed.cu).
+cudaError_t launch_cast_f64_to_f32(const double* A, int64_t lda, float* X, int64_t ldx, int n, cudaStream_t s);
+cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64_t lda, int n, cudaStream_t s);
+int mixed_kpad(int bmax);
+// Runs every elimination step on X32 (n x n, leading dimension ld32). Pinv is
+// bmax^2 floats; U and Vt are n x mixed_kpad(bmax) operands of 4 (TF32) or
+// 2 (BF16) bytes per element.
+cudaError_t mixed_elimination(const Plan& pl, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
+                              void* Vt, int32_t* status, cudaStream_t s);
 
 }  // namespace blockinv

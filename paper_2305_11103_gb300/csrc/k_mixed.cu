@@ -1,0 +1,263 @@
+// Mixed-precision elimination: the same in-place block Gauss-Jordan steps as
+// the FP64 path (Eq. (a) once per diagonal block), on an FP32 copy of the
+// matrix, with the Schur update (the dominant 2 b (n - b) n flops per step)
+// on the tensor cores:
+//
+//   X32[i, j] <- (j in pivot cols ? 0 : X32[i, j]) - sum_l U[i, l] Vt[j, l]
+//
+// U (block column k) and Vt (row panel k = P^-1 X[k, :], transposed) are
+// packed K-major, rounded to TF32 or BF16, by the FP32 row-panel kernel,
+// and multiplied by tcgen05.mma with an FP32 accumulator in TMEM. The pivot
+// blocks are inverted in FP32 by the cluster Gauss-Jordan kernel. Accuracy is
+// recovered afterwards by Newton-Schulz refinement against the FP64 input.
+#include <cuda_bf16.h>
+
+#include "tc_gemm.cuh"
+
+namespace blockinv {
+
+namespace {
+
+__device__ __forceinline__ bool failed(const int32_t* status) {
+  return *(volatile const int32_t*)status != 0;
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+template <bool kBF16>
+struct OpType;
+template <>
+struct OpType<false> {
+  using T = float;
+  static __device__ __forceinline__ T cvt(float x) { return round_tf32(x); }
+};
+template <>
+struct OpType<true> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ T cvt(float x) { return __float2bfloat16_rn(x); }
+};
+
+// ------------------------------------------------------------- casts ------
+__global__ void cast_f64_to_f32_kernel(const double* __restrict__ A, int64_t lda, float* __restrict__ X,
+                                       int64_t ldx, int n) {
+  const int64_t total = (int64_t)n * ldx;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ldx;
+    const int64_t j = e - i * ldx;
+    X[e] = (j < n) ? (float)A[i * lda + j] : 0.f;
+  }
+}
+
+__global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx, double* __restrict__ A,
+                                       int64_t lda, int n) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n;
+    const int64_t j = e - i * n;
+    A[i * lda + j] = (double)X[i * ldx + j];
+  }
+}
+
+// --------------------------------------------------------- row panel ------
+// One CTA per 32-column strip of row panel k: V = P^-1 X32[k, strip] in FP32,
+// written back to X32 (P^-1 itself in the pivot columns) and, transposed and
+// rounded, to Vt[j][0..kpad) (zero beyond b). Extra CTAs pack
+// U[i][l] = X32[i][o + l] for rows outside block k (zero elsewhere).
+constexpr int kCols = 32;
+constexpr int kKc = 8;
+
+template <int MAXB, bool kBF16>
+__global__ void __launch_bounds__(256)
+row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, const float* __restrict__ Pinv,
+                       typename OpType<kBF16>::T* __restrict__ U, typename OpType<kBF16>::T* __restrict__ Vt,
+                       int kpad, const int32_t* status, int col_tiles) {
+  using Op = OpType<kBF16>;
+  if (failed(status)) return;
+  const int tid = threadIdx.x;
+  if ((int)blockIdx.x >= col_tiles) {
+    const int64_t total = (int64_t)n * kpad;
+    const int64_t stride = (int64_t)(gridDim.x - col_tiles) * blockDim.x;
+    for (int64_t e = (int64_t)(blockIdx.x - col_tiles) * blockDim.x + tid; e < total; e += stride) {
+      const int i = (int)(e / kpad);
+      const int l = (int)(e - (int64_t)i * kpad);
+      const bool keep = l < b && !(i >= o && i < o + b);
+      U[e] = Op::cvt(keep ? X[(int64_t)i * ldx + o + l] : 0.f);
+    }
+    return;
+  }
+  extern __shared__ float sm[];
+  float* Ps = sm;                       // [kKc][MAXB]
+  float* Xs = Ps + kKc * MAXB;          // [kKc][kCols]
+  float* Vs = Xs + kKc * kCols;         // [kCols][MAXB + 1]
+  constexpr int RPT = MAXB / 8;
+  const int c = tid & 31;
+  const int g = tid >> 5;
+  const int j0 = blockIdx.x * kCols;
+  const int j = j0 + c;
+  float acc[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) acc[q] = 0.f;
+  for (int kc = 0; kc < b; kc += kKc) {
+    for (int e = tid; e < b * kKc; e += 256) {
+      const int r = e / kKc;
+      const int kk = e - r * kKc;
+      Ps[kk * MAXB + r] = (kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
+    }
+    {
+      const int kk = tid >> 5;
+      const int jj = j0 + (tid & 31);
+      Xs[kk * kCols + (tid & 31)] = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kKc; ++kk) {
+      const float x = Xs[kk * kCols + c];
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) acc[q] = fmaf(Ps[kk * MAXB + g + 8 * q], x, acc[q]);
+    }
+    __syncthreads();
+  }
+  const bool pivot_col = (j >= o && j < o + b);
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = g + 8 * q;
+    if (r < b) {
+      const float v = (j < n) ? (pivot_col ? Pinv[(int64_t)r * b + (j - o)] : acc[q]) : 0.f;
+      if (j < n) X[(int64_t)(o + r) * ldx + j] = v;
+      Vs[c * (MAXB + 1) + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int cc = 0; cc < kCols; ++cc) {
+    const int jj = j0 + cc;
+    if (jj >= n) break;
+    for (int r = tid; r < kpad; r += 256)
+      Vt[(int64_t)jj * kpad + r] = Op::cvt(r < b ? Vs[cc * (MAXB + 1) + r] : 0.f);
+  }
+}
+
+// ---------------------------------------------------- Schur epilogue ------
+struct EpiSchurF32 {
+  float* X;
+  int64_t ldx;
+  int n, o, b;
+  const int32_t* status;
+  __device__ bool skip() const { return failed(status); }
+  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
+    if (row >= n || (row >= o && row < o + b)) return;
+    float* p = X + (int64_t)row * ldx + col0;
+    if (col0 + 32 <= n && (col0 + 32 <= o || col0 >= o + b)) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float4 c = reinterpret_cast<float4*>(p)[q];
+        c.x -= __uint_as_float(v[4 * q + 0]);
+        c.y -= __uint_as_float(v[4 * q + 1]);
+        c.z -= __uint_as_float(v[4 * q + 2]);
+        c.w -= __uint_as_float(v[4 * q + 3]);
+        reinterpret_cast<float4*>(p)[q] = c;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int jj = col0 + q;
+        if (jj < n) {
+          const float base = (jj >= o && jj < o + b) ? 0.f : p[q];
+          p[q] = base - __uint_as_float(v[q]);
+        }
+      }
+    }
+  }
+};
+
+template <int MAXB, bool kBF16>
+cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
+                         int kpad, const int32_t* status, cudaStream_t s) {
+  using T = typename OpType<kBF16>::T;
+  const int col_tiles = (n + kCols - 1) / kCols;
+  const int grid = col_tiles + 64;
+  const size_t smem = sizeof(float) * ((size_t)kKc * MAXB + kKc * kCols + (size_t)kCols * (MAXB + 1));
+  auto k = row_panel_mixed_kernel<MAXB, kBF16>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 256, smem, s>>>(X, ldx, n, o, b, Pinv, static_cast<T*>(U), static_cast<T*>(Vt), kpad, status,
+                            col_tiles);
+  return cudaGetLastError();
+}
+
+template <bool kBF16>
+cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
+                             int kpad, const int32_t* status, cudaStream_t s) {
+  if (b <= 64) return launch_panel<64, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
+  if (b <= 128) return launch_panel<128, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
+  if (b <= 256) return launch_panel<256, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
+  if (b <= 512) return launch_panel<512, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
+  return cudaErrorInvalidValue;
+}
+
+template <tc::Kind K>
+cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float* X, int64_t ldx, int n, int o,
+                            int b, int32_t* status, cudaStream_t s) {
+  constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
+  const int kb = (b + BK - 1) / BK;
+  tc::KMap km{kb, kb, 0, 0};
+  EpiSchurF32 epi{X, ldx, n, o, b, status};
+  return tc::launch_gemm<K>(tU, tV, n, n, km, epi, status, s);
+}
+
+}  // namespace
+
+cudaError_t launch_cast_f64_to_f32(const double* A, int64_t lda, float* X, int64_t ldx, int n, cudaStream_t s) {
+  cast_f64_to_f32_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(A, lda, X, ldx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64_t lda, int n, cudaStream_t s) {
+  cast_f32_to_f64_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(X, ldx, A, lda, n);
+  return cudaGetLastError();
+}
+
+int mixed_kpad(int bmax) { return (bmax + 63) / 64 * 64; }
+
+cudaError_t mixed_elimination(const Plan& mp, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
+                              void* Vt, int32_t* status, cudaStream_t s) {
+  const int n = mp.n;
+  const int kpad = mixed_kpad(mp.bmax);
+  const int eb = bf16 ? 2 : 4;
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const uint32_t BK = 128 / eb;
+  CUtensorMap tU, tV;
+  if (!make_tmap_2d(&tU, U, dt, kpad, n, (uint64_t)kpad * eb, BK, tc::kBM) ||
+      !make_tmap_2d(&tV, Vt, dt, kpad, n, (uint64_t)kpad * eb, BK, tc::kBN))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < mp.sizes.size() && e == cudaSuccess; ++k) {
+    const int o = mp.offs[k], b = mp.sizes[k];
+    const double bd = b, nd = n, rest = n - b;
+    {
+      TraceScope t("pivot_inverse_f32", 2.0 * bd * bd * bd, 8.0 * bd * bd, s);
+      e = launch_pivot_inverse<float>(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, (int)k, s);
+    }
+    if (e != cudaSuccess) break;
+    {
+      TraceScope t("row_panel_mixed", 2.0 * bd * bd * rest, 4.0 * (2.0 * bd * nd + bd * bd + rest * bd) + eb * 2.0 * nd * kpad, s);
+      e = bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, status, s)
+               : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, status, s);
+    }
+    if (e != cudaSuccess || n == b) continue;
+    {
+      TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * rest * nd,
+                     4.0 * 2.0 * rest * nd + eb * 2.0 * nd * bd, s);
+      e = bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, status, s)
+               : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, status, s);
+    }
+  }
+  return e;
+}
+
+}  // namespace blockinv

@@ -1,0 +1,203 @@
+// Persistent, warp-specialised tcgen05 GEMM: D[M x N] = A[M x K] * B[N x K]^T
+// with both operands K-major in global memory, fed by TMA into a 4-stage
+// shared-memory ring (128-byte swizzle), accumulated by tcgen05.mma into one
+// of two TMEM accumulators (128 lanes x 256 columns each), and handed to an
+// epilogue functor that reads the accumulator with tcgen05.ld.
+//
+//   warp 0, lane 0   TMA producer            (also allocates/frees TMEM)
+//   warp 1, lane 0   MMA issuer
+//   warps 2..5       epilogue, one TMEM lane quarter each
+//
+// While the epilogue drains accumulator a, the MMA warp fills the other one,
+// so the C traffic of one tile overlaps the loads and MMAs of the next.
+// The K dimension can be split into "slice pairs" (for the split-operand
+// residual): k-block kb of group g reads A columns p * slice_cols + kk * BK
+// and B columns (g - p) * slice_cols + kk * BK, p = kb / kb_per_pair.
+// A plain GEMM uses one pair with group 0.
+//
+// Every mbarrier wait is bounded; on timeout the status word gets
+// BLOCKINV_ERR_TIMEOUT and the roles wind down.
+#pragma once
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace blockinv {
+namespace tc {
+
+constexpr int kBM = 128;
+constexpr int kBN = 256;
+constexpr int kStages = 4;
+constexpr int kGemmThreads = 192;
+constexpr int kStageBytes = kBM * 128 + kBN * 128;
+
+struct KMap {
+  int kblocks;      // k-blocks per output tile
+  int kb_per_pair;  // k-blocks per slice pair
+  int group;        // g: pairs (p, g - p)
+  int slice_cols;   // operand columns between consecutive slices
+};
+
+struct GemmShared {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint32_t tmem_base;
+};
+
+constexpr size_t gemm_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GemmShared) + 1024; }
+
+__device__ __forceinline__ void flag_timeout(int32_t* status) {
+  if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
+}
+
+template <Kind K, class Epi>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int tiles_m,
+            int tiles_n, KMap km, Epi epi, int32_t* status) {
+  constexpr int BK = 128 / KindTraits<K>::elem_bytes;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  GemmShared* sh = reinterpret_cast<GemmShared*>(smem + kStages * kStageBytes);
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ntiles = tiles_m * tiles_n;
+  if (epi.skip()) return;  // an earlier kernel of this computation failed
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh->full[s], 1);
+      mbar_init(&sh->empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&sh->tfull[a], 1);
+      mbar_init(&sh->tempty[a], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&sh->tmem_base, 2 * kBN);
+    tmem_relinquish();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = sh->tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    uint32_t it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int m0 = (t / tiles_n) * kBM;
+      const int n0 = (t % tiles_n) * kBN;
+      for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (it / kStages) & 1;
+        if (!mbar_wait(&sh->empty[s], ph ^ 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char* sa = smem + s * kStageBytes;
+        unsigned char* sb = sa + kBM * 128;
+        mbar_arrive_expect_tx(&sh->full[s], kStageBytes);
+        const int pair = kb / km.kb_per_pair;
+        const int kk = kb - pair * km.kb_per_pair;
+        tma_load_2d(sa, &tmA, &sh->full[s], pair * km.slice_cols + kk * BK, m0);
+        tma_load_2d(sb, &tmB, &sh->full[s], (km.group - pair) * km.slice_cols + kk * BK, n0);
+      }
+    }
+    if (!ok) {
+      flag_timeout(status);
+    } else if (it > 0) {
+      // Let the last copies land before the CTA can leave (bounded).
+      const uint32_t last = it - 1;
+      mbar_wait(&sh->full[last % kStages], (last / kStages) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t id = idesc<K>(kBM, kBN);
+    uint32_t it = 0, tl = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+      const uint32_t a = tl & 1;
+      const uint32_t aph = (tl >> 1) & 1;
+      if (!mbar_wait(&sh->tempty[a], aph ^ 1)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+      const uint32_t d = tmem + a * kBN;
+      for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (it / kStages) & 1;
+        if (!mbar_wait(&sh->full[s], ph)) {
+          ok = false;
+          break;
+        }
+        fence_after_sync();
+        const uint32_t sa = smem_u32(smem + s * kStageBytes);
+        const uint64_t da = sdesc_sw128(sa);
+        const uint64_t db = sdesc_sw128(sa + kBM * 128);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)  // 4 x 32 bytes of K per 128-byte row
+          mma<K>(d, da + 2 * ks, db + 2 * ks, id, (kb | ks) != 0 ? 1u : 0u);
+        mma_commit(&sh->empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&sh->tfull[a]);
+    }
+    if (!ok) flag_timeout(status);
+  } else if (warp >= 2) {
+    const int q = warp & 3;  // the TMEM lane quarter this warp may access
+    uint32_t tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const uint32_t a = tl & 1;
+      const uint32_t aph = (tl >> 1) & 1;
+      if (!mbar_wait(&sh->tfull[a], aph)) {
+        flag_timeout(status);
+        break;
+      }
+      fence_after_sync();
+      const int m0 = (t / tiles_n) * kBM;
+      const int n0 = (t % tiles_n) * kBN;
+      const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+      for (int c = 0; c < kBN / 32; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + c * 32, v);
+        tmem_wait_ld();
+        epi.apply(row, n0 + c * 32, v);
+      }
+      fence_before_sync();
+      mbar_arrive(&sh->tempty[a]);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 2 * kBN);
+  }
+}
+
+int num_sms();
+
+template <Kind K, class Epi>
+cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int N, KMap km, const Epi& epi,
+                        int32_t* status, cudaStream_t s) {
+  const int tiles_m = (M + kBM - 1) / kBM;
+  const int tiles_n = (N + kBN - 1) / kBN;
+  const int ntiles = tiles_m * tiles_n;
+  if (ntiles == 0 || km.kblocks <= 0) return cudaSuccess;
+  auto kern = gemm_kernel<K, Epi>;
+  const size_t smem = gemm_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ntiles < num_sms() ? ntiles : num_sms();
+  kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, km, epi, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace blockinv

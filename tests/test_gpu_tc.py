@@ -1,0 +1,124 @@
+"""The tcgen05 tensor-core GEMM (through blockinv_diag_gemm) and the
+unrefined mixed-precision elimination, through the C ABI.
+
+Tolerances: integer-valued operands whose products and sums stay below 2^24
+must come out exact (FP32 accumulation of exact products), which is the
+property the split-operand FP64-accurate residual relies on. Non-integer
+operands are compared with an FP64 product of the same rounded operands at
+K * 2^-23 relative to |A| |B|. The unrefined TF32 / BF16 elimination is
+compared with the oracle at the precision of its operands.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_11103_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bi(cuda_device):
+    from paper_2305_11103_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2305_11103_gb300 import blockinv
+    blockinv.lib()
+    return blockinv
+
+
+def run_gemm(bi, kind, A, B):
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    st = bi.blockinv_diag_gemm(kind, M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                               C.data_ptr(), C.stride(0), None)
+    assert st == bi.OK, bi.blockinv_status_str(st)
+    return C
+
+
+def padded(t, mult):
+    M, K = t.shape
+    Kp = (K + mult - 1) // mult * mult
+    out = torch.zeros((M, Kp), dtype=t.dtype, device=t.device)
+    out[:, :K] = t
+    return out[:, :K]
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (2125, 1100, 512), (77, 3000, 1024)])
+def test_e4m3_integer_exact(bi, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    Ai = torch.randint(-15, 16, (M, K), generator=g)
+    Bi = torch.randint(-8, 9, (N, K), generator=g)
+    A = padded(Ai.to(torch.float32).to(torch.float8_e4m3fn).cuda(), 16)
+    B = padded(Bi.to(torch.float32).to(torch.float8_e4m3fn).cuda(), 16)
+    C = run_gemm(bi, 2, A, B).cpu().double()
+    ref = Ai.double() @ Bi.double().T
+    assert torch.equal(C, ref)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (1500, 700, 320)])
+def test_bf16_integer_exact(bi, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(7 + M)
+    Ai = torch.randint(-100, 101, (M, K), generator=g)
+    Bi = torch.randint(-100, 101, (N, K), generator=g)
+    A = padded(Ai.to(torch.bfloat16).cuda(), 8)
+    B = padded(Bi.to(torch.bfloat16).cuda(), 8)
+    C = run_gemm(bi, 0, A, B).cpu().double()
+    assert torch.equal(C, Ai.double() @ Bi.double().T)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 96), (1000, 1300, 260)])
+def test_tf32_matches_fp64_of_rounded_operands(bi, M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(11 + M)
+    A = torch.randn(M, K, generator=g)
+    B = torch.randn(N, K, generator=g)
+    # round to TF32 (10 explicit mantissa bits) so that the hardware's operand
+    # conversion is exact
+    def tf32(x):
+        u = x.view(torch.int32)
+        u = (u + 0x1000) & ~0x1FFF
+        return u.view(torch.float32)
+    A, B = tf32(A), tf32(B)
+    C = run_gemm(bi, 1, padded(A.cuda(), 4), padded(B.cuda(), 4)).cpu().double()
+    ref = A.double() @ B.double().T
+    scale = A.abs().double() @ B.abs().double().T
+    assert torch.all((C - ref).abs() <= K * 2.0 ** -23 * scale + 1e-30)
+
+
+def test_tf32_integer_exact(bi):
+    g = torch.Generator(device="cpu").manual_seed(5)
+    Ai = torch.randint(-300, 301, (640, 128), generator=g).float()
+    Bi = torch.randint(-300, 301, (384, 128), generator=g).float()
+    C = run_gemm(bi, 1, Ai.cuda(), Bi.cuda()).cpu().double()
+    assert torch.equal(C, Ai.double() @ Bi.double().T)
+
+
+# ------------------------------------------------------ mixed elimination ---
+def mixed_unrefined(bi, A, sizes, mode):
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(A.shape[0], sizes, d.data_ptr(), A.shape[0], mode, None, max_refine=0)
+    assert st == bi.OK, bi.blockinv_status_str(st)
+    return d.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode,tol", [("tf32", 2e-3), ("bf16", 3e-2)])
+@pytest.mark.parametrize("sizes", [[256] * 4, [100, 157, 63], [64] * 5 + [37], [512, 300]])
+def test_mixed_elimination_vs_oracle(bi, mode, tol, sizes):
+    n = sum(sizes)
+    A = inputs.gaussian_shifted(n, 3 + n, sigma=1.5)
+    X = mixed_unrefined(bi, A, sizes, mode)
+    Xo = oracle.block_inverse(A, sizes)
+    eps = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    assert eps <= tol, eps
+
+
+def test_mixed_tf32_unimodular_exact(bi):
+    """Small-integer inputs whose inverse stays below 2^11: every product and
+    sum is exact in TF32 / FP32, so the mixed elimination is exact too."""
+    sizes = [4, 4, 4, 4]
+    A, _, _ = inputs.unimodular_block_lu(sizes, 5, lower_density=0.3)
+    Xo = oracle.block_inverse(A, sizes)
+    assert np.abs(Xo).max() < 2 ** 10
+    X = mixed_unrefined(bi, A, sizes, "tf32")
+    assert np.array_equal(X, Xo)
