@@ -146,6 +146,16 @@ int blockinv_diag_gemm(int kind, int64_t M, int64_t N, int64_t K, const void* A,
 int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X,
                       int64_t ldx, double* rho_out, void* stream);
 
+/* FP64-accurate residual on the tensor cores: E = I - A X and
+ * rho = ||E||_F / (||A||_F ||X||_F). The diagonal terms are exact FP64
+ * products; the off-diagonal product comes from `slices` (9..13, 0 = 12)
+ * base-16 FP8 digits of A (by rows) and X (by columns) whose products
+ * accumulate exactly. This is the residual the mixed modes' Newton-Schulz
+ * refinement uses; blockinv_residual is the plain FP64 reference. Device
+ * pointers; E (leading dimension lde) may be NULL. n <= 16384. Blocking. */
+int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, double* E,
+                         int64_t lde, int slices, double* rho_out, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* blockinv_status_str(int status);
 

@@ -32,6 +32,8 @@ SIGNATURES = {
     "blockinv_invert_async": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp]),
     "blockinv_invert_host": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
     "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "blockinv_residual_tc": (_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(ctypes.c_double),
+                                     _vp]),
     "blockinv_status_str": (ctypes.c_char_p, [_int]),
     "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_version": (_int, []),
@@ -134,6 +136,13 @@ def blockinv_invert_host(n, block_sizes, A_host_ptr, lda, mode=F64, stream=None)
 def blockinv_residual(n, A_ptr, lda, X_ptr, ldx, stream=None):
     rho = ctypes.c_double(0.0)
     st = lib().blockinv_residual(n, A_ptr, lda, X_ptr, ldx, ctypes.byref(rho), _stream_ptr(stream))
+    return st, rho.value
+
+
+def blockinv_residual_tc(n, A_ptr, lda, X_ptr, ldx, E_ptr=None, lde=0, slices=0, stream=None):
+    rho = ctypes.c_double(0.0)
+    st = lib().blockinv_residual_tc(n, A_ptr, lda, X_ptr, ldx, E_ptr, lde, slices, ctypes.byref(rho),
+                                    _stream_ptr(stream))
     return st, rho.value
 
 

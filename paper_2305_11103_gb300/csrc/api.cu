@@ -192,18 +192,65 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int32_
   return cuda_status(e);
 }
 
+// Device records of a mixed-precision solve: the untouched input (for the
+// residuals and the FP64 fallback), the refinement workspace, the rho history
+// and the refinement control words. Released in stream order.
+struct MixedState {
+  AsyncBuf a0, ws, hist, ctl;
+  int max_refine = 0;
+  double* A0() const { return static_cast<double*>(a0.ptr); }
+};
+
+int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* status, cudaStream_t s,
+                  const Options& opt, MixedState& ms) {
+  const int n = pl.n;
+  ms.max_refine = opt.max_refine;
+  const size_t row = sizeof(double) * (size_t)n;
+  cudaError_t e = ms.a0.alloc(row * n, s);
+  if (e == cudaSuccess) e = ms.hist.alloc(sizeof(double) * (opt.max_refine + 1), s);
+  if (e == cudaSuccess) e = ms.ctl.alloc(4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ms.ctl.ptr, 0, 4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ms.hist.ptr, 0xFF, sizeof(double) * (opt.max_refine + 1), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(ms.a0.ptr, row, A, sizeof(double) * lda, row, n, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = enqueue_mixed_elim(pl, A, lda, bf16, status, s);
+  if (st != BLOCKINV_OK || opt.max_refine == 0) return st;
+  e = ms.ws.alloc(refine_workspace_bytes(n, kResidualSlices, opt.max_refine), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = enqueue_refine(ms.A0(), n, A, lda, n, opt.tol, opt.max_refine, kResidualSlices, ms.ws.ptr,
+                     static_cast<double*>(ms.hist.ptr), static_cast<int32_t*>(ms.ctl.ptr), status, nullptr, 0, s,
+                     true);
+  return cuda_status(e);
+}
+
 int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s,
-            const Options& opt) {
+            const Options& opt, MixedState* ms) {
   switch (mode) {
     case BLOCKINV_F64:
       return enqueue_f64(pl, A, lda, status, s);
     case BLOCKINV_MIXED_TF32:
-    case BLOCKINV_MIXED_BF16:
-      if (opt.max_refine == 0)
-        return enqueue_mixed_elim(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s);
-      return BLOCKINV_ERR_NOT_CONVERGED;  // refinement is enqueued by invert_ex
+    case BLOCKINV_MIXED_BF16: {
+      MixedState local;
+      return enqueue_mixed(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s, opt, ms ? *ms : local);
+    }
     default:
       return BLOCKINV_ERR_INVALID;
+  }
+}
+
+// After a blocking mixed solve: copy the refinement record into info.
+void read_mixed_info(const MixedState& ms, cudaStream_t s, blockinv_info* info) {
+  if (!info || !ms.hist.ptr) return;
+  std::vector<double> hist(ms.max_refine + 1, -1.0);
+  int32_t ctl[4] = {0, 0, 0, -1};
+  cudaMemcpyAsync(hist.data(), ms.hist.ptr, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(ctl, ms.ctl.ptr, sizeof(ctl), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return;
+  info->refine_iters = ctl[1];
+  if (ctl[3] >= 0) {
+    info->rho_initial = hist[0];
+    info->rho = hist[ctl[3]];
   }
 }
 
@@ -254,7 +301,7 @@ int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
-  return record(enqueue(pl, A, lda, mode, status_dev, s, Options()), -1);
+  return record(enqueue(pl, A, lda, mode, status_dev, s, Options(), nullptr), -1);
 }
 
 int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int mode,
@@ -279,18 +326,31 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
   if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
-  st = enqueue(pl, A, lda, mode, status, s, opt);
+  MixedState ms;
+  st = enqueue(pl, A, lda, mode, status, s, opt, &ms);
   if (st != BLOCKINV_OK) {
     cudaStreamSynchronize(s);
     if (info) info->status = st;
     return record(st, -1);
   }
   st = finish(status, s);
+  const int64_t fb = g_last_block;
+  read_mixed_info(ms, s, info);
+  if (st == BLOCKINV_ERR_NOT_CONVERGED && opt.fallback && ms.a0.ptr) {
+    // The low-precision elimination or its refinement failed: redo in FP64.
+    const size_t row = sizeof(double) * (size_t)n;
+    e = cudaMemcpy2DAsync(A, sizeof(double) * lda, ms.a0.ptr, row, row, n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return record(cuda_status(e), -1);
+    st = enqueue_f64(pl, A, lda, status, s);
+    if (st == BLOCKINV_OK) st = finish(status, s);
+    if (info) info->used_fallback = 1;
+  }
   if (info) {
     info->status = st;
-    info->failing_block = g_last_block;
+    info->failing_block = (st == BLOCKINV_OK) ? -1 : (st == BLOCKINV_ERR_NOT_CONVERGED ? -1 : fb);
   }
-  return st;
+  return record(st, info ? info->failing_block : g_last_block);
 }
 
 int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int mode,
@@ -315,7 +375,7 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
                           cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
-  st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s, Options());
+  st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s, Options(), nullptr);
   if (st != BLOCKINV_OK) {
     cudaStreamSynchronize(s);
     return record(st, -1);
@@ -341,6 +401,33 @@ int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X, 
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   *rho_out = std::sqrt(h[0]) / (std::sqrt(h[1]) * std::sqrt(h[2]));
   return record(BLOCKINV_OK, -1);
+}
+
+int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, double* E,
+                         int64_t lde, int slices, double* rho_out, void* stream) {
+  if (slices == 0) slices = kResidualSlices;
+  if (n < 1 || n > 16384 || lda < n || ldx < n || !A || !X || !rho_out || (E && lde < n) || slices < 9 ||
+      slices > 13)
+    return record(BLOCKINV_ERR_INVALID, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  AsyncBuf ws, hist, ctl, sbuf;
+  cudaError_t e = ws.alloc(refine_workspace_bytes((int)n, slices, 0), s);
+  if (e == cudaSuccess) e = hist.alloc(sizeof(double), s);
+  if (e == cudaSuccess) e = ctl.alloc(4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = sbuf.alloc(2 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
+  if (e == cudaSuccess)
+    e = enqueue_refine(A, lda, const_cast<double*>(X), ldx, (int)n, 0.0, 0, slices, ws.ptr,
+                       static_cast<double*>(hist.ptr), static_cast<int32_t*>(ctl.ptr),
+                       static_cast<int32_t*>(sbuf.ptr), E, lde, s, false);
+  double rho = -1.0;
+  int32_t st[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&rho, hist.ptr, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st, sbuf.ptr, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  *rho_out = rho;
+  return record(st[0], -1);
 }
 
 const char* blockinv_status_str(int status) {

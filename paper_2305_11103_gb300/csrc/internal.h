@@ -85,4 +85,11 @@ int mixed_kpad(int bmax);
 cudaError_t mixed_elimination(const Plan& pl, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, int32_t* status, cudaStream_t s);
 
+// Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
+constexpr int kResidualSlices = 12;
+size_t refine_workspace_bytes(int n, int S, int max_updates);
+cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
+                           int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
+                           double* Eout, int64_t lde, cudaStream_t s, bool report);
+
 }  // namespace blockinv

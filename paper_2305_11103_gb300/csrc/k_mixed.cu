@@ -205,7 +205,7 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float*
                             int b, int32_t* status, cudaStream_t s) {
   constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
   const int kb = (b + BK - 1) / BK;
-  tc::KMap km{kb, kb, 0, 0};
+  tc::KMap km = tc::plain_kmap(kb);
   EpiSchurF32 epi{X, ldx, n, o, b, status};
   return tc::launch_gemm<K>(tU, tV, n, n, km, epi, status, s);
 }

@@ -1,0 +1,539 @@
+// Newton-Schulz refinement of an approximate inverse, X <- X + X (I - A X)
+// (the same step as X (2I - A X)), with the residual E = I - A X computed to
+// FP64 accuracy on the FP8 tensor cores.
+//
+// FP64-accurate residual (error-free splitting, after Ozaki et al.'s scheme
+// for accurate matrix products). The diagonals are split off first:
+// A = D_A + O_A, X = D_X + O_X, and
+//
+//   A X = D_A X + O_A D_X + O_A O_X,
+//
+// where the first two terms are elementwise FP64 products (a_ii x_ij and
+// a_ij x_jj) and only O_A O_X needs a matrix product. Scaling the rows of O_A
+// and the columns of O_X by their own maxima, rather than by a dominant
+// diagonal, keeps the bits of the off-diagonal entries. Every row i of O_A is
+// scaled by a power of two 2^-e_i (e_i the smallest integer with
+// max_k |a_ik| < 2^e_i, k != i) and every column j of O_X by 2^-f_j; the
+// scaled values, as fixed-point numbers with 4S fraction bits, are cut into S
+// signed base-16 digits (the leading digit in [-16, 16], the others in
+// [-8, 7]), each exact in FP8 E4M3. Then
+//
+//   (O_A O_X)_ij ~= 2^(e_i + f_j - 8) sum_g 2^(-4g) G_g(i, j),
+//   G_g = sum_{p + q = g} Adigits_p Xdigits_q^T      (g = 0 .. S - 1),
+//
+// where each G_g is an integer matrix whose entries stay below 2^24 for
+// K <= 16384, so the FP32 tensor-core accumulator holds it exactly. Each group
+// is one GEMM over its digit pairs; its epilogue adds G_g << 4 (S - 1 - g)
+// into an int64 accumulator, again exactly. The finalize kernel converts to
+// FP64, forms E = I - A X, its Frobenius norm and the operands of the update.
+// Dropped groups (p + q >= S) and truncated digits leave an error of order
+// 2^(-4S - 8) S sqrt(K) relative to the row and column scales.
+//
+// The update X += X E uses split TF32 operands (hi + lo for X and E, the
+// three products hi*hi + hi*lo + lo*hi) with the FP32 accumulator added to
+// the FP64 X in the epilogue; E is small, so the correction needs far fewer
+// bits than X itself.
+//
+// The iteration is stream-ordered: after each residual a one-thread kernel
+// computes rho = ||E||_F / (||A||_F ||X||_F), records it, and raises a device
+// flag when rho <= tol, when rho fails to drop by 4x (no contraction), or at
+// the iteration cap. Every later kernel of the refinement returns at once
+// when the flag is up.
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "tc_gemm.cuh"
+
+namespace blockinv {
+
+namespace {
+
+constexpr int kLog2Digit = 4;
+
+struct Ctl {
+  int32_t done;        // refinement finished (converged or gave up)
+  int32_t updates;     // updates applied
+  int32_t code;        // BLOCKINV_OK or BLOCKINV_ERR_NOT_CONVERGED once done
+  int32_t last;        // index of the last residual computed
+};
+
+__device__ __forceinline__ bool halted(const Ctl* ctl, const int32_t* status) {
+  return *(volatile const int32_t*)&ctl->done != 0 || *(volatile const int32_t*)status != 0;
+}
+
+// Smallest e with |v| < 2^e for normal v (from the exponent field); very
+// negative for zero.
+__device__ __forceinline__ int exp_bound(double v) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  return static_cast<int>((bits >> 52) & 0x7FF) - 1022;
+}
+
+// Fixed-point integer round(v * 2^(4S - e)) from the bit pattern, |v| < 2^e.
+__device__ __forceinline__ long long fixed_point(double v, int e, int S) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int ef = static_cast<int>((bits >> 52) & 0x7FF);
+  if (ef == 0) return 0;  // zero or subnormal: below every digit kept
+  const long long m = static_cast<long long>((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  // v = m * 2^(ef - 1075); shift = ef - 1075 + 4S - e (always negative here)
+  const int sh = ef - 1075 + kLog2Digit * S - e;
+  long long q;
+  if (sh >= 0) {
+    q = m << sh;
+  } else if (sh <= -62) {
+    q = 0;
+  } else {
+    q = (m + (1ll << (-sh - 1))) >> (-sh);
+  }
+  return (bits >> 63) ? -q : q;
+}
+
+__device__ __forceinline__ uint8_t e4m3(int d) {
+  return static_cast<uint8_t>(__nv_cvt_float_to_fp8(static_cast<float>(d), __NV_SATFINITE, __NV_E4M3));
+}
+
+// Balanced base-16 digits of q, most significant first: d[0] in [-16, 16],
+// d[1..S-1] in [-8, 7], q = sum_p d[p] 16^(S-1-p).
+template <int S>
+__device__ __forceinline__ void digits(long long q, int (&d)[S]) {
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    const int r = static_cast<int>(((q + 8) & 15)) - 8;
+    d[p] = r;
+    q = (q - r) >> 4;
+  }
+  d[0] = static_cast<int>(q);
+}
+
+// ---------------------------------------------------------- scales -------
+// One warp per row: e_i = max exponent bound over the row, and sum of squares.
+__global__ void row_scale_kernel(const double* __restrict__ M, int64_t ld, int n, int32_t* __restrict__ rexp,
+                                 double* __restrict__ sumsq, const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = M + (int64_t)warp * ld;
+  int e = -2000;
+  double s2 = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    const double v = row[k];
+    if (k != warp) e = max(e, exp_bound(v));
+    s2 = fma(v, v, s2);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e = max(e, __shfl_xor_sync(0xffffffffu, e, off));
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  }
+  if (lane == 0) {
+    rexp[warp] = e;
+    atomicAdd(sumsq, s2);
+  }
+}
+
+// Column exponent bounds (atomicMax per column after a CTA reduction) and the
+// sum of squares. cexp must hold a very negative value beforehand.
+__global__ void col_scale_kernel(const double* __restrict__ X, int64_t ld, int n, int32_t* __restrict__ cexp,
+                                 double* __restrict__ sumsq, const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  __shared__ int se[8][32];
+  __shared__ double ss[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx;
+  const int r0 = blockIdx.y * 256;
+  int e = -2000;
+  double s2 = 0.0;
+  if (j < n) {
+    for (int r = r0 + ty; r < min(n, r0 + 256); r += 8) {
+      const double v = X[(int64_t)r * ld + j];
+      if (r != j) e = max(e, exp_bound(v));
+      s2 = fma(v, v, s2);
+    }
+  }
+  se[ty][tx] = e;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  if (tx == 0) ss[ty] = s2;
+  __syncthreads();
+  if (ty == 0) {
+    int m = se[0][tx];
+    for (int y = 1; y < 8; ++y) m = max(m, se[y][tx]);
+    if (j < n) atomicMax(&cexp[j], m);
+    if (tx == 0) {
+      double t = 0.0;
+      for (int y = 0; y < 8; ++y) t += ss[y];
+      atomicAdd(sumsq, t);
+    }
+  }
+}
+
+// ---------------------------------------------------------- slicing ------
+// Row slices: out[i][p * Kp + k] = digit p of A[i][k] / 2^e_i (k < n), 4 k per thread.
+template <int S>
+__global__ void slice_rows_kernel(const double* __restrict__ M, int64_t ld, int n, const int32_t* __restrict__ rexp,
+                                  int Kp, uint8_t* __restrict__ out, const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  const int64_t quads = (int64_t)n * (Kp / 4);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < quads; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / (Kp / 4));
+    const int k0 = (int)(t - (int64_t)i * (Kp / 4)) * 4;
+    const int e = rexp[i];
+    uint32_t w[S];
+#pragma unroll
+    for (int p = 0; p < S; ++p) w[p] = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = k0 + c;
+      if (k < n) {
+        int d[S];
+        digits<S>(fixed_point(k == i ? 0.0 : M[(int64_t)i * ld + k], e, S), d);
+#pragma unroll
+        for (int p = 0; p < S; ++p) w[p] |= static_cast<uint32_t>(e4m3(d[p])) << (8 * c);
+      }
+    }
+    uint8_t* base = out + (int64_t)i * S * Kp + k0;
+#pragma unroll
+    for (int p = 0; p < S; ++p) *reinterpret_cast<uint32_t*>(base + (int64_t)p * Kp) = w[p];
+  }
+}
+
+// Transposed column slices: out[j][q * Kp + k] = digit q of X[k][j] / 2^f_j.
+// Tiles of 64 k x 32 j through shared memory.
+template <int S>
+__global__ void __launch_bounds__(256)
+slice_cols_t_kernel(const double* __restrict__ X, int64_t ld, int n, const int32_t* __restrict__ cexp, int Kp,
+                    uint8_t* __restrict__ out, const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  __shared__ uint8_t sd[S][32][68];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
+  const int j = j0 + tx;
+  const int f = (j < n) ? cexp[j] : 0;
+  for (int kk = ty; kk < 64; kk += 8) {
+    const int k = k0 + kk;
+    int d[S];
+    const double v = (j < n && k < n && k != j) ? X[(int64_t)k * ld + j] : 0.0;
+    digits<S>(fixed_point(v, f, S), d);
+#pragma unroll
+    for (int p = 0; p < S; ++p) sd[p][tx][kk] = e4m3(d[p]);
+  }
+  __syncthreads();
+  // write: each (p, jj) row segment of 64 bytes = 16 words; 256 threads -> 16 (p, jj) per pass
+  for (int t = threadIdx.x; t < S * 32 * 16; t += 256) {
+    const int w = t & 15;
+    const int jj = (t >> 4) & 31;
+    const int p = t >> 9;
+    const int jg = j0 + jj;
+    if (jg < n) {
+      const uint32_t word = *reinterpret_cast<const uint32_t*>(&sd[p][jj][w * 4]);
+      *reinterpret_cast<uint32_t*>(out + (int64_t)jg * S * Kp + (int64_t)p * Kp + k0 + w * 4) = word;
+    }
+  }
+}
+
+// -------------------------------------------------------- epilogues ------
+struct EpiAccumI64 {
+  long long* T;
+  int64_t ldt;
+  int n;
+  int shift;
+  int first;
+  const Ctl* ctl;
+  const int32_t* status;
+  __device__ bool skip() const { return halted(ctl, status); }
+  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
+    if (row >= n) return;
+    long long* p = T + (int64_t)row * ldt + col0;
+#pragma unroll
+    for (int q = 0; q < 32; q += 2) {
+      if (col0 + q + 1 < n) {
+        longlong2 cur = first ? make_longlong2(0, 0) : *reinterpret_cast<longlong2*>(p + q);
+        cur.x += static_cast<long long>(__float2ll_rn(__uint_as_float(v[q]))) << shift;
+        cur.y += static_cast<long long>(__float2ll_rn(__uint_as_float(v[q + 1]))) << shift;
+        *reinterpret_cast<longlong2*>(p + q) = cur;
+      } else if (col0 + q < n) {
+        const long long cur = first ? 0 : p[q];
+        p[q] = cur + (static_cast<long long>(__float2ll_rn(__uint_as_float(v[q]))) << shift);
+      }
+    }
+  }
+};
+
+struct EpiAddF64 {
+  double* X;
+  int64_t ldx;
+  int n;
+  const Ctl* ctl;
+  const int32_t* status;
+  __device__ bool skip() const { return halted(ctl, status); }
+  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
+    if (row >= n) return;
+    double* p = X + (int64_t)row * ldx + col0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (col0 + q < n) p[q] += static_cast<double>(__uint_as_float(v[q]));
+  }
+};
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+// E = I - a_ii x_ij - [i != j] a_ij x_jj - 2^(e_i + f_j - 8 - 4 (S - 1)) T;
+// ||E||^2; E^T split into TF32 hi/lo (rows j of Eop, columns i and Kp + i);
+// optionally E itself in FP64.
+__global__ void __launch_bounds__(256)
+finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const double* __restrict__ A,
+                int64_t lda, const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ rexp,
+                const int32_t* __restrict__ cexp, int S, double* __restrict__ e2sum, float* __restrict__ Eop,
+                int Kp, double* __restrict__ Eout, int64_t lde, const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  __shared__ double tile[32][33];
+  __shared__ double red[8];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int j = j0 + tx;
+  double s2 = 0.0;
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii;
+    double e = 0.0;
+    if (i < n && j < n) {
+      const int ex = rexp[i] + cexp[j] - 8 - kLog2Digit * (S - 1);
+      const long long t = T[(int64_t)i * ldt + j];
+      const double r = (t == 0) ? 0.0 : ldexp(static_cast<double>(t), ex);
+      const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
+      if (i == j) {
+        e = (1.0 - dx) - r;
+      } else {
+        e = -fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx) - r;   // (O_A D_X)_ij
+      }
+      s2 = fma(e, e, s2);
+      if (Eout) Eout[(int64_t)i * lde + j] = e;
+    }
+    tile[ii][tx] = e;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  if (tx == 0) red[ty] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int y = 0; y < 8; ++y) t += red[y];
+    atomicAdd(e2sum, t);
+  }
+  if (!Eop) return;
+  // transposed write: row j of Eop gets E[i0..i0+31][j]
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int jg = j0 + jj;
+    const int i = i0 + tx;
+    if (jg < n && i < n) {
+      const float v = static_cast<float>(tile[tx][jj]);
+      const float hi = tf32_rn(v);
+      const float lo = tf32_rn(static_cast<float>(tile[tx][jj] - static_cast<double>(hi)));
+      Eop[(int64_t)jg * 2 * Kp + i] = hi;
+      Eop[(int64_t)jg * 2 * Kp + Kp + i] = lo;
+    }
+  }
+}
+
+// X split into TF32 hi/lo operands (rows i, columns k and Kp + k).
+__global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n, float* __restrict__ Xop, int Kp,
+                               const Ctl* ctl, const int32_t* status) {
+  if (halted(ctl, status)) return;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n);
+    const int k = (int)(t - (int64_t)i * n);
+    const double v = X[(int64_t)i * ldx + k];
+    const float hi = tf32_rn(static_cast<float>(v));
+    const float lo = tf32_rn(static_cast<float>(v - static_cast<double>(hi)));
+    Xop[(int64_t)i * 2 * Kp + k] = hi;
+    Xop[(int64_t)i * 2 * Kp + Kp + k] = lo;
+  }
+}
+
+// rho for residual `it`; decides whether refinement goes on.
+__global__ void decide_kernel(const double* sums, int it, double tol, int max_updates, double* hist, Ctl* ctl,
+                              const int32_t* status) {
+  if (ctl->done || *status != 0) return;
+  const double a2 = sums[0], e2 = sums[1 + 2 * it], x2 = sums[2 + 2 * it];
+  const double rho = sqrt(e2) / (sqrt(a2) * sqrt(x2));
+  hist[it] = rho;
+  ctl->last = it;
+  if (rho <= tol) {
+    ctl->done = 1;
+    ctl->code = BLOCKINV_OK;
+  } else if (it >= max_updates || !(rho == rho) || (it > 0 && !(rho < 0.25 * hist[it - 1]))) {
+    ctl->done = 1;
+    ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
+  } else {
+    ctl->updates = it + 1;
+  }
+}
+
+__global__ void finish_kernel(const Ctl* ctl, int32_t* status) {
+  if (*status == 0 && ctl->code != BLOCKINV_OK) atomicCAS(&status[0], 0, ctl->code);
+}
+
+__global__ void init_ctl_kernel(Ctl* ctl, int32_t* cexp, int n, int iters) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->done = 0;
+    ctl->updates = 0;
+    ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
+    ctl->last = -1;
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * iters; t += gridDim.x * blockDim.x) cexp[t] = -2000;
+}
+
+template <int S>
+cudaError_t launch_slices(const double* A0, int64_t ld0, const double* X, int64_t ldx, int n, int Kp,
+                          const int32_t* rexp, int32_t* cexp, uint8_t* Asl, uint8_t* Xsl, double* x2, bool rows,
+                          const Ctl* ctl, const int32_t* status, cudaStream_t s) {
+  if (rows) {
+    const int64_t quads = (int64_t)n * (Kp / 4);
+    const int grid = (int)std::min<int64_t>((quads + 255) / 256, 16 * tc::num_sms());
+    slice_rows_kernel<S><<<grid, 256, 0, s>>>(A0, ld0, n, rexp, Kp, Asl, ctl, status);
+    return cudaGetLastError();
+  }
+  dim3 g1((n + 31) / 32, (n + 255) / 256);
+  col_scale_kernel<<<g1, 256, 0, s>>>(X, ldx, n, cexp, x2, ctl, status);
+  dim3 g2((n + 31) / 32, Kp / 64);
+  slice_cols_t_kernel<S><<<g2, 256, 0, s>>>(X, ldx, n, cexp, Kp, Xsl, ctl, status);
+  return cudaGetLastError();
+}
+
+cudaError_t slices_dispatch(int S, const double* A0, int64_t ld0, const double* X, int64_t ldx, int n, int Kp,
+                            const int32_t* rexp, int32_t* cexp, uint8_t* Asl, uint8_t* Xsl, double* x2, bool rows,
+                            const Ctl* ctl, const int32_t* status, cudaStream_t s) {
+  switch (S) {
+    case 9: return launch_slices<9>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 10: return launch_slices<10>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 11: return launch_slices<11>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 12: return launch_slices<12>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 13: return launch_slices<13>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t refine_workspace_bytes(int n, int S, int max_updates) {
+  const size_t Kp = (size_t)(n + 127) / 128 * 128;
+  const size_t ldt = (size_t)(n + 31) / 32 * 32;
+  size_t b = 0;
+  b += 2 * (size_t)n * S * Kp;                  // A and X digit slices
+  b += sizeof(long long) * (size_t)n * ldt;     // int64 accumulator
+  b += 2 * sizeof(float) * (size_t)n * 2 * Kp;  // X and E^T TF32 hi/lo operands
+  b += sizeof(int32_t) * (size_t)n * (max_updates + 2);   // exponents
+  b += sizeof(double) * (3 + 2 * (max_updates + 1)) + sizeof(double) * (max_updates + 1) + 64;
+  return b + 8 * 256;
+}
+
+// Enqueue the refinement of X (n x n, FP64, in place) toward A0^-1.
+// ws must hold refine_workspace_bytes(n, S, max_updates) bytes. hist (device,
+// max_updates + 1 doubles) receives the rho of every residual computed; ctl
+// (device, 4 int32: done, updates, code, last) the outcome. If Eout is
+// non-null and max_updates == 0, the residual E = I - A0 X is written there.
+// With `report`, a refinement that stops short of tol sets the status word to
+// BLOCKINV_ERR_NOT_CONVERGED.
+cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
+                           int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
+                           double* Eout, int64_t lde, cudaStream_t s, bool report) {
+  if (S < 9 || S > 13 || n < 1) return cudaErrorInvalidValue;
+  Ctl* ctl = reinterpret_cast<Ctl*>(ctl_words);
+  const int Kp = (n + 127) / 128 * 128;
+  const int64_t ldt = (n + 31) / 32 * 32;
+  auto carve = [&](size_t bytes) {
+    uintptr_t p = (reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255);
+    ws = reinterpret_cast<void*>(p + bytes);
+    return reinterpret_cast<void*>(p);
+  };
+  uint8_t* Asl = static_cast<uint8_t*>(carve((size_t)n * S * Kp));
+  uint8_t* Xsl = static_cast<uint8_t*>(carve((size_t)n * S * Kp));
+  long long* T = static_cast<long long*>(carve(sizeof(long long) * (size_t)n * ldt));
+  float* Xop = static_cast<float*>(carve(sizeof(float) * (size_t)n * 2 * Kp));
+  float* Eop = static_cast<float*>(carve(sizeof(float) * (size_t)n * 2 * Kp));
+  int32_t* rexp = static_cast<int32_t*>(carve(sizeof(int32_t) * n));
+  int32_t* cexp = static_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)n * (max_updates + 1)));
+  double* sums = static_cast<double*>(carve(sizeof(double) * (1 + 2 * (max_updates + 1))));
+
+  cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * (1 + 2 * (max_updates + 1)), s);
+  // K padding of the operands must be zero (only columns < n are written).
+  if (e == cudaSuccess) e = cudaMemsetAsync(Asl, 0, (size_t)n * S * Kp, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Xsl, 0, (size_t)n * S * Kp, s);
+  if (e == cudaSuccess && max_updates > 0) e = cudaMemsetAsync(Xop, 0, sizeof(float) * (size_t)n * 2 * Kp, s);
+  if (e == cudaSuccess && max_updates > 0) e = cudaMemsetAsync(Eop, 0, sizeof(float) * (size_t)n * 2 * Kp, s);
+  if (e != cudaSuccess) return e;
+  init_ctl_kernel<<<64, 256, 0, s>>>(ctl, cexp, n, max_updates + 1);
+
+  CUtensorMap tAs, tXs, tXo, tEo;
+  if (!make_tmap_2d(&tAs, Asl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBM) ||
+      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN) ||
+      !make_tmap_2d(&tXo, Xop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBM) ||
+      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN))
+    return cudaErrorInvalidValue;
+
+  const double nd = n;
+  {
+    TraceScope t("residual_slice_a", 0, 8.0 * nd * nd + (double)S * nd * Kp, s);
+    row_scale_kernel<<<(n + 7) / 8, 256, 0, s>>>(A0, ld0, n, rexp, &sums[0], ctl, status);
+    e = slices_dispatch(S, A0, ld0, nullptr, 0, n, Kp, rexp, nullptr, Asl, nullptr, nullptr, true, ctl, status, s);
+  }
+  for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {
+    int32_t* cx = cexp + (size_t)it * n;
+    {
+      TraceScope t("residual_slice_x", 0, 16.0 * nd * nd + (double)S * nd * Kp, s);
+      e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
+                          status, s);
+    }
+    for (int g = 0; g < S && e == cudaSuccess; ++g) {
+      tc::KMap km{};
+      km.kb_per_pair = Kp / 128;
+      km.slice_cols = Kp;
+      km.kblocks = (g + 1) * km.kb_per_pair;
+      for (int p = 0; p <= g; ++p) {
+        km.pa[p] = (int8_t)p;
+        km.pb[p] = (int8_t)(g - p);
+      }
+      EpiAccumI64 epi{T, ldt, n, kLog2Digit * (S - 1 - g), g == 0 ? 1 : 0, ctl, status};
+      TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * (g + 1), (double)(g + 1) * 2.0 * nd * Kp + 16.0 * nd * nd, s);
+      e = tc::launch_gemm<tc::Kind::E4M3>(tAs, tXs, n, n, km, epi, status, s);
+    }
+    if (e != cudaSuccess) break;
+    {
+      TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 8.0 * nd * nd : 0.0), s);
+      dim3 g((n + 31) / 32, (n + 31) / 32);
+      finalize_kernel<<<g, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
+                                        it < max_updates ? Eop : nullptr, Kp,
+                                        (max_updates == 0) ? Eout : nullptr, lde, ctl, status);
+    }
+    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status);
+    if (it == max_updates) break;
+    {
+      TraceScope t("ns_split_x", 0, 16.0 * nd * nd, s);
+      split_x_kernel<<<8 * tc::num_sms(), 256, 0, s>>>(X, ldx, n, Xop, Kp, ctl, status);
+    }
+    {
+      tc::KMap km{};
+      km.kb_per_pair = Kp / 32;
+      km.slice_cols = Kp;
+      km.kblocks = 3 * km.kb_per_pair;
+      km.pa[0] = 0; km.pb[0] = 0;
+      km.pa[1] = 0; km.pb[1] = 1;
+      km.pa[2] = 1; km.pb[2] = 0;
+      EpiAddF64 epi{X, ldx, n, ctl, status};
+      TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd + 16.0 * nd * Kp, s);
+      e = tc::launch_gemm<tc::Kind::TF32>(tXo, tEo, n, n, km, epi, status, s);
+    }
+  }
+  if (e == cudaSuccess && report) {
+    finish_kernel<<<1, 1, 0, s>>>(ctl, status);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace blockinv

@@ -76,7 +76,7 @@ int diag(int M, int N, int Kdim, const void* A, int64_t lda, const void* B, int6
   if (!make_tmap_2d(&ta, A, dt, (uint64_t)Kdim, (uint64_t)M, (uint64_t)lda * eb, BK, tc::kBM) ||
       !make_tmap_2d(&tb, B, dt, (uint64_t)Kdim, (uint64_t)N, (uint64_t)ldb * eb, BK, tc::kBN))
     return BLOCKINV_ERR_INVALID;
-  tc::KMap km{(Kdim + BK - 1) / BK, (Kdim + BK - 1) / BK, 0, 0};
+  tc::KMap km = tc::plain_kmap((Kdim + BK - 1) / BK);
   EpiStoreF32 epi{C, ldc, M, N};
   cudaError_t e = tc::launch_gemm<K>(ta, tb, M, N, km, epi, nullptr, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -10,10 +10,11 @@
 //
 // While the epilogue drains accumulator a, the MMA warp fills the other one,
 // so the C traffic of one tile overlaps the loads and MMAs of the next.
-// The K dimension can be split into "slice pairs" (for the split-operand
-// residual): k-block kb of group g reads A columns p * slice_cols + kk * BK
-// and B columns (g - p) * slice_cols + kk * BK, p = kb / kb_per_pair.
-// A plain GEMM uses one pair with group 0.
+// The K dimension can run over a list of operand "slice pairs" (for
+// split-operand products): k-block kb belongs to pair i = kb / kb_per_pair
+// and reads A columns pa[i] * slice_cols + kk * BK and B columns
+// pb[i] * slice_cols + kk * BK, kk = kb - i * kb_per_pair. All pairs
+// accumulate into the same FP32 accumulator. A plain GEMM has one pair (0, 0).
 //
 // Every mbarrier wait is bounded; on timeout the status word gets
 // BLOCKINV_ERR_TIMEOUT and the roles wind down.
@@ -30,12 +31,23 @@ constexpr int kStages = 4;
 constexpr int kGemmThreads = 192;
 constexpr int kStageBytes = kBM * 128 + kBN * 128;
 
+constexpr int kMaxPairs = 16;
+
 struct KMap {
-  int kblocks;      // k-blocks per output tile
-  int kb_per_pair;  // k-blocks per slice pair
-  int group;        // g: pairs (p, g - p)
-  int slice_cols;   // operand columns between consecutive slices
+  int kblocks;            // k-blocks per output tile (= pairs * kb_per_pair)
+  int kb_per_pair;        // k-blocks per slice pair
+  int slice_cols;         // operand columns between consecutive slices
+  int8_t pa[kMaxPairs];   // A slice of pair i
+  int8_t pb[kMaxPairs];   // B slice of pair i
 };
+
+inline KMap plain_kmap(int kblocks) {
+  KMap km{};
+  km.kblocks = kblocks;
+  km.kb_per_pair = kblocks;
+  km.slice_cols = 0;
+  return km;
+}
 
 struct GemmShared {
   uint64_t full[kStages];
@@ -105,8 +117,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         mbar_arrive_expect_tx(&sh->full[s], kStageBytes);
         const int pair = kb / km.kb_per_pair;
         const int kk = kb - pair * km.kb_per_pair;
-        tma_load_2d(sa, &tmA, &sh->full[s], pair * km.slice_cols + kk * BK, m0);
-        tma_load_2d(sb, &tmB, &sh->full[s], (km.group - pair) * km.slice_cols + kk * BK, n0);
+        tma_load_2d(sa, &tmA, &sh->full[s], km.pa[pair] * km.slice_cols + kk * BK, m0);
+        tma_load_2d(sb, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK, n0);
       }
     }
     if (!ok) {

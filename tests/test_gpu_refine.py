@@ -1,0 +1,147 @@
+"""Mixed-precision path with Newton-Schulz refinement, through the C ABI.
+
+The FP64-accurate tensor-core residual is checked entry by entry against
+exact rational arithmetic (Python fractions) on sampled entries: the error
+must stay below 2^-40 of sum_k |a_ik| |x_kj| (44 bits are kept relative to
+the row and column scales; 4 bits of margin). Refined inverses must meet the
+same gate as the FP64 path, rho <= 1e-12, and the forward-error bound against
+the oracle.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_11103_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def bi(cuda_device):
+    from paper_2305_11103_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2305_11103_gb300 import blockinv
+    blockinv.lib()
+    return blockinv
+
+
+def rho_np(A, X):
+    return np.linalg.norm(A @ X - np.eye(A.shape[0])) / (np.linalg.norm(A) * np.linalg.norm(X))
+
+
+def exact_residual_entries(A, X, idx):
+    out = []
+    for i, j in idx:
+        exact = (1 if i == j else 0) - sum(Fraction(float(a)) * Fraction(float(x)) for a, x in zip(A[i], X[:, j]))
+        out.append(float(exact))
+    return np.array(out)
+
+
+def tc_residual(bi, A, X, slices=0):
+    n = A.shape[0]
+    dA, dX = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
+    E = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    st, rho = bi.blockinv_residual_tc(n, dA.data_ptr(), n, dX.data_ptr(), n, E.data_ptr(), n, slices)
+    assert st == bi.OK
+    return E.cpu().numpy(), rho
+
+
+@pytest.mark.parametrize("n,kind", [(300, "gauss"), (1000, "gauss"), (500, "dd"), (400, "general")])
+def test_tc_residual_exact_on_samples(bi, n, kind):
+    if kind == "gauss":
+        A = inputs.gaussian_shifted(n, 40 + n, sigma=1.5)
+    elif kind == "dd":
+        A = inputs.diag_dominant_uniform(n, 40 + n, shift=n)
+    else:  # no dominant diagonal: N(0, 1) entries
+        A = inputs.rng(40 + n).standard_normal((n, n))
+    g = inputs.rng(41 + n)
+    X = np.linalg.inv(A) * (1 + 1e-7 * g.standard_normal((n, n)))
+    idx = [(int(i), int(j)) for i, j in zip(g.integers(0, n, 40), g.integers(0, n, 40))] + [(k, k) for k in range(5)]
+    exact = exact_residual_entries(A, X, idx)
+    scale = np.array([np.abs(A[i]) @ np.abs(X[:, j]) for i, j in idx])
+    errs = []
+    for S in (10, 11, 12, 13):
+        E, rho = tc_residual(bi, A, X, S)
+        got = np.array([E[i, j] for i, j in idx])
+        errs.append(np.max(np.abs(got - exact) / scale))
+    # the default (12 digits) keeps 2^-44 of |A| |X| on every sampled entry
+    assert errs[2] <= 2.0 ** -44, errs
+    # more digits never hurt, and the error keeps falling until the FP64 floor
+    assert errs[3] <= errs[0] + 1e-17, errs
+    E, rho = tc_residual(bi, A, X)
+    dA, dX = torch.from_numpy(A).cuda(), torch.from_numpy(X).cuda()
+    st, rho64 = bi.blockinv_residual(n, dA.data_ptr(), n, dX.data_ptr(), n)
+    assert abs(rho - rho64) <= 1e-3 * rho64
+
+
+def refine(bi, A, sizes, mode, **kw):
+    n = A.shape[0]
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, mode, None, **kw)
+    return st, info, d.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,sizes,kind", [
+    (256, [64] * 4, "dd"),
+    (1024, [256] * 4, "gauss"),
+    (777, [256, 256, 265], "gauss"),
+    (1500, [200] * 7 + [100], "dd"),
+])
+def test_refined_mixed_meets_gate(bi, mode, n, sizes, kind):
+    A = inputs.diag_dominant_uniform(n, n, shift=n) if kind == "dd" else inputs.gaussian_shifted(n, 2 + n, sigma=1.5)
+    st, info, X = refine(bi, A, sizes, mode)
+    assert st == bi.OK, (bi.blockinv_status_str(st), info.as_dict())
+    assert info.used_fallback == 0
+    assert 0 <= info.rho <= 1e-12 and info.rho_initial > info.rho
+    r = rho_np(A, X)
+    assert r <= 1e-12
+    Xo = oracle.block_inverse(A, sizes)
+    kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
+    # the GPU's own rho agrees with the one measured here
+    assert abs(info.rho - r) <= 0.05 * r + 1e-16
+
+
+def test_poorly_conditioned_sigma_105(bi):
+    """N(0,1)/sqrt(n) + 1.05 I: the smallest singular values approach 0.05."""
+    n = 1024
+    A = inputs.gaussian_shifted(n, 4, sigma=1.05)
+    st, info, X = refine(bi, A, [256] * 4, "tf32")
+    assert st == bi.OK
+    assert rho_np(A, X) <= 1e-12
+
+
+def test_not_converged_then_fallback(bi):
+    n = 512
+    A = inputs.gaussian_shifted(n, 9, sigma=1.5)
+    # one update cannot reach 1e-30: NOT_CONVERGED without fallback ...
+    st, info, _ = refine(bi, A, [128] * 4, "bf16", tol=1e-30, max_refine=1, fallback=0)
+    assert st == bi.ERR_NOT_CONVERGED and info.used_fallback == 0
+    # ... and the FP64 path's result with it
+    st, info, X = refine(bi, A, [128] * 4, "bf16", tol=1e-30, max_refine=1, fallback=1)
+    assert st == bi.OK and info.used_fallback == 1
+    assert rho_np(A, X) <= 1e-12
+
+
+def test_mixed_async_status(bi):
+    n = 384
+    A = inputs.diag_dominant_uniform(n, 3)
+    d = torch.from_numpy(A).cuda()
+    status = torch.full((2,), 5, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    assert bi.blockinv_invert_async(n, [128] * 3, d.data_ptr(), n, "tf32", s, status.data_ptr()) == bi.OK
+    s.synchronize()
+    assert status.tolist()[0] == 0
+    assert rho_np(A, d.cpu().numpy()) <= 1e-12
+
+
+def test_mixed_singular_reported(bi):
+    J = np.fliplr(np.eye(8)).copy()
+    st, info, _ = refine(bi, J, [4, 4], "tf32")
+    assert st == bi.ERR_SINGULAR and info.failing_block == 0

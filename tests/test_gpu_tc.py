@@ -122,3 +122,34 @@ def test_mixed_tf32_unimodular_exact(bi):
     assert np.abs(Xo).max() < 2 ** 10
     X = mixed_unrefined(bi, A, sizes, "tf32")
     assert np.array_equal(X, Xo)
+
+
+# ---------------------------------------------- accumulator exactness ------
+# The split-operand residual adds many exact integer products per output in
+# the FP32 accumulator and needs every partial sum below 2^24 to stay exact.
+# Rows carry large equal products plus one small odd term at a row-dependent
+# position, with alternating signs, so that any truncation of low bits during
+# accumulation changes the result.
+@pytest.mark.parametrize("kind,big_a,big_b,K", [
+    (2, 16.0, 8.0, 4096),     # E4M3: products 2^7, sums near 2^19
+    (2, 16.0, 8.0, 16384),    # sums near 2^21
+    (2, 16.0, 16.0, 16384),   # sums near 2^22
+    (0, 128.0, 64.0, 1024),   # BF16: products 2^13, sums near 2^23
+    (1, 1024.0, 512.0, 32),   # TF32: products 2^19, sums near 2^24
+])
+def test_accumulator_exact_near_2_24(bi, kind, big_a, big_b, K):
+    M, N = 128, 256
+    A = np.full((M, K), big_a)
+    B = np.full((N, K), big_b)
+    A[np.arange(M), (np.arange(M) * 37) % K] = 1.0
+    B[np.arange(N), (np.arange(N) * 101 + 5) % K] = 1.0
+    A[1::2] *= -1.0
+    B[:, 1::3] *= -1.0
+    expect = A.astype(np.int64) @ B.astype(np.int64).T
+    assert np.abs(expect).max() < 2 ** 24
+    dt = {2: torch.float8_e4m3fn, 0: torch.bfloat16, 1: torch.float32}[kind]
+    tA = torch.from_numpy(A).float().to(dt).cuda()
+    tB = torch.from_numpy(B).float().to(dt).cuda()
+    C = run_gemm(bi, kind, tA, tB).cpu().numpy().astype(np.int64)
+    bad = np.count_nonzero(C != expect)
+    assert bad == 0, f"{bad} inexact outputs; max error {np.abs(C - expect).max()}"
