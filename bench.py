@@ -36,6 +36,21 @@ RHO_GATE = 1e-12
 # FP64 ALU peak from unit counts: 2 DFMA/clock/SM x 2 flop x 152 SMs x 2.07 GHz.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
+
+def measured_peaks():
+    """HBM and dense BF16 peaks measured by the driver on this pool's GB300s;
+    FP8 and TF32 from BF16 by the nominal ratios (4.5 / 2.25 and 1.1 / 2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        src = "measured"
+    except OSError:
+        m = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+        src = "fallback"
+    bf = m["bf16_tflops"]
+    return {"hbm_gbs": m["hbm_gbs"], "bf16": bf, "fp8": bf * 2.0, "tf32": bf * 1.1 / 2.25,
+            "bf16_sustained": m.get("bf16_tflops_sustained", bf), "source": src}
+
 WORKLOADS = {
     "f64_8192": dict(n=8192, block=256, sigma=1.5, seed=2, mode="f64",
                      desc="8192x8192 FP64, 32x32 grid of 256x256 blocks, N(0,1)/sqrt(n)+1.5I, seed 2, plain FP64 GPU path"),
@@ -67,6 +82,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="f64_8192")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision + refinement legs")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="measure library GEMM rates (FP64, FP32, TF32, BF16, FP16, FP8, INT8) and exit")
     return ap.parse_args()
@@ -246,6 +262,69 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
+def percentiles(xs):
+    ys = sorted(xs)
+    pick = lambda q: ys[min(len(ys) - 1, int(round(q * (len(ys) - 1))))]
+    return {"p50": pick(0.5), "p99": pick(0.99), "min": ys[0], "max": ys[-1]}
+
+
+def run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms):
+    """The same matrix through the mixed-precision elimination (TF32 or BF16
+    Schur updates on tensor cores) and Newton-Schulz refinement to
+    rho <= 1e-12 with the FP64-accurate FP8 residual."""
+    peaks = measured_peaks()
+    out = {}
+    for mode in ("tf32", "bf16"):
+        def step():
+            dX.copy_(dA)
+            st, info = bi.blockinv_invert_ex(n, sizes, dX.data_ptr(), n, mode, stream, tol=RHO_GATE)
+            if st != bi.OK:
+                raise bi.BlockinvError(st, info.failing_block, f"blockinv_invert_ex({mode})")
+            return info
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        bi.blockinv_trace_enable(True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        infos = []
+        for k in range(args.steps):
+            infos.append(step())
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+        bi.blockinv_trace_enable(False)
+        trace = bi.blockinv_trace_summary()
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+        ms = sum(per) / len(per)
+        rho64 = bi.residual(dA, dX)
+        info = infos[-1]
+        g = trace.get("residual_group_gemm_e4m3", {"ms": 0, "flops": 0, "launches": 0})
+        schur = trace.get(f"schur_update_{mode}_tc", {"ms": 0, "bytes": 0, "launches": 0})
+        kt_total = sum(v["ms"] for v in trace.values())
+        achieved_g = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] else None
+        achieved_s = schur["bytes"] / (schur["ms"] / 1e3) / 1e9 if schur["ms"] else None
+        out[mode] = {
+            "ms_per_step": ms, "value": 2.0 * n ** 3 / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+            "inverses_per_s": 1e3 / ms, "speedup_vs_fp64_path": fp64_ms / ms,
+            "latency_ms": percentiles(per),
+            "rho_refinement": info.rho, "rho_initial": info.rho_initial, "rho_fp64_check": rho64,
+            "refine_iters": info.refine_iters, "used_fallback": info.used_fallback,
+            "roofline": {
+                "bound": "tensor", "kernel": "residual_group_gemm_e4m3", "achieved": achieved_g,
+                "peak": peaks["fp8"], "unit": "TFLOP/s",
+                "frac": achieved_g / peaks["fp8"] if achieved_g else None,
+                "peak_source": f"BF16 dense {peaks['source']} x 2 (FP8 / BF16 nominal ratio)",
+                "share_of_kernel_time": g["ms"] / kt_total if kt_total else None},
+            "roofline_schur_update": {
+                "bound": "hbm", "kernel": f"schur_update_{mode}_tc", "achieved": achieved_s,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved_s / peaks["hbm_gbs"] if achieved_s else None},
+            "gpu_launches_per_step": sum(v["launches"] for v in trace.values()) / args.steps,
+            "kernels": trace,
+        }
+    return out
+
+
 # ----------------------------------------------------------- our arm -------
 def run_ours(args):
     import numpy as np
@@ -281,19 +360,22 @@ def run_ours(args):
     bi.blockinv_trace_enable(True)
     torch.cuda.synchronize()
     barrier(world)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
         step()
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    e0, e1 = evs[0], evs[-1]
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    lat = percentiles(per_step)
     barrier(world)
     bi.blockinv_trace_enable(False)
     clk = clocks.stop()
     trace = bi.blockinv_trace_summary()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world)
+    fp64_ms = ms
     flops = 2.0 * n ** 3
     value = world * flops / (ms / 1e3) / 1e12
     rho = bi.residual(dA, dX)
@@ -337,6 +419,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
 
+    mixed = {} if args.no_mixed else run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
@@ -347,6 +431,8 @@ def run_ours(args):
             "inverses_per_s": world * 1e3 / ms, "rho": rho, "rho_gate": RHO_GATE,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches, "kernels": trace,
+            "latency_ms": lat,
+            "mixed": mixed,
         }
         print(json.dumps(out))
     if world > 1:

@@ -202,7 +202,7 @@ struct MixedState {
 };
 
 int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* status, cudaStream_t s,
-                  const Options& opt, MixedState& ms) {
+                  const Options& opt, MixedState& ms, bool host_steps) {
   const int n = pl.n;
   ms.max_refine = opt.max_refine;
   const size_t row = sizeof(double) * (size_t)n;
@@ -220,7 +220,7 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
   if (e != cudaSuccess) return cuda_status(e);
   e = enqueue_refine(ms.A0(), n, A, lda, n, opt.tol, opt.max_refine, kResidualSlices, ms.ws.ptr,
                      static_cast<double*>(ms.hist.ptr), static_cast<int32_t*>(ms.ctl.ptr), status, nullptr, 0, s,
-                     true);
+                     true, host_steps);
   return cuda_status(e);
 }
 
@@ -232,7 +232,8 @@ int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, c
     case BLOCKINV_MIXED_TF32:
     case BLOCKINV_MIXED_BF16: {
       MixedState local;
-      return enqueue_mixed(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s, opt, ms ? *ms : local);
+      return enqueue_mixed(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s, opt, ms ? *ms : local,
+                           ms != nullptr);
     }
     default:
       return BLOCKINV_ERR_INVALID;
@@ -419,7 +420,7 @@ int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* 
   if (e == cudaSuccess)
     e = enqueue_refine(A, lda, const_cast<double*>(X), ldx, (int)n, 0.0, 0, slices, ws.ptr,
                        static_cast<double*>(hist.ptr), static_cast<int32_t*>(ctl.ptr),
-                       static_cast<int32_t*>(sbuf.ptr), E, lde, s, false);
+                       static_cast<int32_t*>(sbuf.ptr), E, lde, s, false, false);
   double rho = -1.0;
   int32_t st[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&rho, hist.ptr, sizeof(double), cudaMemcpyDeviceToHost, s);

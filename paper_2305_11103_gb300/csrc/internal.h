@@ -90,6 +90,6 @@ constexpr int kResidualSlices = 12;
 size_t refine_workspace_bytes(int n, int S, int max_updates);
 cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
-                           double* Eout, int64_t lde, cudaStream_t s, bool report);
+                           double* Eout, int64_t lde, cudaStream_t s, bool report, bool host_steps);
 
 }  // namespace blockinv

@@ -438,10 +438,13 @@ size_t refine_workspace_bytes(int n, int S, int max_updates) {
 // (device, 4 int32: done, updates, code, last) the outcome. If Eout is
 // non-null and max_updates == 0, the residual E = I - A0 X is written there.
 // With `report`, a refinement that stops short of tol sets the status word to
-// BLOCKINV_ERR_NOT_CONVERGED.
+// BLOCKINV_ERR_NOT_CONVERGED. With `host_steps` the host waits for each
+// decision and enqueues no further iteration once the device is done (for
+// blocking callers); otherwise every iteration is enqueued and the kernels of
+// iterations past the decision return at once (stream-ordered, capturable).
 cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
-                           double* Eout, int64_t lde, cudaStream_t s, bool report) {
+                           double* Eout, int64_t lde, cudaStream_t s, bool report, bool host_steps) {
   if (S < 9 || S > 13 || n < 1) return cudaErrorInvalidValue;
   Ctl* ctl = reinterpret_cast<Ctl*>(ctl_words);
   const int Kp = (n + 127) / 128 * 128;
@@ -512,6 +515,14 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     }
     decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status);
     if (it == max_updates) break;
+    if (host_steps) {
+      // Blocking callers stop enqueueing as soon as the device has decided.
+      int32_t h[2] = {0, 0};
+      e = cudaMemcpyAsync(h, ctl_words, sizeof(h), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess || h[0] != 0 || h[1] != 0) break;
+    }
     {
       TraceScope t("ns_split_x", 0, 16.0 * nd * nd, s);
       split_x_kernel<<<8 * tc::num_sms(), 256, 0, s>>>(X, ldx, n, Xop, Kp, ctl, status);
