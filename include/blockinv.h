@@ -106,6 +106,27 @@ int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, doub
 int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
                          int64_t lda, int mode, void* stream);
 
+/* FP64 in-place inversion that allocates no device memory (the paper has no
+ * counterpart: this is a deployment variant of blockinv_invert, mode
+ * BLOCKINV_F64). For callers that cannot call cudaMalloc or any other
+ * allocator - for example code that runs inside a memory-pool callback, or a
+ * plugin whose host application owns every allocation. The scratch the
+ * kernels need lives in a fixed file-scope device array (about 4.5 MiB on
+ * every GPU that loads the library, kept until the process exits).
+ *  n, p, block_sizes, A, lda as for blockinv_invert, with n <= 2048, every
+ *               block order <= 256, and an explicit partition (p >= 1);
+ *               larger sizes return BLOCKINV_ERR_INVALID with A untouched.
+ *  stream       cudaStream_t or NULL; the call synchronises it.
+ *  failing_block (host, may be NULL) receives the failing block index for
+ *               SINGULAR / NONFINITE, else -1.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one scratch array: calls whose GPU work overlaps on
+ * the same device (other streams or host threads) race and must be
+ * serialised by the caller. */
+int blockinv_invert_noalloc(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
+                            void* stream, int64_t* failing_block);
+
 /* Options and per-call report for blockinv_invert_ex. */
 typedef struct {
   double tol;          /* refinement target for rho (mixed modes); <= 0 means 1e-12     */

@@ -31,6 +31,7 @@ SIGNATURES = {
     "blockinv_invert": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
     "blockinv_invert_async": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp]),
     "blockinv_invert_host": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
+    "blockinv_invert_noalloc": (_int, [_i64, _i32, _i32p, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "blockinv_residual_tc": (_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(ctypes.c_double),
                                      _vp]),
@@ -126,6 +127,15 @@ def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.
 
 def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None):
     return lib().blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, _stream_ptr(stream))
+
+
+def blockinv_invert_noalloc(n, block_sizes, A_ptr, lda, stream=None):
+    """FP64 inversion without device allocation (n <= 2048, blocks <= 256).
+    Returns (status, failing_block)."""
+    p, arr, _ = _sizes(block_sizes)
+    fb = ctypes.c_int64(-1)
+    st = lib().blockinv_invert_noalloc(n, p, arr, A_ptr, lda, _stream_ptr(stream), ctypes.byref(fb))
+    return st, fb.value
 
 
 def blockinv_invert_host(n, block_sizes, A_host_ptr, lda, mode=F64, stream=None):
