@@ -127,6 +127,51 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
 int blockinv_invert_noalloc(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
                             void* stream, int64_t* failing_block);
 
+/* Batched inversion of `count` small FP64 matrices of one order n (1..8), in
+ * place: the paper's repeated small inversions (Sec. 2, systematics matrices
+ * of order 5), each matrix partitioned by the paper's rule (Sec. 5.1, Table 2:
+ * 5 -> [2, 3], 8 -> [2, 2, 2, 2]) and inverted by Eq. (a) block by block with
+ * closed-form pivot-block inverses (the "algebraic expressions" for orders
+ * 2..4). A: device, count matrices of n * n doubles each, row-major,
+ * contiguous (matrix m starts at A + m * n * n). status_dev: device int32
+ * per matrix (may be NULL): 0, BLOCKINV_ERR_SINGULAR (a pivot block with a
+ * zero determinant) or BLOCKINV_ERR_NONFINITE; a failed matrix is left
+ * unchanged. Stream-ordered: returns after enqueueing; argument errors are
+ * returned at once. */
+int blockinv_invert_batched_small(int64_t count, int32_t n, double* A, int32_t* status_dev, void* stream);
+
+/* Batched inversion of `count` independent FP64 matrices of uneven orders,
+ * each in place (the paper's method applied to every matrix; matrices do not
+ * interact). For each elimination step k, the pivot inverses, row panels and
+ * Schur updates of all matrices run as one grouped launch each.
+ *  n            host int32[count]: orders.
+ *  p            host int32[count]: blocks per matrix (ignored if block_sizes
+ *               is NULL).
+ *  block_sizes  host int32, the partitions concatenated, or NULL for the
+ *               default: the paper's Table 2 rule below order 8, else four
+ *               blocks of floor(n/4) (more when that exceeds 128), the last
+ *               blocks taking the remainder. Every block order <= 512.
+ *  A            host array of `count` device pointers; lda host int64[count].
+ *  mode         BLOCKINV_F64 (other modes return BLOCKINV_ERR_INVALID).
+ *  status_dev   device int32[count] (may be NULL): per-matrix BLOCKINV_OK,
+ *               SINGULAR or NONFINITE.
+ * Blocking (synchronises stream). Argument errors return at once. */
+int blockinv_invert_batched(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
+                            double* const* A, const int64_t* lda, int mode, void* stream, int32_t* status_dev);
+
+/* Reusable batch plan: validates the partitions and allocates the descriptor
+ * tables and workspace once (the plan owns that device memory until
+ * destroyed); the matrices' pointers are fixed in the plan. The first run
+ * captures the launch sequence in a CUDA graph; every run replays it on
+ * `stream` (stream-ordered, no synchronisation) and, if status_dev is not
+ * NULL, writes the per-matrix status there. A plan must not be run on two
+ * streams at the same time. */
+typedef struct blockinv_batch_plan blockinv_batch_plan;
+int blockinv_batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
+                               double* const* A, const int64_t* lda, blockinv_batch_plan** plan);
+int blockinv_batch_plan_run(blockinv_batch_plan* plan, void* stream, int32_t* status_dev);
+int blockinv_batch_plan_destroy(blockinv_batch_plan* plan);
+
 /* Options and per-call report for blockinv_invert_ex. */
 typedef struct {
   double tol;          /* refinement target for rho (mixed modes); <= 0 means 1e-12     */

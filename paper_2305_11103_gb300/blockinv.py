@@ -31,6 +31,13 @@ SIGNATURES = {
     "blockinv_invert": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
     "blockinv_invert_async": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp]),
     "blockinv_invert_host": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
+    "blockinv_invert_batched_small": (_int, [_i64, _i32, _vp, _vp, _vp]),
+    "blockinv_invert_batched": (_int, [_i32, _i32p, _i32p, _i32p, _vp, ctypes.POINTER(ctypes.c_int64), _int, _vp,
+                                        _vp]),
+    "blockinv_batch_plan_create": (_int, [_i32, _i32p, _i32p, _i32p, _vp, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "blockinv_batch_plan_run": (_int, [_vp, _vp, _vp]),
+    "blockinv_batch_plan_destroy": (_int, [_vp]),
     "blockinv_invert_noalloc": (_int, [_i64, _i32, _i32p, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "blockinv_residual_tc": (_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(ctypes.c_double),
@@ -127,6 +134,55 @@ def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.
 
 def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None):
     return lib().blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, _stream_ptr(stream))
+
+
+def blockinv_invert_batched_small(count, n, A_ptr, status_ptr=None, stream=None):
+    return lib().blockinv_invert_batched_small(count, n, A_ptr, status_ptr, _stream_ptr(stream))
+
+
+def _batch_args(ns, partitions, A_ptrs, ldas):
+    count = len(ns)
+    n_arr = (ctypes.c_int32 * count)(*ns)
+    if partitions is None:
+        p_arr, s_arr = None, None
+    else:
+        p_arr = (ctypes.c_int32 * count)(*[len(q) for q in partitions])
+        flat = [int(v) for q in partitions for v in q]
+        s_arr = (ctypes.c_int32 * len(flat))(*flat)
+    a_arr = (ctypes.c_void_p * count)(*A_ptrs)
+    l_arr = (ctypes.c_int64 * count)(*ldas)
+    return count, n_arr, p_arr, s_arr, a_arr, l_arr
+
+
+def blockinv_invert_batched(ns, partitions, A_ptrs, ldas, mode=F64, stream=None, status_ptr=None):
+    count, n_arr, p_arr, s_arr, a_arr, l_arr = _batch_args(ns, partitions, A_ptrs, ldas)
+    return lib().blockinv_invert_batched(count, n_arr, p_arr, s_arr, a_arr, l_arr, _mode(mode),
+                                         _stream_ptr(stream), status_ptr)
+
+
+class BatchPlan:
+    """A reusable batch plan (graph-replayed grouped launches)."""
+
+    def __init__(self, ns, partitions, A_ptrs, ldas):
+        count, n_arr, p_arr, s_arr, a_arr, l_arr = _batch_args(ns, partitions, A_ptrs, ldas)
+        self.handle = ctypes.c_void_p()
+        st = lib().blockinv_batch_plan_create(count, n_arr, p_arr, s_arr, a_arr, l_arr, ctypes.byref(self.handle))
+        if st != OK:
+            raise BlockinvError(st, -1, "blockinv_batch_plan_create")
+
+    def run(self, stream=None, status_ptr=None):
+        return lib().blockinv_batch_plan_run(self.handle, _stream_ptr(stream), status_ptr)
+
+    def close(self):
+        if self.handle:
+            lib().blockinv_batch_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def blockinv_invert_noalloc(n, block_sizes, A_ptr, lda, stream=None):

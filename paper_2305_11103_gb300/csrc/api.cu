@@ -431,6 +431,20 @@ int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* 
   return record(st[0], -1);
 }
 
+int blockinv_invert_batched_small(int64_t count, int32_t n, double* A, int32_t* status_dev, void* stream) {
+  if (count < 0 || n < 1 || n > 8 || (count > 0 && !A) || count > ((int64_t)1 << 31) * 64)
+    return record(BLOCKINV_ERR_INVALID, -1);
+  if (count == 0) return record(BLOCKINV_OK, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  {
+    const double nd = n;
+    TraceScope t("small_batched_f64", 2.0 * nd * nd * nd * (double)count, 16.0 * nd * nd * (double)count, s);
+    e = launch_small_batched(n, A, count, status_dev, s);
+  }
+  return record(cuda_status(e), -1);
+}
+
 const char* blockinv_status_str(int status) {
   switch (status) {
     case BLOCKINV_OK: return "ok";

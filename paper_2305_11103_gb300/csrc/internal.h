@@ -53,6 +53,25 @@ struct PivotPlan {
 
 bool plan_pivot(int b, int elem_bytes, PivotPlan* plan);
 
+// One matrix's elimination step k in a grouped (batched) launch.
+struct GroupStep {
+  double* X;       // matrix (device), row-major
+  int64_t ldx;
+  int n, o, b, k;  // order, pivot offset, pivot order, step index
+  double* Pinv;    // b x b workspace
+  double* U;       // n x b workspace
+  int32_t* status; // this matrix's status word pair
+};
+// Largest pivot order of the grouped (one CTA per matrix) pivot kernel.
+constexpr int kGroupedMaxB = 128;
+cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s);
+// Grouped K2 / K3 over `count` items; col_start / tile_start are exclusive
+// prefix sums (count + 1 entries) of each item's column strips / 64 x 64 tiles.
+cudaError_t launch_row_panel_grouped(const GroupStep* items, int count, const int32_t* col_start,
+                                     int total_cols, int bmax, cudaStream_t s);
+cudaError_t launch_schur_update_grouped(const GroupStep* items, int count, const int32_t* tile_start,
+                                        int total_tiles, cudaStream_t s);
+
 // K1: P^-1 of the b x b pivot block at P (leading dimension ldp) into Pinv
 // (leading dimension ldo). T = double (FP64 path) or float (mixed path).
 template <typename T>
@@ -84,6 +103,9 @@ int mixed_kpad(int bmax);
 // 2 (BF16) bytes per element.
 cudaError_t mixed_elimination(const Plan& pl, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, int32_t* status, cudaStream_t s);
+
+// Batched small matrices, order 1..8, one thread per matrix (k_small.cu).
+cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* status, cudaStream_t s);
 
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
 constexpr int kResidualSlices = 12;

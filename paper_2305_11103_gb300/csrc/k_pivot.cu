@@ -68,9 +68,9 @@ __device__ __forceinline__ void argmax_step(T& bv, int& bi, T ov, int oi) {
 }
 
 template <typename T, bool kCluster>
-__global__ void __launch_bounds__(kPivotThreads)
-pivot_gj_kernel(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog,
-                T* __restrict__ out, int64_t ldo, int32_t* status, int block_index) {
+__device__ __forceinline__ void pivot_gj_body(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog,
+                                              T* __restrict__ out, int64_t ldo, int32_t* status,
+                                              int block_index) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rows = reinterpret_cast<T*>(smem_raw);   // R x b, this CTA's rows
   T* prow = rows + (size_t)R * b;             // b: scaled pivot row
@@ -209,6 +209,30 @@ pivot_gj_kernel(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog,
   }
 }
 
+template <typename T, bool kCluster>
+__global__ void __launch_bounds__(kPivotThreads)
+pivot_gj_kernel(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog, T* __restrict__ out, int64_t ldo,
+                int32_t* status, int block_index) {
+  pivot_gj_body<T, kCluster>(P, ldp, b, R, jlog, out, ldo, status, block_index);
+}
+
+// Grouped form: one CTA per matrix of a batch, block order <= kGroupedMaxB,
+// every row of the pivot block in the CTA's shared memory.
+__global__ void __launch_bounds__(kPivotThreads)
+pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count) {
+  const int m = blockIdx.x;
+  if (m >= count) return;
+  const GroupStep it = items[m];
+  if (it.b > kGroupedMaxB) return;  // handled by the cluster kernel
+  int jw = 1, jlog = 0;
+  while (jw < it.b && jw < kPivotThreads) {
+    jw <<= 1;
+    ++jlog;
+  }
+  pivot_gj_body<double, false>(it.X + (int64_t)it.o * it.ldx + it.o, it.ldx, it.b, it.b, jlog, it.Pinv, it.b,
+                               it.status, it.k);
+}
+
 size_t pivot_smem_bytes(int b, int R, int elem) {
   size_t t = (size_t)R * b + b + R + 2;            // T arrays
   size_t i = 2 + (size_t)R + b + 1;                // int arrays
@@ -283,6 +307,17 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
   if (e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, pivot_gj_kernel<T, false>, P, ldp, b, plan.rows, jlog, Pinv, ldo,
                             status, block_index);
+}
+
+cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (bmax > kGroupedMaxB) return cudaErrorInvalidValue;
+  const size_t smem = pivot_smem_bytes(bmax, bmax, sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(pivot_gj_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  pivot_gj_grouped_kernel<<<count, kPivotThreads, smem, s>>>(items, count);
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_pivot_inverse<double>(const double*, int64_t, int, double*, int64_t,

@@ -32,31 +32,16 @@ __device__ __forceinline__ bool failed(const int32_t* status) {
 constexpr int kPanelCols = 32;
 constexpr int kPanelK = 8;
 
+// Row panel for the 32-column strip starting at j0 (all b rows of block k).
 template <int MAXB>
-__global__ void __launch_bounds__(256)
-row_panel_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
-                     const double* __restrict__ Pinv, double* __restrict__ U,
-                     const int32_t* status, int col_tiles) {
-  if (failed(status)) return;
-  const int tid = threadIdx.x;
-  if ((int)blockIdx.x >= col_tiles) {
-    // Copy block column k, rows outside block k, into U (n x b, ld b).
-    const int64_t total = (int64_t)n * b;
-    const int64_t stride = (int64_t)(gridDim.x - col_tiles) * blockDim.x;
-    for (int64_t e = (int64_t)(blockIdx.x - col_tiles) * blockDim.x + tid; e < total; e += stride) {
-      const int i = (int)(e / b);
-      const int l = (int)(e - (int64_t)i * b);
-      if (i >= o && i < o + b) continue;
-      U[e] = X[(int64_t)i * ldx + o + l];
-    }
-    return;
-  }
+__device__ __forceinline__ void row_panel_strip(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                                                const double* __restrict__ Pinv, int j0) {
   constexpr int RPT = MAXB / 8;  // rows per thread
   __shared__ double Ps[kPanelK][MAXB];
   __shared__ double Xs[kPanelK][kPanelCols];
+  const int tid = threadIdx.x;
   const int c = tid & 31;
   const int g = tid >> 5;
-  const int j0 = blockIdx.x * kPanelCols;
   const int j = j0 + c;
   double acc[RPT];
 #pragma unroll
@@ -91,17 +76,67 @@ row_panel_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
   }
 }
 
+// Copy block column k (rows [r0, r1) outside block k) into U (n x b, ld b).
+__device__ __forceinline__ void copy_column_panel(const double* __restrict__ X, int64_t ldx, int o, int b,
+                                                  double* __restrict__ U, int r0, int r1, int part,
+                                                  int nparts) {
+  const int64_t total = (int64_t)(r1 - r0) * b;
+  for (int64_t e = (int64_t)part * blockDim.x + threadIdx.x; e < total; e += (int64_t)nparts * blockDim.x) {
+    const int i = r0 + (int)(e / b);
+    const int l = (int)(e - (int64_t)(i - r0) * b);
+    if (i >= o && i < o + b) continue;
+    U[(int64_t)i * b + l] = X[(int64_t)i * ldx + o + l];
+  }
+}
+
+// One CTA per 32-column strip of row panel k (all b rows), so the strip can
+// be read completely before it is overwritten in place. Thread (g, c) holds
+// rows g, g + 8, g + 16, ... of column c. Extra CTAs copy the column panel.
+template <int MAXB>
+__global__ void __launch_bounds__(256)
+row_panel_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                     const double* __restrict__ Pinv, double* __restrict__ U,
+                     const int32_t* status, int col_tiles) {
+  if (failed(status)) return;
+  if ((int)blockIdx.x >= col_tiles) {
+    copy_column_panel(X, ldx, o, b, U, 0, n, blockIdx.x - col_tiles, gridDim.x - col_tiles);
+    return;
+  }
+  row_panel_strip<MAXB>(X, ldx, n, o, b, Pinv, blockIdx.x * kPanelCols);
+}
+
+__device__ __forceinline__ int find_item(const int32_t* __restrict__ start, int count, int t) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grouped row panel: strip t of the batch belongs to item m; the same CTA
+// also copies its share of item m's column panel.
+template <int MAXB>
+__global__ void __launch_bounds__(256)
+row_panel_grouped_kernel(const GroupStep* __restrict__ items, int count, const int32_t* __restrict__ col_start) {
+  const int t = blockIdx.x;
+  const int m = find_item(col_start, count, t);
+  const GroupStep it = items[m];
+  if (failed(it.status)) return;
+  const int strips = col_start[m + 1] - col_start[m];
+  const int s = t - col_start[m];
+  const int rows_per = (it.n + strips - 1) / strips;
+  const int r0 = min(it.n, s * rows_per), r1 = min(it.n, r0 + rows_per);
+  copy_column_panel(it.X, it.ldx, it.o, it.b, it.U, r0, r1, 0, 1);
+  row_panel_strip<MAXB>(it.X, it.ldx, it.n, it.o, it.b, it.Pinv, s * kPanelCols);
+}
+
 // ---------------------------------------------------------------- K3 ------
 constexpr int kTile = 64;
 constexpr int kTileK = 8;
 
-__global__ void __launch_bounds__(256)
-schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
-                        const double* __restrict__ U, const int32_t* status) {
-  const int i0 = blockIdx.y * kTile;
-  const int j0 = blockIdx.x * kTile;
-  if (i0 >= o && i0 + kTile <= o + b) return;  // tile lies inside the pivot rows
-  if (failed(status)) return;
+__device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                                           const double* __restrict__ U, int i0, int j0) {
   __shared__ __align__(16) double Us[kTileK][kTile];
   __shared__ __align__(16) double Vs[kTileK][kTile];
   const int tid = threadIdx.x;
@@ -154,6 +189,31 @@ schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b
       row[j] = base - acc[a][d];
     }
   }
+}
+
+__global__ void __launch_bounds__(256)
+schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b,
+                        const double* __restrict__ U, const int32_t* status) {
+  const int i0 = blockIdx.y * kTile;
+  const int j0 = blockIdx.x * kTile;
+  if (i0 >= o && i0 + kTile <= o + b) return;  // tile lies inside the pivot rows
+  if (failed(status)) return;
+  schur_tile(X, ldx, n, o, b, U, i0, j0);
+}
+
+// Grouped Schur update: tile t of the batch belongs to item m.
+__global__ void __launch_bounds__(256)
+schur_update_grouped_kernel(const GroupStep* __restrict__ items, int count, const int32_t* __restrict__ tile_start) {
+  const int t = blockIdx.x;
+  const int m = find_item(tile_start, count, t);
+  const GroupStep it = items[m];
+  const int tiles_row = (it.n + kTile - 1) / kTile;
+  const int local = t - tile_start[m];
+  const int i0 = (local / tiles_row) * kTile;
+  const int j0 = (local % tiles_row) * kTile;
+  if (i0 >= it.o && i0 + kTile <= it.o + it.b) return;
+  if (failed(it.status)) return;
+  schur_tile(it.X, it.ldx, it.n, it.o, it.b, it.U, i0, j0);
 }
 
 // --------------------------------------------------------- residual -------
@@ -262,6 +322,29 @@ cudaError_t launch_schur_update_f64(double* X, int64_t ldx, int n, int o, int b,
   if (n == b) return cudaSuccess;
   const int t = (n + kTile - 1) / kTile;
   schur_update_f64_kernel<<<dim3(t, t), 256, 0, s>>>(X, ldx, n, o, b, U, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_panel_grouped(const GroupStep* items, int count, const int32_t* col_start,
+                                     int total_cols, int bmax, cudaStream_t s) {
+  if (count <= 0 || total_cols <= 0) return cudaSuccess;
+  if (bmax <= 64)
+    row_panel_grouped_kernel<64><<<total_cols, 256, 0, s>>>(items, count, col_start);
+  else if (bmax <= 128)
+    row_panel_grouped_kernel<128><<<total_cols, 256, 0, s>>>(items, count, col_start);
+  else if (bmax <= 256)
+    row_panel_grouped_kernel<256><<<total_cols, 256, 0, s>>>(items, count, col_start);
+  else if (bmax <= 512)
+    row_panel_grouped_kernel<512><<<total_cols, 256, 0, s>>>(items, count, col_start);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schur_update_grouped(const GroupStep* items, int count, const int32_t* tile_start,
+                                        int total_tiles, cudaStream_t s) {
+  if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+  schur_update_grouped_kernel<<<total_tiles, 256, 0, s>>>(items, count, tile_start);
   return cudaGetLastError();
 }
 

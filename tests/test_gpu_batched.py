@@ -1,0 +1,186 @@
+"""Batched small-matrix inversion (orders 1..8, one thread per matrix) through
+the C ABI, against the oracle with the same partition (the paper's Table 2
+rule) and against the residual gate rho <= 1e-12 per matrix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_11103_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def bi(cuda_device):
+    from paper_2305_11103_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2305_11103_gb300 import blockinv
+    blockinv.lib()
+    return blockinv
+
+
+def batched_rho(A, X):
+    n = A.shape[-1]
+    R = np.einsum("bij,bjk->bik", A, X) - np.eye(n)[None]
+    return np.linalg.norm(R, axis=(1, 2)) / (np.linalg.norm(A, axis=(1, 2)) * np.linalg.norm(X, axis=(1, 2)))
+
+
+def run(bi, A):
+    count, n, _ = A.shape
+    d = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    st = torch.full((count,), 99, dtype=torch.int32, device="cuda")
+    assert bi.blockinv_invert_batched_small(count, n, d.data_ptr(), st.data_ptr(), None) == bi.OK
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), st.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("count", [1, 127, 1000])
+def test_small_orders_vs_oracle(bi, n, count):
+    g = inputs.rng(500 + 10 * n + count)
+    A = g.uniform(-1, 1, size=(count, n, n)) + n * np.eye(n)[None]
+    X, st = run(bi, A)
+    assert np.all(st == 0)
+    sizes = oracle.paper_partition(n) if n >= 2 else [1]
+    assert np.all(batched_rho(A, X) <= 1e-12)
+    for m in range(0, count, max(1, count // 25)):
+        Xo = oracle.block_inverse(A[m], sizes)
+        kappa = np.linalg.norm(A[m]) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X[m] - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
+
+
+def test_spd_5x5_full_batch(bi):
+    """200 000 SPD 5 x 5 matrices B B^T + 0.1 I, B iid N(0, 1), seed 5."""
+    A = inputs.spd_covariance_batch(200_000, 5, 5)
+    X, st = run(bi, A)
+    assert np.all(st == 0)
+    assert np.all(batched_rho(A, X) <= 1e-12)
+    g = inputs.rng(55)
+    for m in g.choice(200_000, size=50, replace=False):
+        Xo = oracle.block_inverse(A[m], [2, 3])
+        kappa = np.linalg.norm(A[m]) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X[m] - Xo) / np.linalg.norm(Xo) <= 4 * 5 * kappa * U64
+    # SPD input: symmetric inverse up to rounding
+    assert np.max(np.abs(X - X.transpose(0, 2, 1)) / np.abs(X).max(axis=(1, 2))[:, None, None]) < 1e-9
+
+
+def test_exact_unimodular_batch(bi):
+    mats = [inputs.unimodular_block_lu([2, 3], 900 + k)[0] for k in range(64)]
+    A = np.stack(mats)
+    X, st = run(bi, A)
+    assert np.all(st == 0)
+    for m in range(64):
+        assert np.array_equal(X[m], oracle.block_inverse(A[m], [2, 3]))
+
+
+def test_per_matrix_status(bi):
+    g = inputs.rng(77)
+    A = g.uniform(-1, 1, size=(300, 5, 5)) + 5 * np.eye(5)[None]
+    A[10] = np.fliplr(np.eye(5))            # leading 2 x 2 block singular
+    A[20, :2, :2] = [[1.0, 2.0], [2.0, 4.0]]  # singular leading block again
+    A[30, 3, 3] = np.nan
+    keep = A.copy()
+    X, st = run(bi, A)
+    assert st[10] == bi.ERR_SINGULAR and st[20] == bi.ERR_SINGULAR and st[30] == bi.ERR_NONFINITE
+    ok = np.ones(300, bool)
+    ok[[10, 20, 30]] = False
+    assert np.all(st[ok] == 0)
+    assert np.array_equal(X[10], keep[10]) and np.array_equal(X[20], keep[20])
+    assert np.all(batched_rho(A[ok], X[ok]) <= 1e-12)
+
+
+def test_argument_errors(bi):
+    assert bi.blockinv_invert_batched_small(10, 9, 0x1000, None, None) == bi.ERR_INVALID
+    assert bi.blockinv_invert_batched_small(10, 0, 0x1000, None, None) == bi.ERR_INVALID
+    assert bi.blockinv_invert_batched_small(0, 5, None, None, None) == bi.OK
+
+
+# ------------------------------------------------- uneven (grouped) batches ---
+def device_batch(mats):
+    ts = [torch.from_numpy(np.ascontiguousarray(A)).cuda() for A in mats]
+    return ts, [t.data_ptr() for t in ts], [t.shape[0] for t in ts]
+
+
+def quarter(n):
+    if n < 8:
+        return oracle.paper_partition(n) if n >= 2 else [1]
+    return oracle.quarter_partition(n)
+
+
+def test_uneven_default_partition_vs_oracle(bi):
+    mats = inputs.uneven_batch(60, 8, 300, 61)
+    ts, ptrs, ns = device_batch(mats)
+    st = torch.full((60,), 7, dtype=torch.int32, device="cuda")
+    assert bi.blockinv_invert_batched(ns, None, ptrs, ns, bi.F64, None, st.data_ptr()) == bi.OK
+    assert torch.all(st == 0)
+    for A, t in zip(mats, ts):
+        X = t.cpu().numpy()
+        n = A.shape[0]
+        Xo = oracle.block_inverse(A, quarter(n))
+        assert np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e-12
+        kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
+
+
+def test_uneven_explicit_partitions_and_large_block(bi):
+    parts = [[3, 4], [100, 157], [1, 1, 1], [200, 200], [64] * 5 + [3], [129]]
+    mats = [inputs.gaussian_shifted(sum(q), 62 + i, sigma=1.5) for i, q in enumerate(parts)]
+    ts, ptrs, ns = device_batch(mats)
+    st = torch.full((len(mats),), 7, dtype=torch.int32, device="cuda")
+    assert bi.blockinv_invert_batched(ns, parts, ptrs, ns, bi.F64, None, st.data_ptr()) == bi.OK
+    assert torch.all(st == 0)
+    for A, t, q in zip(mats, ts, parts):
+        X = t.cpu().numpy()
+        Xo = oracle.block_inverse(A, q)
+        kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * A.shape[0] * kappa * U64
+
+
+def test_uneven_status_and_plan_replay(bi):
+    mats = inputs.uneven_batch(40, 8, 200, 63)
+    mats[5] = np.fliplr(np.eye(mats[5].shape[0])).copy()   # singular leading block
+    ts, ptrs, ns = device_batch(mats)
+    plan = bi.BatchPlan(ns, None, ptrs, ns)
+    st = torch.full((40,), 7, dtype=torch.int32, device="cuda")
+    first = None
+    for rep in range(3):     # the first run captures the graph, the others replay it
+        for A, t in zip(mats, ts):
+            t.copy_(torch.from_numpy(A))
+        assert plan.run(None, st.data_ptr()) == bi.OK
+        torch.cuda.synchronize()
+        assert st[5].item() == bi.ERR_SINGULAR
+        ok = [i for i in range(40) if i != 5]
+        assert all(st[i].item() == 0 for i in ok)
+        res = [ts[i].cpu().numpy() for i in ok]
+        if first is None:
+            first = res
+        else:
+            assert all(np.array_equal(a, b) for a, b in zip(first, res))
+    plan.close()
+
+
+def test_uneven_full_config(bi):
+    """2000 matrices, n = round(exp(U(ln 8, ln 512))), U[-1,1] + n I, seed 6."""
+    mats = inputs.uneven_batch(2000, 8, 512, 6)
+    ts, ptrs, ns = device_batch(mats)
+    st = torch.full((2000,), 7, dtype=torch.int32, device="cuda")
+    assert bi.blockinv_invert_batched(ns, None, ptrs, ns, bi.F64, None, st.data_ptr()) == bi.OK
+    assert torch.all(st == 0)
+    g = inputs.rng(66)
+    for i in g.choice(2000, size=25, replace=False):
+        A, X = mats[i], ts[i].cpu().numpy()
+        n = A.shape[0]
+        assert np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e-12
+        Xo = oracle.block_inverse(A, quarter(n))
+        kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
+
+
+def test_batched_argument_errors(bi):
+    t = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    assert bi.blockinv_invert_batched([8], [[4, 3]], [t.data_ptr()], [8]) == bi.ERR_INVALID
+    assert bi.blockinv_invert_batched([8], None, [t.data_ptr()], [7]) == bi.ERR_INVALID
+    assert bi.blockinv_invert_batched([8], None, [t.data_ptr()], [8], mode="tf32") == bi.ERR_INVALID
