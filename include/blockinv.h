@@ -70,7 +70,8 @@ enum {
   BLOCKINV_ERR_BUDGET = -5,          /* serving: request larger than the HBM budget  */
   BLOCKINV_ERR_NOT_CONVERGED = -6,   /* refinement did not reach the tolerance       */
   BLOCKINV_ERR_TIMEOUT = -7,         /* a bounded device wait gave up                */
-  BLOCKINV_ERR_CUDA = -8             /* a CUDA runtime call failed                   */
+  BLOCKINV_ERR_CUDA = -8,            /* a CUDA runtime call failed                   */
+  BLOCKINV_ERR_CANCELLED = -9        /* serving: request cancelled before it ran     */
 };
 
 /* Largest diagonal block order the GPU pivot-block kernel accepts. */
@@ -171,6 +172,54 @@ int blockinv_batch_plan_create(int32_t count, const int32_t* n, const int32_t* p
                                double* const* A, const int64_t* lda, blockinv_batch_plan** plan);
 int blockinv_batch_plan_run(blockinv_batch_plan* plan, void* stream, int32_t* status_dev);
 int blockinv_batch_plan_destroy(blockinv_batch_plan* plan);
+
+/* ------------------------------------------------------------- serving ---
+ * A serving context inverts independent requests (one matrix each, any
+ * order and mode) as they arrive. A worker thread admits queued requests
+ * first-fit whenever one of `max_slots` slots (CUDA streams) is free and the
+ * request's device footprint fits in what is left of `hbm_budget_bytes`;
+ * admitted requests run concurrently on their slots, and new arrivals join
+ * as slots and memory free up (continuous batching). A request's result does
+ * not depend on the other requests in flight. Not part of the paper's method:
+ * a serving front end for it. */
+typedef struct blockinv_ctx blockinv_ctx;
+
+/* Submit flag: A is host memory (pinned for overlap); the context copies it
+ * in and the inverse back out, counting the device copy in the budget. */
+#define BLOCKINV_SUBMIT_HOST 1
+
+typedef struct {
+  int32_t status;        /* final status of the request                     */
+  int32_t mode;
+  int64_t n;
+  int32_t refine_iters;  /* mixed modes: Newton-Schulz updates              */
+  int32_t reserved;
+  double rho;            /* mixed modes: final residual; else -1            */
+  double t_queue_ms;     /* submit -> admitted                              */
+  double t_device_ms;    /* GPU time of the request on its slot stream      */
+  double t_total_ms;     /* submit -> result available                      */
+} blockinv_result;
+
+/* Create a context on `device` (1 <= max_slots <= 64). */
+int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, blockinv_ctx** ctx);
+/* Queue one inversion (arguments as blockinv_invert; A device memory unless
+ * flags has BLOCKINV_SUBMIT_HOST). A must stay valid until the request is
+ * finished. Returns BLOCKINV_ERR_BUDGET if the request alone exceeds the
+ * budget. *ticket identifies the request. */
+int blockinv_submit(blockinv_ctx* ctx, int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
+                    int mode, int flags, uint64_t* ticket);
+/* BLOCKINV_PENDING while the request is queued or running; otherwise its
+ * final status, with the record in *out; the ticket is then released. */
+int blockinv_poll(blockinv_ctx* ctx, uint64_t ticket, blockinv_result* out);
+/* As blockinv_poll, but blocks until the request is finished. */
+int blockinv_wait(blockinv_ctx* ctx, uint64_t ticket, blockinv_result* out);
+/* Cancel a queued request (its status becomes BLOCKINV_ERR_CANCELLED);
+ * returns BLOCKINV_PENDING if it is already running. */
+int blockinv_cancel(blockinv_ctx* ctx, uint64_t ticket);
+/* Queued and running request counts and the device bytes admitted. */
+int blockinv_ctx_stats(blockinv_ctx* ctx, int64_t* queued, int64_t* running, size_t* bytes_in_use);
+/* Finish running requests, cancel queued ones, release everything. */
+int blockinv_ctx_destroy(blockinv_ctx* ctx);
 
 /* Options and per-call report for blockinv_invert_ex. */
 typedef struct {

@@ -19,6 +19,8 @@ MODES = {"f64": F64, "tf32": MIXED_TF32, "bf16": MIXED_BF16}
 OK, PENDING = 0, 1
 ERR_INVALID, ERR_SINGULAR, ERR_NONFINITE, ERR_NOMEM = -1, -2, -3, -4
 ERR_BUDGET, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = -5, -6, -7, -8
+ERR_CANCELLED = -9
+SUBMIT_HOST = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -38,6 +40,14 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "blockinv_batch_plan_run": (_int, [_vp, _vp, _vp]),
     "blockinv_batch_plan_destroy": (_int, [_vp]),
+    "blockinv_ctx_create": (_int, [_int, ctypes.c_size_t, _int, ctypes.POINTER(ctypes.c_void_p)]),
+    "blockinv_submit": (_int, [_vp, _i64, _i32, _i32p, _vp, _i64, _int, _int, ctypes.POINTER(ctypes.c_uint64)]),
+    "blockinv_poll": (_int, [_vp, ctypes.c_uint64, _vp]),
+    "blockinv_wait": (_int, [_vp, ctypes.c_uint64, _vp]),
+    "blockinv_cancel": (_int, [_vp, ctypes.c_uint64]),
+    "blockinv_ctx_stats": (_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "blockinv_ctx_destroy": (_int, [_vp]),
     "blockinv_invert_noalloc": (_int, [_i64, _i32, _i32p, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "blockinv_residual_tc": (_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(ctypes.c_double),
@@ -176,6 +186,60 @@ class BatchPlan:
     def close(self):
         if self.handle:
             lib().blockinv_batch_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("mode", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("refine_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho", ctypes.c_double),
+                ("t_queue_ms", ctypes.c_double), ("t_device_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class Context:
+    """Serving context: submit / poll / wait / cancel (see include/blockinv.h)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=8 << 30, max_slots=8):
+        self.handle = ctypes.c_void_p()
+        st = lib().blockinv_ctx_create(device, hbm_budget_bytes, max_slots, ctypes.byref(self.handle))
+        if st != OK:
+            raise BlockinvError(st, -1, "blockinv_ctx_create")
+
+    def submit(self, n, block_sizes, A_ptr, lda, mode=F64, flags=0):
+        p, arr, _ = _sizes(block_sizes)
+        t = ctypes.c_uint64(0)
+        st = lib().blockinv_submit(self.handle, n, p, arr, A_ptr, lda, _mode(mode), flags, ctypes.byref(t))
+        return st, t.value
+
+    def poll(self, ticket):
+        r = Result()
+        st = lib().blockinv_poll(self.handle, ticket, ctypes.byref(r))
+        return st, r
+
+    def wait(self, ticket):
+        r = Result()
+        st = lib().blockinv_wait(self.handle, ticket, ctypes.byref(r))
+        return st, r
+
+    def cancel(self, ticket):
+        return lib().blockinv_cancel(self.handle, ticket)
+
+    def stats(self):
+        q, r, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        lib().blockinv_ctx_stats(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b))
+        return q.value, r.value, b.value
+
+    def close(self):
+        if self.handle:
+            lib().blockinv_ctx_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

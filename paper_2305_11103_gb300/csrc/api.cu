@@ -266,6 +266,53 @@ int finish(const int32_t* status_dev, cudaStream_t s) {
 
 }  // namespace
 
+// ---------------------------------------------- hooks for the serving loop --
+struct ServeJob {
+  MixedState ms;
+};
+
+int serve_make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, int mode, Plan* pl) {
+  if (!valid_mode(mode)) return BLOCKINV_ERR_INVALID;
+  return make_plan(n, p, block_sizes, lda, pl);
+}
+
+size_t serve_footprint(const Plan& pl, int mode) {
+  const size_t n = pl.n, b = pl.bmax;
+  size_t f = 8 * (b * b + n * b) + 256;
+  if (mode != BLOCKINV_F64) {
+    const size_t kp = mixed_kpad(pl.bmax);
+    f = 8 * n * n + 4 * n * ((n + 31) / 32 * 32) + 4 * b * b + 2 * 4 * n * kp +
+        refine_workspace_bytes(pl.n, kResidualSlices, 5) + 4096;
+  }
+  return f;
+}
+
+int serve_enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s, double tol,
+                  int max_refine, ServeJob** job) {
+  *job = nullptr;
+  if (mode == BLOCKINV_F64) return enqueue_f64(pl, A, lda, status, s);
+  Options opt;
+  if (tol > 0) opt.tol = tol;
+  if (max_refine >= 0) opt.max_refine = max_refine;
+  auto j = new ServeJob();
+  const int st = enqueue_mixed(pl, A, lda, mode == BLOCKINV_MIXED_BF16, status, s, opt, j->ms, false);
+  *job = j;
+  return st;
+}
+
+void serve_job_info(ServeJob* job, cudaStream_t s, double* rho, int* iters) {
+  *rho = -1.0;
+  *iters = 0;
+  if (!job || !job->ms.hist.ptr) return;
+  blockinv_info info{};
+  info.rho = -1;
+  read_mixed_info(job->ms, s, &info);
+  *rho = info.rho;
+  *iters = info.refine_iters;
+}
+
+void serve_job_release(ServeJob* job) { delete job; }
+
 TraceScope::TraceScope(const char* name, double flops, double bytes, cudaStream_t s) : s_(s) {
   std::lock_guard<std::mutex> g(g_trace_mu);
   if (!g_trace_on) return;
@@ -457,6 +504,7 @@ const char* blockinv_status_str(int status) {
     case BLOCKINV_ERR_NOT_CONVERGED: return "refinement did not converge";
     case BLOCKINV_ERR_TIMEOUT: return "device wait timed out";
     case BLOCKINV_ERR_CUDA: return "CUDA error";
+    case BLOCKINV_ERR_CANCELLED: return "cancelled";
     default: return "unknown status";
   }
 }

@@ -107,6 +107,15 @@ cudaError_t mixed_elimination(const Plan& pl, bool bf16, float* X32, int64_t ld3
 // Batched small matrices, order 1..8, one thread per matrix (k_small.cu).
 cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* status, cudaStream_t s);
 
+// Hooks the serving loop (serve.cu) uses to run one request (api.cu).
+struct ServeJob;
+int serve_make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, int mode, Plan* pl);
+size_t serve_footprint(const Plan& pl, int mode);
+int serve_enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s, double tol,
+                  int max_refine, ServeJob** job);
+void serve_job_info(ServeJob* job, cudaStream_t s, double* rho, int* iters);
+void serve_job_release(ServeJob* job);
+
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
 constexpr int kResidualSlices = 12;
 size_t refine_workspace_bytes(int n, int S, int max_updates);

@@ -1,0 +1,346 @@
+// Serving loop: a context owns a worker thread and `max_slots` CUDA streams.
+// Requests (one matrix each, any order, any mode) enter a queue; the worker
+// admits them first-fit whenever a slot is free and the request's device
+// footprint fits in what is left of the HBM budget, and enqueues the
+// inversion on that slot's stream. Requests on different slots overlap on
+// the GPU, and a request that arrives while others run starts as soon as a
+// slot and memory free up (continuous batching: the set of requests on the
+// device changes while it works). Each request's result does not depend on
+// what runs beside it: the kernels of one request read and write only that
+// request's matrix and workspace.
+//
+// Per request the context records the time in the queue, the device time
+// (CUDA events on its slot stream) and the end-to-end time, plus the
+// refinement residual for the mixed modes.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+using Clock = std::chrono::steady_clock;
+
+namespace blockinv {
+namespace {
+
+struct Request {
+  uint64_t id = 0;
+  Plan plan;
+  double* A = nullptr;
+  int64_t lda = 0;
+  int mode = 0;
+  bool host = false;
+  size_t footprint = 0;
+  Clock::time_point t_submit, t_admit, t_done;
+  int status = BLOCKINV_PENDING;
+  double rho = -1.0;
+  int iters = 0;
+  float dev_ms = 0.f;
+  bool done = false;
+};
+
+struct Slot {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int32_t* status_dev = nullptr;   // 2 words
+  int32_t* status_host = nullptr;  // pinned, 2 words
+  double* dbuf = nullptr;          // device copy of a host request
+  ServeJob* job = nullptr;
+  Request* req = nullptr;
+  int enqueue_status = BLOCKINV_OK;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+}  // namespace blockinv
+
+struct blockinv_ctx {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  double tol = 1e-12;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<blockinv::Request*> queue;
+  std::unordered_map<uint64_t, blockinv::Request*> reqs;
+  uint64_t next_id = 1;
+  std::vector<blockinv::Slot> slots;
+  std::thread worker;
+  bool stopping = false;
+  size_t busy = 0;
+};
+
+namespace blockinv {
+namespace {
+
+void launch_request(blockinv_ctx* c, Slot& sl) {
+  Request* r = sl.req;
+  const int n = r->plan.n;
+  const size_t row = sizeof(double) * (size_t)n;
+  cudaStream_t s = sl.s;
+  cudaEventRecord(sl.ev0, s);
+  double* X = r->A;
+  int64_t ld = r->lda;
+  cudaError_t e = cudaSuccess;
+  sl.dbuf = nullptr;
+  if (r->host) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&sl.dbuf), row * n, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(sl.dbuf, row, r->A, sizeof(double) * r->lda, row, n, cudaMemcpyHostToDevice, s);
+    X = sl.dbuf;
+    ld = n;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(sl.status_dev, 0, 2 * sizeof(int32_t), s);
+  int st = (e == cudaSuccess) ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  if (st == BLOCKINV_OK) st = serve_enqueue(r->plan, X, ld, r->mode, sl.status_dev, s, c->tol, -1, &sl.job);
+  if (st == BLOCKINV_OK && r->host)
+    e = cudaMemcpy2DAsync(r->A, sizeof(double) * r->lda, sl.dbuf, row, row, n, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (sl.dbuf) cudaFreeAsync(sl.dbuf, s);
+  sl.dbuf = nullptr;
+  cudaEventRecord(sl.ev1, s);
+  sl.enqueue_status = (st == BLOCKINV_OK && e != cudaSuccess) ? BLOCKINV_ERR_CUDA : st;
+}
+
+void finalize_request(blockinv_ctx* c, Slot& sl) {
+  Request* r = sl.req;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
+  int st = sl.enqueue_status != BLOCKINV_OK ? sl.enqueue_status : sl.status_host[0];
+  double rho = -1.0;
+  int iters = 0;
+  if (sl.job) {
+    serve_job_info(sl.job, sl.s, &rho, &iters);
+    serve_job_release(sl.job);
+    sl.job = nullptr;
+  }
+  std::lock_guard<std::mutex> g(c->mu);
+  r->dev_ms = ms;
+  r->status = st;
+  r->rho = rho;
+  r->iters = iters;
+  r->t_done = Clock::now();
+  r->done = true;
+  c->used -= r->footprint;
+  c->busy -= 1;
+  sl.req = nullptr;
+  c->cv_done.notify_all();
+}
+
+void worker_loop(blockinv_ctx* c) {
+  cudaSetDevice(c->device);
+  std::vector<Slot*> admitted;
+  for (;;) {
+    bool progressed = false;
+    for (Slot& sl : c->slots) {
+      if (sl.req && cudaEventQuery(sl.ev1) == cudaSuccess) {
+        finalize_request(c, sl);
+        progressed = true;
+      }
+    }
+    admitted.clear();
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      if (c->stopping && c->queue.empty() && c->busy == 0) break;
+      for (Slot& sl : c->slots) {
+        if (sl.req) continue;
+        // first fit: the oldest queued request that fits in the remaining budget
+        auto it = c->queue.begin();
+        for (; it != c->queue.end(); ++it)
+          if ((*it)->footprint <= c->budget - c->used) break;
+        if (it == c->queue.end()) break;
+        Request* r = *it;
+        c->queue.erase(it);
+        c->used += r->footprint;
+        c->busy += 1;
+        r->t_admit = Clock::now();
+        sl.req = r;
+        admitted.push_back(&sl);
+      }
+      if (admitted.empty() && !progressed) {
+        c->cv_work.wait_for(lk, std::chrono::microseconds(50));
+        continue;
+      }
+    }
+    for (Slot* sl : admitted) launch_request(c, *sl);
+  }
+}
+
+}  // namespace
+}  // namespace blockinv
+
+using namespace blockinv;
+
+extern "C" {
+
+int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, blockinv_ctx** out) {
+  if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0) return BLOCKINV_ERR_INVALID;
+  *out = nullptr;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) return BLOCKINV_ERR_INVALID;
+  auto c = new blockinv_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  c->slots.resize(max_slots);
+  cudaError_t e = cudaSuccess;
+  for (Slot& sl : c->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&sl.ev1);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.status_dev), 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.status_host), 2 * sizeof(int32_t));
+  }
+  if (e != cudaSuccess) {
+    for (Slot& sl : c->slots) {
+      if (sl.s) cudaStreamDestroy(sl.s);
+      if (sl.ev0) cudaEventDestroy(sl.ev0);
+      if (sl.ev1) cudaEventDestroy(sl.ev1);
+      if (sl.status_dev) cudaFree(sl.status_dev);
+      if (sl.status_host) cudaFreeHost(sl.status_host);
+    }
+    delete c;
+    cudaSetDevice(prev);
+    return BLOCKINV_ERR_CUDA;
+  }
+  c->worker = std::thread(worker_loop, c);
+  cudaSetDevice(prev);
+  *out = c;
+  return BLOCKINV_OK;
+}
+
+int blockinv_submit(blockinv_ctx* c, int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
+                    int mode, int flags, uint64_t* ticket) {
+  if (!c || !ticket || !A || (flags & ~BLOCKINV_SUBMIT_HOST)) return BLOCKINV_ERR_INVALID;
+  auto r = new Request();
+  int st = serve_make_plan(n, p, block_sizes, lda, mode, &r->plan);
+  if (st != BLOCKINV_OK) {
+    delete r;
+    return st;
+  }
+  r->A = A;
+  r->lda = lda;
+  r->mode = mode;
+  r->host = (flags & BLOCKINV_SUBMIT_HOST) != 0;
+  r->footprint = serve_footprint(r->plan, mode) + (r->host ? sizeof(double) * (size_t)n * n : 0);
+  if (r->footprint > c->budget) {
+    delete r;
+    return BLOCKINV_ERR_BUDGET;
+  }
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (c->stopping) {
+      delete r;
+      return BLOCKINV_ERR_INVALID;
+    }
+    r->id = c->next_id++;
+    c->reqs[r->id] = r;
+    c->queue.push_back(r);
+  }
+  c->cv_work.notify_one();
+  *ticket = r->id;
+  return BLOCKINV_OK;
+}
+
+static int take_result(blockinv_ctx* c, std::unordered_map<uint64_t, Request*>::iterator it, blockinv_result* out) {
+  Request* r = it->second;
+  const int st = r->status;
+  if (out) {
+    out->status = st;
+    out->mode = r->mode;
+    out->n = r->plan.n;
+    out->refine_iters = r->iters;
+    out->rho = r->rho;
+    out->t_queue_ms = st == BLOCKINV_ERR_CANCELLED ? ms_between(r->t_submit, r->t_done)
+                                                   : ms_between(r->t_submit, r->t_admit);
+    out->t_device_ms = r->dev_ms;
+    out->t_total_ms = ms_between(r->t_submit, r->t_done);
+  }
+  c->reqs.erase(it);
+  delete r;
+  return st;
+}
+
+int blockinv_poll(blockinv_ctx* c, uint64_t ticket, blockinv_result* out) {
+  if (!c) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  auto it = c->reqs.find(ticket);
+  if (it == c->reqs.end()) return BLOCKINV_ERR_INVALID;
+  if (!it->second->done) return BLOCKINV_PENDING;
+  return take_result(c, it, out);
+}
+
+int blockinv_wait(blockinv_ctx* c, uint64_t ticket, blockinv_result* out) {
+  if (!c) return BLOCKINV_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(ticket);
+  if (it == c->reqs.end()) return BLOCKINV_ERR_INVALID;
+  Request* r = it->second;
+  c->cv_done.wait(lk, [&] { return r->done; });
+  return take_result(c, c->reqs.find(ticket), out);
+}
+
+int blockinv_cancel(blockinv_ctx* c, uint64_t ticket) {
+  if (!c) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  auto it = c->reqs.find(ticket);
+  if (it == c->reqs.end()) return BLOCKINV_ERR_INVALID;
+  Request* r = it->second;
+  if (r->done) return BLOCKINV_OK;
+  for (auto q = c->queue.begin(); q != c->queue.end(); ++q) {
+    if (*q == r) {
+      c->queue.erase(q);
+      r->status = BLOCKINV_ERR_CANCELLED;
+      r->t_done = Clock::now();
+      r->done = true;
+      c->cv_done.notify_all();
+      return BLOCKINV_OK;
+    }
+  }
+  return BLOCKINV_PENDING;  // already on the GPU: runs to completion
+}
+
+int blockinv_ctx_stats(blockinv_ctx* c, int64_t* queued, int64_t* running, size_t* bytes_in_use) {
+  if (!c) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (queued) *queued = (int64_t)c->queue.size();
+  if (running) *running = (int64_t)c->busy;
+  if (bytes_in_use) *bytes_in_use = c->used;
+  return BLOCKINV_OK;
+}
+
+int blockinv_ctx_destroy(blockinv_ctx* c) {
+  if (!c) return BLOCKINV_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->stopping = true;
+    for (Request* r : c->queue) {
+      r->status = BLOCKINV_ERR_CANCELLED;
+      r->done = true;
+    }
+    c->queue.clear();
+  }
+  c->cv_work.notify_all();
+  c->cv_done.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  for (Slot& sl : c->slots) {
+    cudaStreamSynchronize(sl.s);
+    cudaStreamDestroy(sl.s);
+    cudaEventDestroy(sl.ev0);
+    cudaEventDestroy(sl.ev1);
+    cudaFree(sl.status_dev);
+    cudaFreeHost(sl.status_host);
+  }
+  for (auto& kv : c->reqs) delete kv.second;
+  delete c;
+  return BLOCKINV_OK;
+}
+
+}  // extern "C"
