@@ -19,6 +19,7 @@ bounded sample of the same workload (order 4096, same block order and
 distribution) and prints the same line with "impl": "reference".
 """
 import argparse
+import numpy as np
 import hashlib
 import json
 import os
@@ -83,6 +84,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision + refinement legs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched legs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="length of the Poisson arrival window of the serving leg")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="measure library GEMM rates (FP64, FP32, TF32, BF16, FP16, FP8, INT8) and exit")
     return ap.parse_args()
@@ -325,6 +330,164 @@ def run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms):
     return out
 
 
+def run_batched(args, bi, torch, stream):
+    """200 000 SPD 5 x 5 (one thread per matrix) and 2000 uneven matrices
+    n in [8, 512] (grouped launches replayed from a CUDA graph)."""
+    from paper_2305_11103_gb300 import inputs
+    out = {}
+    # --- 200 000 x 5 x 5 SPD, B B^T + 0.1 I, seed 5
+    count, n = 200_000, 5
+    A = inputs.spd_covariance_batch(count, n, 5)
+    dA = torch.from_numpy(A).cuda()
+    dX = torch.empty_like(dA)
+    st = torch.empty(count, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        dX.copy_(dA)
+        bi.blockinv_invert_batched_small(count, n, dX.data_ptr(), st.data_ptr(), stream)
+    torch.cuda.synchronize()
+    bi.blockinv_trace_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 10)
+    e0.record(stream)
+    for _ in range(reps):
+        dX.copy_(dA)
+        bi.blockinv_invert_batched_small(count, n, dX.data_ptr(), st.data_ptr(), stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bi.blockinv_trace_enable(False)
+    tr = bi.blockinv_trace_summary()["small_batched_f64"]
+    ms = e0.elapsed_time(e1) / reps
+    X = dX.cpu().numpy()
+    R = np.einsum("bij,bjk->bik", A, X) - np.eye(n)[None]
+    rho = np.linalg.norm(R, axis=(1, 2)) / (np.linalg.norm(A, axis=(1, 2)) * np.linalg.norm(X, axis=(1, 2)))
+    kms = tr["ms"] / tr["launches"]
+    peaks = measured_peaks()
+    gbs = tr["bytes"] / tr["launches"] / (kms / 1e3) / 1e9
+    tfs = tr["flops"] / tr["launches"] / (kms / 1e3) / 1e12
+    out["spd5x5_200k"] = {
+        "workload": "200000 SPD 5x5 FP64 (B B^T + 0.1 I, seed 5), blocks [2, 3], one thread per matrix",
+        "ms_per_batch": ms, "inverses_per_s": count / (ms / 1e3), "kernel_ms": kms,
+        "max_rho": float(rho.max()), "failed": int((st != 0).sum().item()),
+        "roofline": {"bound": "alu", "kernel": "small_batched_f64", "achieved": tfs, "unit": "TFLOP/s",
+                     "peak": FP64_PEAK_TFLOPS, "frac": tfs / FP64_PEAK_TFLOPS,
+                     "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"],
+                     "algorithmic": "2 n^3 = 250 flop and 2 x 200 B per matrix"},
+    }
+    del dA, dX, st
+    # --- 2000 uneven matrices, n = round(exp(U(ln 8, ln 512))), U[-1,1] + n I, seed 6
+    mats = inputs.uneven_batch(2000, 8, 512, 6)
+    src = [torch.from_numpy(M).cuda() for M in mats]
+    dst = [torch.empty_like(t) for t in src]
+    ns = [t.shape[0] for t in src]
+    plan = bi.BatchPlan(ns, None, [t.data_ptr() for t in dst], ns)
+    stt = torch.empty(len(mats), dtype=torch.int32, device="cuda")
+
+    def refresh():
+        torch._foreach_copy_(dst, src)
+
+    for _ in range(args.warmup):
+        refresh()
+        plan.run(stream, stt.data_ptr())
+    torch.cuda.synchronize()
+    bi.blockinv_trace_enable(True)
+    per = []
+    for _ in range(args.steps):
+        refresh()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run(stream, stt.data_ptr())
+        b.record(stream)
+        torch.cuda.synchronize()
+        per.append(a.elapsed_time(b))
+    bi.blockinv_trace_enable(False)
+    tr = bi.blockinv_trace_summary()["batched_grouped_f64"]
+    ms = sum(per) / len(per)
+    flops = sum(2.0 * m ** 3 for m in ns)
+    g = inputs.rng(66)
+    rhos = []
+    for i in g.choice(len(mats), size=20, replace=False):
+        Xi = dst[i].cpu().numpy()
+        Ai = mats[i]
+        rhos.append(np.linalg.norm(Ai @ Xi - np.eye(Ai.shape[0])) / (np.linalg.norm(Ai) * np.linalg.norm(Xi)))
+    plan.close()
+    tfs = flops / (ms / 1e3) / 1e12
+    out["uneven_2000"] = {
+        "workload": "2000 FP64 matrices, n log-uniform in [8, 512], U[-1,1] + n I (seed 6), 4 blocks of n/4",
+        "ms_per_batch": ms, "inverses_per_s": len(mats) / (ms / 1e3), "value": tfs, "unit": "TFLOP/s",
+        "latency_ms": percentiles(per), "max_rho_sampled": float(max(rhos)),
+        "failed": int((stt != 0).sum().item()),
+        "launches_per_batch": tr["launches"] / args.steps,
+        "roofline": {"bound": "alu", "kernel": "batched_grouped_f64 (graph)", "achieved": tfs,
+                     "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "frac": tfs / FP64_PEAK_TFLOPS},
+    }
+    return out
+
+
+def run_serving(args, bi, torch):
+    """Poisson arrivals at 2000 req/s, sizes log-uniform in [5, 4096] (70%
+    U[-1,1] + n I, 30% B B^T + 0.1 I), through a serving context with a
+    120 GB budget; FP64 and mixed TF32 + refinement."""
+    from paper_2305_11103_gb300 import inputs
+    rate, window = 2000.0, args.serve_seconds
+    arrivals = inputs.poisson_arrivals(rate, window, 7)
+    nreq = len(arrivals)
+    # sizes quantised to 32 log-spaced orders; one pooled matrix per (order, kind)
+    grid = np.unique(np.rint(np.exp(np.linspace(np.log(5), np.log(4096), 32))).astype(int))
+    want = inputs.log_uniform_sizes(nreq, 5, 4096, 7)
+    idx = np.abs(np.log(want)[:, None] - np.log(grid)[None, :]).argmin(axis=1)
+    kinds = (inputs.rng(8).random(nreq) < 0.3).astype(int)
+    pool = {}
+    for k in sorted(set(zip(idx.tolist(), kinds.tolist()))):
+        n = int(grid[k[0]])
+        if k[1] == 0:
+            M = torch.from_numpy(inputs.diag_dominant_uniform(n, 7000 + n, shift=n)).cuda()
+        else:
+            B = torch.from_numpy(inputs.rng(8000 + n).standard_normal((n, n))).cuda()
+            M = B @ B.T + 0.1 * torch.eye(n, dtype=torch.float64, device="cuda")
+        pool[k] = M
+    out = {"workload": f"Poisson {rate:.0f} req/s for {window:g} s ({nreq} requests), n log-uniform in [5, 4096] "
+                       f"quantised to {len(grid)} orders, 70% U[-1,1]+nI / 30% B B^T+0.1I, seed 7; "
+                       "budget 120 GB, 16 slots"}
+    for mode in ("f64", "tf32"):
+        ctx = bi.Context(0, 120 << 30, 16)
+        bufs, tickets, lat = {}, {}, []
+        done = 0
+        t0 = time.perf_counter()
+        i = 0
+        statuses = []
+        while done < nreq:
+            now = time.perf_counter() - t0
+            while i < nreq and arrivals[i] <= now:
+                key = (int(idx[i]), int(kinds[i]))
+                buf = pool[key].clone()
+                n = buf.shape[0]
+                st, t = ctx.submit(n, None, buf.data_ptr(), n, mode)
+                if st != bi.OK:
+                    raise bi.BlockinvError(st, -1, "blockinv_submit")
+                bufs[t] = buf
+                tickets[t] = arrivals[i]
+                i += 1
+            for t in list(tickets):
+                st, r = ctx.poll(t)
+                if st == bi.PENDING:
+                    continue
+                lat.append(1e3 * ((time.perf_counter() - t0) - tickets.pop(t)))
+                statuses.append(st)
+                bufs.pop(t)
+                done += 1
+            if i < nreq and not tickets:
+                time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
+        wall = time.perf_counter() - t0
+        ctx.close()
+        flops = sum(2.0 * float(grid[k]) ** 3 for k in idx)
+        out[mode] = {"completed": done, "wall_s": wall, "throughput_req_s": done / wall,
+                     "offered_req_s": rate, "effective_tflops": flops / wall / 1e12,
+                     "latency_ms": percentiles(lat), "failed": sum(1 for s in statuses if s != bi.OK)}
+    return out
+
+
 # ----------------------------------------------------------- our arm -------
 def run_ours(args):
     import numpy as np
@@ -420,6 +583,10 @@ def run_ours(args):
         cpu = cpu_baseline(w)
 
     mixed = {} if args.no_mixed else run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms)
+    del dA, dX
+    torch.cuda.empty_cache()
+    batched = {} if args.no_batched else run_batched(args, bi, torch, stream)
+    serving = {} if args.no_serve else run_serving(args, bi, torch)
 
     if rank == 0:
         out = {
@@ -433,6 +600,8 @@ def run_ours(args):
             "gpu_launches": launches, "kernels": trace,
             "latency_ms": lat,
             "mixed": mixed,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:

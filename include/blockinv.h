@@ -193,7 +193,7 @@ typedef struct {
   int32_t mode;
   int64_t n;
   int32_t refine_iters;  /* mixed modes: Newton-Schulz updates              */
-  int32_t reserved;
+  int32_t used_fallback; /* 1: refinement failed, the FP64 path was rerun   */
   double rho;            /* mixed modes: final residual; else -1            */
   double t_queue_ms;     /* submit -> admitted                              */
   double t_device_ms;    /* GPU time of the request on its slot stream      */
@@ -208,6 +208,8 @@ int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, bloc
  * budget. *ticket identifies the request. */
 int blockinv_submit(blockinv_ctx* ctx, int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
                     int mode, int flags, uint64_t* ticket);
+/* A mixed-mode request whose refinement does not converge (for example an
+ * ill-conditioned input) is rerun on its slot with the FP64 path. */
 /* BLOCKINV_PENDING while the request is queued or running; otherwise its
  * final status, with the record in *out; the ticket is then released. */
 int blockinv_poll(blockinv_ctx* ctx, uint64_t ticket, blockinv_result* out);

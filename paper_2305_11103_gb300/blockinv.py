@@ -197,7 +197,7 @@ class BatchPlan:
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("mode", ctypes.c_int32), ("n", ctypes.c_int64),
-                ("refine_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho", ctypes.c_double),
+                ("refine_iters", ctypes.c_int32), ("used_fallback", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("t_queue_ms", ctypes.c_double), ("t_device_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
 
     def as_dict(self):

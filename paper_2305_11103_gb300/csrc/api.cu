@@ -313,6 +313,19 @@ void serve_job_info(ServeJob* job, cudaStream_t s, double* rho, int* iters) {
 
 void serve_job_release(ServeJob* job) { delete job; }
 
+// After a mixed request ended NOT_CONVERGED: restore the input from the
+// job's FP64 copy and enqueue the FP64 path on the same stream.
+int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda, int32_t* status,
+                           cudaStream_t s) {
+  if (!job || !job->ms.a0.ptr) return BLOCKINV_ERR_NOT_CONVERGED;
+  const size_t row = sizeof(double) * (size_t)pl.n;
+  cudaError_t e = cudaMemcpy2DAsync(A, sizeof(double) * lda, job->ms.a0.ptr, row, row, pl.n,
+                                    cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  return enqueue_f64(pl, A, lda, status, s);
+}
+
 TraceScope::TraceScope(const char* name, double flops, double bytes, cudaStream_t s) : s_(s) {
   std::lock_guard<std::mutex> g(g_trace_mu);
   if (!g_trace_on) return;

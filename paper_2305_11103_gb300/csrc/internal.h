@@ -115,6 +115,8 @@ int serve_enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* sta
                   int max_refine, ServeJob** job);
 void serve_job_info(ServeJob* job, cudaStream_t s, double* rho, int* iters);
 void serve_job_release(ServeJob* job);
+int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda, int32_t* status,
+                           cudaStream_t s);
 
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
 constexpr int kResidualSlices = 12;

@@ -41,6 +41,7 @@ struct Request {
   int iters = 0;
   float dev_ms = 0.f;
   bool done = false;
+  bool fell_back = false;
 };
 
 struct Slot {
@@ -49,9 +50,12 @@ struct Slot {
   int32_t* status_dev = nullptr;   // 2 words
   int32_t* status_host = nullptr;  // pinned, 2 words
   double* dbuf = nullptr;          // device copy of a host request
+  double* X = nullptr;             // the matrix the kernels work on
+  int64_t ld = 0;
   ServeJob* job = nullptr;
   Request* req = nullptr;
   int enqueue_status = BLOCKINV_OK;
+  float dev_ms = 0.f;              // device time of earlier passes (fallback)
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -99,27 +103,59 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
   if (e == cudaSuccess) e = cudaMemsetAsync(sl.status_dev, 0, 2 * sizeof(int32_t), s);
   int st = (e == cudaSuccess) ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
   if (st == BLOCKINV_OK) st = serve_enqueue(r->plan, X, ld, r->mode, sl.status_dev, s, c->tol, -1, &sl.job);
+  sl.X = X;
+  sl.ld = ld;
+  sl.dev_ms = 0.f;
   if (st == BLOCKINV_OK && r->host)
     e = cudaMemcpy2DAsync(r->A, sizeof(double) * r->lda, sl.dbuf, row, row, n, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (sl.dbuf) cudaFreeAsync(sl.dbuf, s);
-  sl.dbuf = nullptr;
   cudaEventRecord(sl.ev1, s);
   sl.enqueue_status = (st == BLOCKINV_OK && e != cudaSuccess) ? BLOCKINV_ERR_CUDA : st;
 }
 
-void finalize_request(blockinv_ctx* c, Slot& sl) {
+// A mixed request whose refinement failed is rerun in FP64 on its slot, from
+// the FP64 copy of its input. Returns true if the rerun was enqueued.
+bool fall_back(Slot& sl) {
+  Request* r = sl.req;
+  cudaStream_t s = sl.s;
+  const int n = r->plan.n;
+  const size_t row = sizeof(double) * (size_t)n;
+  cudaEventRecord(sl.ev0, s);
+  int st = serve_enqueue_fallback(sl.job, r->plan, sl.X, sl.ld, sl.status_dev, s);
+  if (st != BLOCKINV_OK) return false;
+  if (r->host)
+    cudaMemcpy2DAsync(r->A, sizeof(double) * r->lda, sl.dbuf, row, row, n, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaEventRecord(sl.ev1, s);
+  r->fell_back = true;
+  return true;
+}
+
+// Returns false if the request continues (an FP64 rerun was enqueued).
+bool finalize_request(blockinv_ctx* c, Slot& sl) {
   Request* r = sl.req;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
+  ms += sl.dev_ms;
   int st = sl.enqueue_status != BLOCKINV_OK ? sl.enqueue_status : sl.status_host[0];
   double rho = -1.0;
   int iters = 0;
   if (sl.job) {
     serve_job_info(sl.job, sl.s, &rho, &iters);
+    if (st == BLOCKINV_ERR_NOT_CONVERGED && !r->fell_back) {
+      sl.dev_ms = ms;
+      r->iters = iters;
+      if (fall_back(sl)) return false;
+    }
     serve_job_release(sl.job);
     sl.job = nullptr;
   }
+  if (r->fell_back) {
+    rho = -1.0;
+    iters = r->iters;
+  }
+  if (sl.dbuf) cudaFreeAsync(sl.dbuf, sl.s);
+  sl.dbuf = nullptr;
   std::lock_guard<std::mutex> g(c->mu);
   r->dev_ms = ms;
   r->status = st;
@@ -131,6 +167,7 @@ void finalize_request(blockinv_ctx* c, Slot& sl) {
   c->busy -= 1;
   sl.req = nullptr;
   c->cv_done.notify_all();
+  return true;
 }
 
 void worker_loop(blockinv_ctx* c) {
@@ -257,6 +294,7 @@ static int take_result(blockinv_ctx* c, std::unordered_map<uint64_t, Request*>::
     out->mode = r->mode;
     out->n = r->plan.n;
     out->refine_iters = r->iters;
+    out->used_fallback = r->fell_back ? 1 : 0;
     out->rho = r->rho;
     out->t_queue_ms = st == BLOCKINV_ERR_CANCELLED ? ms_between(r->t_submit, r->t_done)
                                                    : ms_between(r->t_submit, r->t_admit);

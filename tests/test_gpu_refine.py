@@ -145,3 +145,36 @@ def test_mixed_singular_reported(bi):
     J = np.fliplr(np.eye(8)).copy()
     st, info, _ = refine(bi, J, [4, 4], "tf32")
     assert st == bi.ERR_SINGULAR and info.failing_block == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("sigma,seed", [(1.5, 3), (1.05, 4)])
+def test_full_size_16384_mixed(bi, mode, sigma, seed):
+    """n = 16384, 64 x 64 grid of 256-blocks, N(0,1)/sqrt(n) + sigma I: the
+    mixed path with refinement to rho <= 1e-12. The oracle cannot invert it in
+    test time: the GPU's own FP64-accurate residual, sampled rows of A X - I in
+    FP64 on the CPU, and sampled columns against LAPACK solves."""
+    n = 16384
+    A = inputs.gaussian_shifted(n, seed, sigma=sigma)
+    dA = torch.from_numpy(A).cuda()
+    dX = dA.clone()
+    st, info = bi.blockinv_invert_ex(n, [256] * 64, dX.data_ptr(), n, mode, None)
+    assert st == bi.OK and info.used_fallback == 0, info.as_dict()
+    assert info.rho <= 1e-12
+    st, rho_tc = bi.blockinv_residual_tc(n, dA.data_ptr(), n, dX.data_ptr(), n)
+    assert st == bi.OK and rho_tc <= 1e-12
+    X = dX.cpu().numpy()
+    g = inputs.rng(seed + 99)
+    nA, nX = np.linalg.norm(A), np.linalg.norm(X)
+    for i in g.choice(n, size=8, replace=False):
+        e = A[i] @ X
+        e[i] -= 1.0
+        assert np.linalg.norm(e) * np.sqrt(n) / (nA * nX) <= 1e-12
+    cols = g.choice(n, size=2, replace=False)
+    E = np.zeros((n, 2))
+    E[cols, range(2)] = 1.0
+    S = np.linalg.solve(A, E)
+    kappa = nA * nX
+    for t, j in enumerate(cols):
+        assert np.linalg.norm(X[:, j] - S[:, t]) / np.linalg.norm(S[:, t]) <= 4 * n * kappa * U64

@@ -100,6 +100,20 @@ def test_mixed_mode_requests(bi):
     ctx.close()
 
 
+def test_mixed_fallback_for_ill_conditioned(bi):
+    """B B^T + 0.1 I at n = 1500 (kappa ~ 1e5): BF16 refinement does not
+    contract, so the request is rerun in FP64 and still meets the gate."""
+    n = 1500
+    A = inputs.spd_covariance(n, 760)
+    ctx = bi.Context(0, 8 << 30, 2)
+    d = torch.from_numpy(A).cuda()
+    st, t = ctx.submit(n, None, d.data_ptr(), n, "bf16")
+    st, r = ctx.wait(t)
+    assert st == bi.OK
+    assert rho(A, d.cpu().numpy()) <= 1e-12
+    ctx.close()
+
+
 def test_budget_admission(bi):
     n = 1024
     A = inputs.diag_dominant_uniform(n, 730)
