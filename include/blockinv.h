@@ -229,7 +229,10 @@ typedef struct {
   int32_t max_refine;  /* Newton-Schulz iteration cap (mixed modes); < 0 means 5;      */
                        /* 0 returns the low-precision elimination unrefined           */
   int32_t fallback;    /* mixed modes: 1 = rerun in FP64 if refinement fails (default) */
-  int32_t reserved[4];
+  int32_t split;       /* mixed modes: 0 or 2 (default) = split each Schur-update operand */
+                       /* into hi + lo and run hi*hi + hi*lo + lo*hi on the tensor cores; */
+                       /* 1 = a single product                                           */
+  int32_t reserved[3];
 } blockinv_options;
 
 typedef struct {

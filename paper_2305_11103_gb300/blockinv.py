@@ -64,7 +64,7 @@ SIGNATURES = {
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("fallback", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -132,10 +132,11 @@ def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_p
                                        status_dev_ptr)
 
 
-def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1):
+def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1,
+                       split=0):
     """Returns (status, Info)."""
     p, arr, _ = _sizes(block_sizes)
-    opt = Options(tol=tol, max_refine=max_refine, fallback=fallback)
+    opt = Options(tol=tol, max_refine=max_refine, fallback=fallback, split=split)
     info = Info()
     st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
                                   ctypes.byref(info))

@@ -153,6 +153,7 @@ struct Options {
   double tol = 1e-12;
   int max_refine = 5;
   bool fallback = true;
+  int split = 2;  // operand slices of the mixed Schur update (1 or 2)
 };
 
 Options resolve(const blockinv_options* o) {
@@ -161,13 +162,15 @@ Options resolve(const blockinv_options* o) {
     if (o->tol > 0) r.tol = o->tol;
     if (o->max_refine >= 0) r.max_refine = o->max_refine;
     r.fallback = o->fallback != 0;
+    if (o->split == 1) r.split = 1;
   }
   return r;
 }
 
 // Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
 // of the low-precision inverse).
-int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* status, cudaStream_t s) {
+int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int nsl, int32_t* status,
+                       cudaStream_t s) {
   const int n = pl.n;
   const int64_t ld32 = (n + 31) / 32 * 32;
   const int kpad = mixed_kpad(pl.bmax);
@@ -175,8 +178,8 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int32_
   AsyncBuf x32, pinv, u, vt;
   cudaError_t e = x32.alloc(sizeof(float) * (size_t)n * ld32, s);
   if (e == cudaSuccess) e = pinv.alloc(sizeof(float) * (size_t)pl.bmax * pl.bmax, s);
-  if (e == cudaSuccess) e = u.alloc(eb * (size_t)n * kpad, s);
-  if (e == cudaSuccess) e = vt.alloc(eb * (size_t)n * kpad, s);
+  if (e == cudaSuccess) e = u.alloc(eb * (size_t)n * kpad * nsl, s);
+  if (e == cudaSuccess) e = vt.alloc(eb * (size_t)n * kpad * nsl, s);
   if (e != cudaSuccess) return cuda_status(e);
   float* X32 = static_cast<float*>(x32.ptr);
   {
@@ -184,7 +187,7 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int32_
     e = launch_cast_f64_to_f32(A, lda, X32, ld32, n, s);
   }
   if (e == cudaSuccess)
-    e = mixed_elimination(pl, bf16, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, status, s);
+    e = mixed_elimination(pl, bf16, nsl, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, status, s);
   if (e == cudaSuccess) {
     TraceScope t("cast_f32_to_f64", 0, 12.0 * n * (double)n, s);
     e = launch_cast_f32_to_f64(X32, ld32, A, lda, n, s);
@@ -214,7 +217,7 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(ms.a0.ptr, row, A, sizeof(double) * lda, row, n, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  int st = enqueue_mixed_elim(pl, A, lda, bf16, status, s);
+  int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, status, s);
   if (st != BLOCKINV_OK || opt.max_refine == 0) return st;
   e = ms.ws.alloc(refine_workspace_bytes(n, kResidualSlices, opt.max_refine), s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -281,7 +284,7 @@ size_t serve_footprint(const Plan& pl, int mode) {
   size_t f = 8 * (b * b + n * b) + 256;
   if (mode != BLOCKINV_F64) {
     const size_t kp = mixed_kpad(pl.bmax);
-    f = 8 * n * n + 4 * n * ((n + 31) / 32 * 32) + 4 * b * b + 2 * 4 * n * kp +
+    f = 8 * n * n + 4 * n * ((n + 31) / 32 * 32) + 4 * b * b + 2 * 2 * 4 * n * kp +
         refine_workspace_bytes(pl.n, kResidualSlices, 5) + 4096;
   }
   return f;

@@ -99,9 +99,10 @@ cudaError_t launch_cast_f64_to_f32(const double* A, int64_t lda, float* X, int64
 cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64_t lda, int n, cudaStream_t s);
 int mixed_kpad(int bmax);
 // Runs every elimination step on X32 (n x n, leading dimension ld32). Pinv is
-// bmax^2 floats; U and Vt are n x mixed_kpad(bmax) operands of 4 (TF32) or
-// 2 (BF16) bytes per element.
-cudaError_t mixed_elimination(const Plan& pl, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
+// bmax^2 floats; U and Vt are n x (nsl * mixed_kpad(bmax)) operands of 4
+// (TF32) or 2 (BF16) bytes per element; nsl = 2 splits each operand into
+// hi + lo and runs the three products hi*hi + hi*lo + lo*hi.
+cudaError_t mixed_elimination(const Plan& pl, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, int32_t* status, cudaStream_t s);
 
 // Batched small matrices, order 1..8, one thread per matrix (k_small.cu).

@@ -72,14 +72,18 @@ __global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx,
 constexpr int kCols = 32;
 constexpr int kKc = 8;
 
+// Operands are stored as `nsl` slices of kpad columns: slice 0 holds the
+// rounded value (hi), slice 1 (if present) the rounded remainder (lo), so
+// that hi*hi + hi*lo + lo*hi carries about twice the operand precision.
 template <int MAXB, bool kBF16>
 __global__ void __launch_bounds__(256)
 row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, const float* __restrict__ Pinv,
                        typename OpType<kBF16>::T* __restrict__ U, typename OpType<kBF16>::T* __restrict__ Vt,
-                       int kpad, const int32_t* status, int col_tiles) {
+                       int kpad, int nsl, const int32_t* status, int col_tiles) {
   using Op = OpType<kBF16>;
   if (failed(status)) return;
   const int tid = threadIdx.x;
+  const int64_t ldop = (int64_t)nsl * kpad;
   if ((int)blockIdx.x >= col_tiles) {
     const int64_t total = (int64_t)n * kpad;
     const int64_t stride = (int64_t)(gridDim.x - col_tiles) * blockDim.x;
@@ -87,7 +91,10 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
       const int i = (int)(e / kpad);
       const int l = (int)(e - (int64_t)i * kpad);
       const bool keep = l < b && !(i >= o && i < o + b);
-      U[e] = Op::cvt(keep ? X[(int64_t)i * ldx + o + l] : 0.f);
+      const float v = keep ? X[(int64_t)i * ldx + o + l] : 0.f;
+      const auto hi = Op::cvt(v);
+      U[(int64_t)i * ldop + l] = hi;
+      if (nsl > 1) U[(int64_t)i * ldop + kpad + l] = Op::cvt(v - static_cast<float>(hi));
     }
     return;
   }
@@ -137,8 +144,12 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
   for (int cc = 0; cc < kCols; ++cc) {
     const int jj = j0 + cc;
     if (jj >= n) break;
-    for (int r = tid; r < kpad; r += 256)
-      Vt[(int64_t)jj * kpad + r] = Op::cvt(r < b ? Vs[cc * (MAXB + 1) + r] : 0.f);
+    for (int r = tid; r < kpad; r += 256) {
+      const float v = r < b ? Vs[cc * (MAXB + 1) + r] : 0.f;
+      const auto hi = Op::cvt(v);
+      Vt[(int64_t)jj * ldop + r] = hi;
+      if (nsl > 1) Vt[(int64_t)jj * ldop + kpad + r] = Op::cvt(v - static_cast<float>(hi));
+    }
   }
 }
 
@@ -177,7 +188,7 @@ struct EpiSchurF32 {
 
 template <int MAXB, bool kBF16>
 cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
-                         int kpad, const int32_t* status, cudaStream_t s) {
+                         int kpad, int nsl, const int32_t* status, cudaStream_t s) {
   using T = typename OpType<kBF16>::T;
   const int col_tiles = (n + kCols - 1) / kCols;
   const int grid = col_tiles + 64;
@@ -185,27 +196,35 @@ cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float
   auto k = row_panel_mixed_kernel<MAXB, kBF16>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, 256, smem, s>>>(X, ldx, n, o, b, Pinv, static_cast<T*>(U), static_cast<T*>(Vt), kpad, status,
+  k<<<grid, 256, smem, s>>>(X, ldx, n, o, b, Pinv, static_cast<T*>(U), static_cast<T*>(Vt), kpad, nsl, status,
                             col_tiles);
   return cudaGetLastError();
 }
 
 template <bool kBF16>
 cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
-                             int kpad, const int32_t* status, cudaStream_t s) {
-  if (b <= 64) return launch_panel<64, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
-  if (b <= 128) return launch_panel<128, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
-  if (b <= 256) return launch_panel<256, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
-  if (b <= 512) return launch_panel<512, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, status, s);
+                             int kpad, int nsl, const int32_t* status, cudaStream_t s) {
+  if (b <= 64) return launch_panel<64, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
+  if (b <= 128) return launch_panel<128, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
+  if (b <= 256) return launch_panel<256, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
+  if (b <= 512) return launch_panel<512, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
   return cudaErrorInvalidValue;
 }
 
 template <tc::Kind K>
 cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float* X, int64_t ldx, int n, int o,
-                            int b, int32_t* status, cudaStream_t s) {
+                            int b, int kpad, int nsl, int32_t* status, cudaStream_t s) {
   constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
   const int kb = (b + BK - 1) / BK;
   tc::KMap km = tc::plain_kmap(kb);
+  if (nsl > 1) {  // hi*hi + hi*lo + lo*hi
+    km.kb_per_pair = kb;
+    km.slice_cols = kpad;
+    km.kblocks = 3 * kb;
+    km.pa[0] = 0; km.pb[0] = 0;
+    km.pa[1] = 0; km.pb[1] = 1;
+    km.pa[2] = 1; km.pb[2] = 0;
+  }
   EpiSchurF32 epi{X, ldx, n, o, b, status};
   return tc::launch_gemm<K>(tU, tV, n, n, km, epi, status, s);
 }
@@ -224,16 +243,16 @@ cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64
 
 int mixed_kpad(int bmax) { return (bmax + 63) / 64 * 64; }
 
-cudaError_t mixed_elimination(const Plan& mp, bool bf16, float* X32, int64_t ld32, float* Pinv, void* U,
+cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, int32_t* status, cudaStream_t s) {
   const int n = mp.n;
   const int kpad = mixed_kpad(mp.bmax);
   const int eb = bf16 ? 2 : 4;
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const uint32_t BK = 128 / eb;
+  const uint64_t w = (uint64_t)nsl * kpad;
   CUtensorMap tU, tV;
-  if (!make_tmap_2d(&tU, U, dt, kpad, n, (uint64_t)kpad * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tV, Vt, dt, kpad, n, (uint64_t)kpad * eb, BK, tc::kBN))
+  if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) || !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   for (size_t k = 0; k < mp.sizes.size() && e == cudaSuccess; ++k) {
@@ -246,15 +265,15 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, float* X32, int64_t ld3
     if (e != cudaSuccess) break;
     {
       TraceScope t("row_panel_mixed", 2.0 * bd * bd * rest, 4.0 * (2.0 * bd * nd + bd * bd + rest * bd) + eb * 2.0 * nd * kpad, s);
-      e = bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, status, s)
-               : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, status, s);
+      e = bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s)
+               : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
     }
     if (e != cudaSuccess || n == b) continue;
     {
-      TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * rest * nd,
-                     4.0 * 2.0 * rest * nd + eb * 2.0 * nd * bd, s);
-      e = bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, status, s)
-               : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, status, s);
+      TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * rest * nd * (nsl > 1 ? 3 : 1),
+                     4.0 * 2.0 * rest * nd + eb * 2.0 * nd * bd * nsl, s);
+      e = bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s)
+               : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s);
     }
   }
   return e;

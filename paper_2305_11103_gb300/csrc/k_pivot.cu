@@ -24,6 +24,8 @@
 // Errors: a non-finite entry in the block gives BLOCKINV_ERR_NONFINITE; a
 // column whose candidates are all exactly zero gives BLOCKINV_ERR_SINGULAR;
 // the first error is kept in the device status word with the block index.
+// The pivot row is scaled by multiplying with the correctly rounded
+// reciprocal of the pivot (within an ulp of dividing; exact for unit pivots).
 #include <climits>
 #include <cooperative_groups.h>
 
@@ -58,6 +60,11 @@ __device__ __forceinline__ P* peer(P* p, int rank) {
 __device__ __forceinline__ void set_status(int32_t* status, int code, int block) {
   if (atomicCAS(&status[0], 0, code) == 0) status[1] = block;
 }
+
+// Correctly rounded reciprocal; a column is scaled by multiplying with it (a
+// full IEEE division per element is a long instruction sequence).
+__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
 
 template <typename T>
 __device__ __forceinline__ void argmax_step(T& bv, int& bi, T ov, int oi) {
@@ -173,8 +180,8 @@ __device__ __forceinline__ void pivot_gj_body(const T* __restrict__ P, int64_t l
     const int p = gi;
     const int owner = p / R;
     const T* prem = peer<kCluster>(rows, owner) + (size_t)(p - owner * R) * b;
-    const T piv = prem[c];
-    for (int j = tid; j < b; j += kPivotThreads) prow[j] = (j == c) ? T(1) / piv : prem[j] / piv;
+    const T inv = recip(prem[c]);
+    for (int j = tid; j < b; j += kPivotThreads) prow[j] = (j == c) ? inv : prem[j] * inv;
     for (int r = tid; r < nloc; r += kPivotThreads) fvec[r] = rows[(size_t)r * b + c];
     if (tid == 0) {
       perm[c] = p;
@@ -233,6 +240,273 @@ pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count) {
                                it.status, it.k);
 }
 
+// ------------------------------------------------------------------------
+// Panel-blocked variant for FP32 blocks of order 65..512. The columns are cut
+// into panels of 32, dealt round-robin to the CTAs of a cluster (each CTA
+// keeps its columns for all rows, column-major). For panel k, its owner runs
+// the 32 Gauss-Jordan steps restricted to the panel's columns (partial
+// pivoting over all unused rows; CTA barriers only). After one cluster
+// barrier every CTA copies the panel and its 32 pivot rows and applies the
+// combined effect of the 32 steps to its own other columns as one rank-32
+// update:
+//
+//   P[r, j] <- (r a pivot row of the panel ? 0 : P[r, j]) + sum_l Panel[r, l] P_old[R_l, j]
+//
+// which equals performing the 32 steps on those columns. So a 256-block takes
+// 8 cluster barriers instead of 256; the sequential column steps run inside
+// one CTA.
+constexpr int kPanel = 32;
+
+template <typename T>
+struct BlockedSmem {
+  T* cols;      // ncl x b, column-major
+  T* panel;     // kPanel x b, column-major: copy of the current panel
+  T* pr;        // ncl x kPanel: old pivot rows restricted to my columns
+  T* prow;      // kPanel
+  T* wv;        // 8 warp candidates
+  int* wi;      // 8
+  int* perm;    // b: pivot row of each global column
+  int* srow;    // b: column at which each row was the pivot (-1: not yet)
+  unsigned char* inpanel;  // b
+  int* flags;   // [0] non-finite seen, [1] singular, [2] non-finite pivot
+};
+
+template <typename T>
+__device__ __forceinline__ BlockedSmem<T> blocked_layout(unsigned char* raw, int b, int ncl) {
+  BlockedSmem<T> m;
+  m.cols = reinterpret_cast<T*>(raw);
+  m.panel = m.cols + (size_t)ncl * b;
+  m.pr = m.panel + (size_t)kPanel * b;
+  m.prow = m.pr + (size_t)ncl * kPanel;
+  m.wv = m.prow + kPanel;
+  m.wi = reinterpret_cast<int*>(m.wv + 8);
+  m.perm = m.wi + 8;
+  m.srow = m.perm + b;
+  m.flags = m.srow + b;
+  m.inpanel = reinterpret_cast<unsigned char*>(m.flags + 4);
+  return m;
+}
+
+template <typename T, bool kCluster>
+__global__ void __launch_bounds__(kPivotThreads, 1)
+pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __restrict__ out, int64_t ldo,
+                     int32_t* status, int block_index) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockedSmem<T> m = blocked_layout<T>(smem_raw, b, ncl);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int rank = 0, nranks = 1;
+  if constexpr (kCluster) {
+    rank = (int)cg::this_cluster().block_rank();
+    nranks = (int)cg::this_cluster().num_blocks();
+  }
+  const int npanels = (b + kPanel - 1) / kPanel;
+  // load my panels' columns (rows read coalesced, stored column-major)
+  int bad = 0;
+  for (int k = rank, slot = 0; k < npanels; k += nranks, ++slot) {
+    const int w = min(kPanel, b - k * kPanel);
+    for (int e = tid; e < kPanel * b; e += kPivotThreads) {
+      const int r = e / kPanel, l = e - r * kPanel;
+      if (l < w) {
+        const T v = P[(int64_t)r * ldp + k * kPanel + l];
+        if (!isfinite(v)) bad = 1;
+        m.cols[(size_t)(slot * kPanel + l) * b + r] = v;
+      }
+    }
+  }
+  for (int r = tid; r < b; r += kPivotThreads) {
+    m.srow[r] = -1;
+    m.inpanel[r] = 0;
+  }
+  if (tid < 4) m.flags[tid] = 0;
+  __syncthreads();
+  if (bad) atomicOr(&m.flags[0], 1);
+  const int prior = *(volatile int32_t*)&status[0];
+  cluster_or_block_sync<kCluster>();
+  int anybad = 0;
+  for (int q = 0; q < nranks; ++q) anybad |= *peer<kCluster>(&m.flags[0], q);
+  if (anybad || prior != 0) {
+    if (anybad && prior == 0 && rank == 0 && tid == 0) set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
+    cluster_or_block_sync<kCluster>();
+    return;
+  }
+  const int r0 = tid, r1 = tid + kPivotThreads;  // rows of this thread (b <= 512)
+  int failed = 0;
+  for (int k = 0; k < npanels; ++k) {
+    const int owner = k % nranks, kslot = k / nranks;
+    const int w = min(kPanel, b - k * kPanel);
+    if (rank == owner) {
+      // Gauss-Jordan on the panel's w columns with this thread's rows in
+      // registers (x0: row r0, x1: row r1); two CTA barriers per column.
+      T* pc = m.cols + (size_t)kslot * kPanel * b;
+      T x0[kPanel], x1[kPanel];
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l) {
+        x0[l] = (l < w && r0 < b) ? pc[(size_t)l * b + r0] : T(0);
+        x1[l] = (l < w && r1 < b) ? pc[(size_t)l * b + r1] : T(0);
+      }
+      bool free0 = r0 < b && m.srow[r0] < 0;
+      bool free1 = r1 < b && m.srow[r1] < 0;
+      bool stop = false;
+#pragma unroll
+      for (int c = 0; c < kPanel; ++c) {
+        if (c < w && !stop) {
+          T bv = T(-1);
+          int bi = INT_MAX;
+          if (free0) {
+            bv = fabs(x0[c]);
+            bi = r0;
+          }
+          if (free1) argmax_step(bv, bi, T(fabs(x1[c])), r1);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            argmax_step(bv, bi, ov, oi);
+          }
+          if (lane == 0) {
+            m.wv[warp] = bv;
+            m.wi[warp] = bi;
+          }
+          __syncthreads();
+          T gv = (lane < 8) ? m.wv[lane] : T(-1);
+          int gi = (lane < 8) ? m.wi[lane] : INT_MAX;
+#pragma unroll
+          for (int off = 4; off > 0; off >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, gv, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, gi, off);
+            argmax_step(gv, gi, ov, oi);
+          }
+          gv = __shfl_sync(0xffffffffu, gv, 0);
+          gi = __shfl_sync(0xffffffffu, gi, 0);
+          if (gi == INT_MAX || !(gv > T(0)) || !isfinite(gv)) {
+            if (tid == 0) m.flags[(gi == INT_MAX || !(gv > T(0))) ? 1 : 2] = 1;
+            stop = true;
+          } else {
+            const int p = gi;
+            if (p == r0 || p == r1) {  // the thread holding the pivot row publishes it, scaled
+              const bool h = (p == r1);
+              const T inv = recip(h ? x1[c] : x0[c]);
+#pragma unroll
+              for (int l = 0; l < kPanel; ++l)
+                if (l < w) m.prow[l] = (l == c) ? inv : (h ? x1[l] : x0[l]) * inv;
+              m.perm[k * kPanel + c] = p;
+              m.srow[p] = k * kPanel + c;
+            }
+            __syncthreads();
+            const T f0 = x0[c], f1 = x1[c];
+#pragma unroll
+            for (int l = 0; l < kPanel; ++l) {
+              const T pl = m.prow[l];
+              x0[l] = (r0 == p) ? pl : ((l == c) ? T(0) : x0[l]) - f0 * pl;
+              x1[l] = (r1 == p) ? pl : ((l == c) ? T(0) : x1[l]) - f1 * pl;
+            }
+            free0 = free0 && r0 != p;
+            free1 = free1 && r1 != p;
+          }
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l) {
+        if (l < w && r0 < b) pc[(size_t)l * b + r0] = x0[l];
+        if (l < w && r1 < b) pc[(size_t)l * b + r1] = x1[l];
+      }
+      __syncthreads();
+    }
+    cluster_or_block_sync<kCluster>();
+    // everyone: pivot rows and panel of step k from the owner
+    const int* rflags = peer<kCluster>(m.flags, owner);
+    if (rflags[1] || rflags[2]) {
+      failed = rflags[1] ? BLOCKINV_ERR_SINGULAR : BLOCKINV_ERR_NONFINITE;
+      break;
+    }
+    const int* rperm = peer<kCluster>(m.perm, owner);
+    const T* rpanel = peer<kCluster>(m.cols, owner) + (size_t)kslot * kPanel * b;
+    if (tid < w) {
+      const int rr = rperm[k * kPanel + tid];
+      m.perm[k * kPanel + tid] = rr;
+      m.srow[rr] = k * kPanel + tid;
+      m.inpanel[rr] = 1;
+    }
+    for (int e = tid; e < w * b; e += kPivotThreads) m.panel[e] = rpanel[e];
+    __syncthreads();
+    // old pivot rows in my columns outside the panel
+    const int my_cols = ncl;
+    for (int e = tid; e < my_cols * kPanel; e += kPivotThreads) {
+      const int lc = e / kPanel, l = e - lc * kPanel;
+      m.pr[e] = (l < w) ? m.cols[(size_t)lc * b + m.perm[k * kPanel + l]] : T(0);
+    }
+    __syncthreads();
+    // rank-w update of my columns (skipping the panel itself on the owner)
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int r = h ? r1 : r0;
+      if (r >= b) continue;
+      T pv[kPanel];
+#pragma unroll
+      for (int l = 0; l < kPanel; ++l) pv[l] = (l < w) ? m.panel[(size_t)l * b + r] : T(0);
+      const bool piv_row = m.inpanel[r] != 0;
+      for (int lc = 0; lc < my_cols; ++lc) {
+        const int gk = (lc / kPanel) * nranks + rank;  // global panel of this local column
+        if (gk >= npanels || (rank == owner && gk == k)) continue;
+        if ((lc % kPanel) >= min(kPanel, b - gk * kPanel)) continue;
+        T acc = piv_row ? T(0) : m.cols[(size_t)lc * b + r];
+        const T* prc = m.pr + (size_t)lc * kPanel;
+        if constexpr (sizeof(T) == 4) {
+          const float4* p4 = reinterpret_cast<const float4*>(prc);
+#pragma unroll
+          for (int q = 0; q < kPanel / 4; ++q) {
+            const float4 v = p4[q];
+            acc += pv[4 * q] * v.x + pv[4 * q + 1] * v.y + pv[4 * q + 2] * v.z + pv[4 * q + 3] * v.w;
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < kPanel; ++l) acc += pv[l] * prc[l];
+        }
+        m.cols[(size_t)lc * b + r] = acc;
+      }
+    }
+    __syncthreads();
+    if (tid < w) m.inpanel[m.perm[k * kPanel + tid]] = 0;
+    __syncthreads();
+  }
+  // after this barrier nobody reads another CTA's shared memory
+  cluster_or_block_sync<kCluster>();
+  if (failed) {
+    if (rank == 0 && tid == 0) set_status(status, failed, block_index);
+    return;
+  }
+  for (int k = rank, slot = 0; k < npanels; k += nranks, ++slot) {
+    const int w = min(kPanel, b - k * kPanel);
+    for (int l = 0; l < w; ++l) {
+      const int gc = k * kPanel + l;
+      const T* col = m.cols + (size_t)(slot * kPanel + l) * b;
+      for (int r = tid; r < b; r += kPivotThreads) out[(int64_t)m.srow[r] * ldo + m.perm[gc]] = col[r];
+    }
+  }
+}
+
+size_t blocked_smem_bytes(int b, int ncl, int elem) {
+  return (size_t)elem * ((size_t)ncl * b + (size_t)kPanel * b + (size_t)ncl * kPanel + kPanel + 8) +
+         sizeof(int) * (8 + 2 * (size_t)b + 4) + b + 64;
+}
+
+// Cluster size for the blocked kernel: the fewest CTAs (1, 2, 4, 8) whose
+// columns fit in 225 KiB of shared memory each.
+bool plan_blocked(int b, int elem, int* ctas, int* ncl, size_t* smem) {
+  const int npanels = (b + kPanel - 1) / kPanel;
+  for (int c = 1; c <= 8; c *= 2) {
+    const int per = (npanels + c - 1) / c;
+    const size_t bytes = blocked_smem_bytes(b, per * kPanel, elem);
+    if (bytes <= 225 * 1024) {
+      *ctas = c;
+      *ncl = per * kPanel;
+      *smem = bytes;
+      return true;
+    }
+  }
+  return false;
+}
+
 size_t pivot_smem_bytes(int b, int R, int elem) {
   size_t t = (size_t)R * b + b + R + 2;            // T arrays
   size_t i = 2 + (size_t)R + b + 1;                // int arrays
@@ -276,8 +550,50 @@ bool plan_pivot(int b, int elem_bytes, PivotPlan* plan) {
 }
 
 template <typename T>
+cudaError_t launch_pivot_blocked(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo, int32_t* status,
+                                 int block_index, cudaStream_t s, bool* done) {
+  *done = false;
+  int ctas = 0, ncl = 0;
+  size_t smem = 0;
+  if (!plan_blocked(b, (int)sizeof(T), &ctas, &ncl, &smem)) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas, 1, 1);
+  cfg.blockDim = dim3(kPivotThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  cudaError_t e;
+  if (ctas > 1) {
+    auto k = pivot_blocked_kernel<T, true>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, P, ldp, b, ncl, Pinv, ldo, status, block_index);
+  } else {
+    auto k = pivot_blocked_kernel<T, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchKernelEx(&cfg, k, P, ldp, b, ncl, Pinv, ldo, status, block_index);
+  }
+  *done = (e == cudaSuccess);
+  return e;
+}
+
+template <typename T>
 cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
                                  int32_t* status, int block_index, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (b > 64) {
+      bool done = false;
+      cudaError_t e = launch_pivot_blocked<T>(P, ldp, b, Pinv, ldo, status, block_index, s, &done);
+      if (e != cudaSuccess || done) return e;
+    }
+  }
   PivotPlan plan;
   if (!plan_pivot(b, (int)sizeof(T), &plan)) return cudaErrorInvalidValue;
   int jw = 1, jlog = 0;

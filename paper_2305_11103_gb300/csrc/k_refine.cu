@@ -50,6 +50,7 @@ namespace blockinv {
 namespace {
 
 constexpr int kLog2Digit = 4;
+constexpr int kFirstResidualGroups = 7;
 
 struct Ctl {
   int32_t done;        // refinement finished (converged or gave up)
@@ -282,6 +283,12 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(u);
 }
 
+// 2^e for -1022 <= e <= 1023 from its bit pattern (exact); 0 below.
+__device__ __forceinline__ double pow2(int e) {
+  if (e < -1022) return 0.0;
+  return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+}
+
 // E = I - a_ii x_ij - [i != j] a_ij x_jj - 2^(e_i + f_j - 8 - 4 (S - 1)) T;
 // ||E||^2; E^T split into TF32 hi/lo (rows j of Eop, columns i and Kp + i);
 // optionally E itself in FP64.
@@ -303,7 +310,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     if (i < n && j < n) {
       const int ex = rexp[i] + cexp[j] - 8 - kLog2Digit * (S - 1);
       const long long t = T[(int64_t)i * ldt + j];
-      const double r = (t == 0) ? 0.0 : ldexp(static_cast<double>(t), ex);
+      const double r = (t == 0) ? 0.0 : static_cast<double>(t) * pow2(ex);
       const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
       if (i == j) {
         e = (1.0 - dx) - r;
@@ -355,17 +362,21 @@ __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n,
   }
 }
 
-// rho for residual `it`; decides whether refinement goes on.
+// rho for residual `it`; decides whether refinement goes on. A residual with
+// fewer digit groups (can_accept == 0) may continue the iteration but never
+// declare convergence.
 __global__ void decide_kernel(const double* sums, int it, double tol, int max_updates, double* hist, Ctl* ctl,
-                              const int32_t* status) {
+                              const int32_t* status, int can_accept) {
   if (ctl->done || *status != 0) return;
   const double a2 = sums[0], e2 = sums[1 + 2 * it], x2 = sums[2 + 2 * it];
   const double rho = sqrt(e2) / (sqrt(a2) * sqrt(x2));
   hist[it] = rho;
   ctl->last = it;
-  if (rho <= tol) {
+  if (rho <= tol && can_accept) {
     ctl->done = 1;
     ctl->code = BLOCKINV_OK;
+  } else if (!can_accept && it < max_updates && rho == rho) {
+    ctl->updates = it + 1;
   } else if (it >= max_updates || !(rho == rho) || (it > 0 && !(rho < 0.25 * hist[it - 1]))) {
     ctl->done = 1;
     ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
@@ -492,7 +503,11 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
                           status, s);
     }
-    for (int g = 0; g < S && e == cudaSuccess; ++g) {
+    // The first residual only steers the first update (its error is squared
+    // away by the next one), so it keeps fewer digit groups; every later
+    // residual, including the final check, keeps all S.
+    const int groups = (it == 0 && max_updates > 0) ? std::min(S, kFirstResidualGroups) : S;
+    for (int g = 0; g < groups && e == cudaSuccess; ++g) {
       tc::KMap km{};
       km.kb_per_pair = Kp / 128;
       km.slice_cols = Kp;
@@ -501,7 +516,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
         km.pa[p] = (int8_t)p;
         km.pb[p] = (int8_t)(g - p);
       }
-      EpiAccumI64 epi{T, ldt, n, kLog2Digit * (S - 1 - g), g == 0 ? 1 : 0, ctl, status};
+      EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), g == 0 ? 1 : 0, ctl, status};
       TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * (g + 1), (double)(g + 1) * 2.0 * nd * Kp + 16.0 * nd * nd, s);
       e = tc::launch_gemm<tc::Kind::E4M3>(tAs, tXs, n, n, km, epi, status, s);
     }
@@ -509,11 +524,11 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     {
       TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 8.0 * nd * nd : 0.0), s);
       dim3 g((n + 31) / 32, (n + 31) / 32);
-      finalize_kernel<<<g, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
+      finalize_kernel<<<g, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, groups, &sums[1 + 2 * it],
                                         it < max_updates ? Eop : nullptr, Kp,
                                         (max_updates == 0) ? Eout : nullptr, lde, ctl, status);
     }
-    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status);
+    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status, groups == S ? 1 : 0);
     if (it == max_updates) break;
     if (host_steps) {
       // Blocking callers stop enqueueing as soon as the device has decided.

@@ -104,8 +104,9 @@ def test_refined_mixed_meets_gate(bi, mode, n, sizes, kind):
     Xo = oracle.block_inverse(A, sizes)
     kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
     assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
-    # the GPU's own rho agrees with the one measured here
-    assert abs(info.rho - r) <= 0.05 * r + 1e-16
+    # the GPU's own rho agrees with the one measured here, down to the
+    # rounding floor of evaluating A X - I in FP64 (about sqrt(n) u)
+    assert abs(info.rho - r) <= 0.05 * r + 20 * np.sqrt(n) * U64
 
 
 def test_poorly_conditioned_sigma_105(bi):

@@ -103,7 +103,8 @@ def mixed_unrefined(bi, A, sizes, mode):
 
 
 @pytest.mark.parametrize("mode,tol", [("tf32", 2e-3), ("bf16", 3e-2)])
-@pytest.mark.parametrize("sizes", [[256] * 4, [100, 157, 63], [64] * 5 + [37], [512, 300]])
+@pytest.mark.parametrize("sizes", [[256] * 4, [100, 157, 63], [64] * 5 + [37], [512, 300], [129], [256], [300, 33],
+                                   [512], [65, 97]])
 def test_mixed_elimination_vs_oracle(bi, mode, tol, sizes):
     n = sum(sizes)
     A = inputs.gaussian_shifted(n, 3 + n, sigma=1.5)
@@ -153,3 +154,19 @@ def test_accumulator_exact_near_2_24(bi, kind, big_a, big_b, K):
     C = run_gemm(bi, kind, tA, tB).cpu().numpy().astype(np.int64)
     bad = np.count_nonzero(C != expect)
     assert bad == 0, f"{bad} inexact outputs; max error {np.abs(C - expect).max()}"
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_split_operands_tighten_unrefined_inverse(bi, mode):
+    """hi + lo operand splitting (three products) must give a clearly smaller
+    residual than one product before any refinement."""
+    n = 1024
+    A = inputs.gaussian_shifted(n, 81, sigma=1.5)
+    rhos = []
+    for split in (1, 2):
+        d = torch.from_numpy(A).cuda()
+        st, info = bi.blockinv_invert_ex(n, [256] * 4, d.data_ptr(), n, mode, None, max_refine=0, split=split)
+        assert st == bi.OK
+        X = d.cpu().numpy()
+        rhos.append(np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X)))
+    assert rhos[1] < 0.1 * rhos[0], rhos
