@@ -120,7 +120,7 @@ int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda
                            cudaStream_t s);
 
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
-constexpr int kResidualSlices = 12;
+constexpr int kResidualSlices = 11;
 size_t refine_workspace_bytes(int n, int S, int max_updates);
 cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,

@@ -29,7 +29,8 @@
 // Dropped groups (p + q >= S) and truncated digits leave an error of order
 // 2^(-4S - 8) S sqrt(K) relative to the row and column scales.
 //
-// The update X += X E uses split TF32 operands (hi + lo for X and E, the
+// Both products run on the cluster-of-two GEMM that multicasts the shared B
+// tile. The update X += X E uses split TF32 operands (hi + lo for X and E, the
 // three products hi*hi + hi*lo + lo*hi) with the FP32 accumulator added to
 // the FP64 X in the epilogue; E is small, so the correction needs far fewer
 // bits than X itself.
@@ -485,9 +486,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
 
   CUtensorMap tAs, tXs, tXo, tEo;
   if (!make_tmap_2d(&tAs, Asl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBM) ||
-      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN) ||
+      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN / 2) ||
       !make_tmap_2d(&tXo, Xop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBM) ||
-      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN))
+      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN / 2))
     return cudaErrorInvalidValue;
 
   const double nd = n;
@@ -518,7 +519,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       }
       EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), g == 0 ? 1 : 0, ctl, status};
       TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * (g + 1), (double)(g + 1) * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-      e = tc::launch_gemm<tc::Kind::E4M3>(tAs, tXs, n, n, km, epi, status, s);
+      e = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
     }
     if (e != cudaSuccess) break;
     {
@@ -552,7 +553,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       km.pa[2] = 1; km.pb[2] = 0;
       EpiAddF64 epi{X, ldx, n, ctl, status};
       TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd + 16.0 * nd * Kp, s);
-      e = tc::launch_gemm<tc::Kind::TF32>(tXo, tEo, n, n, km, epi, status, s);
+      e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true>(tXo, tEo, n, n, km, epi, status, s);
     }
   }
   if (e == cudaSuccess && report) {

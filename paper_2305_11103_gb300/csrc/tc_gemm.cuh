@@ -6,7 +6,9 @@
 //
 //   warp 0, lane 0   TMA producer            (also allocates/frees TMEM)
 //   warp 1, lane 0   MMA issuer
-//   warps 2..5       epilogue, one TMEM lane quarter each
+//   warps 2..9       epilogue: two warps per TMEM lane quarter, each taking
+//                    half of the tile's columns (more loads in flight for
+//                    the memory-bound epilogues)
 //
 // While the epilogue drains accumulator a, the MMA warp fills the other one,
 // so the C traffic of one tile overlaps the loads and MMAs of the next.
@@ -18,6 +20,13 @@
 //
 // Every mbarrier wait is bounded; on timeout the status word gets
 // BLOCKINV_ERR_TIMEOUT and the roles wind down.
+//
+// With kMC (TMA multicast) the kernel runs in clusters of two CTAs that own
+// vertically adjacent tiles with the same columns: each CTA loads its own A
+// tile and one half of the shared B tile, multicast into both CTAs, so the
+// L2 reads of B are halved. A stage is reused only after both CTAs' MMAs
+// released it (the MMA warp commits to the empty barriers of both CTAs); the
+// producer drains those releases at the end and the pair leaves together.
 #pragma once
 #include "internal.h"
 #include "tc_common.cuh"
@@ -28,7 +37,8 @@ namespace tc {
 constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kStages = 4;
-constexpr int kGemmThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr int kStageBytes = kBM * 128 + kBN * 128;
 
 constexpr int kMaxPairs = 16;
@@ -63,7 +73,7 @@ __device__ __forceinline__ void flag_timeout(int32_t* status) {
   if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
 }
 
-template <Kind K, class Epi>
+template <Kind K, class Epi, bool kMC = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int tiles_m,
             int tiles_n, KMap km, Epi epi, int32_t* status) {
@@ -74,8 +84,13 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   GemmShared* sh = reinterpret_cast<GemmShared*>(smem + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int ntiles = tiles_m * tiles_n;
-  if (epi.skip()) return;  // an earlier kernel of this computation failed
+  // Work items: single tiles, or (kMC) pairs of vertically adjacent tiles per cluster.
+  const int tiles_mp = kMC ? (tiles_m + 1) / 2 : tiles_m;
+  const int ntiles = tiles_mp * tiles_n;
+  const int rank = kMC ? (int)cluster_ctarank() : 0;
+  const int first = kMC ? (int)cluster_id_x() : (int)blockIdx.x;
+  const int stride = kMC ? (int)cluster_count_x() : (int)gridDim.x;
+  if (epi.skip()) return;  // an earlier kernel of this computation failed (uniform over the grid)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -84,8 +99,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&sh->tfull[a], 1);
-      mbar_init(&sh->tempty[a], 128);
+      mbar_init(&sh->tempty[a], 32 * kEpiWarps);
     }
+    if (kMC)
+      for (int s2 = 0; s2 < kStages; ++s2) mbar_init(&sh->empty[s2], 2);  // released by both CTAs
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -94,6 +111,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   fence_before_sync();
   __syncthreads();
+  if (kMC) cluster_sync_all();  // peers may target our barriers only after they exist
   fence_after_sync();
   const uint32_t tmem = sh->tmem_base;
 
@@ -102,8 +120,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     prefetch_tmap(&tmB);
     uint32_t it = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int m0 = (t / tiles_n) * kBM;
+    for (int t = first; t < ntiles && ok; t += stride) {
+      const int m0 = (kMC ? 2 * (t / tiles_n) + rank : t / tiles_n) * kBM;
       const int n0 = (t % tiles_n) * kBN;
       for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
         const int s = it % kStages;
@@ -118,11 +136,20 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int pair = kb / km.kb_per_pair;
         const int kk = kb - pair * km.kb_per_pair;
         tma_load_2d(sa, &tmA, &sh->full[s], km.pa[pair] * km.slice_cols + kk * BK, m0);
-        tma_load_2d(sb, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK, n0);
+        if (kMC) {
+          tma_load_2d_mc(sb + rank * (kBN / 2) * 128, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK,
+                         n0 + rank * (kBN / 2), 0x3);
+        } else {
+          tma_load_2d(sb, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK, n0);
+        }
       }
     }
     if (!ok) {
       flag_timeout(status);
+    } else if (kMC) {
+      // Drain: every stage released by both CTAs, so no late arrival targets a
+      // barrier of a CTA that has left (bounded).
+      for (int d = 0; d < kStages; ++d, ++it) mbar_wait(&sh->empty[it % kStages], ((it / kStages) & 1) ^ 1);
     } else if (it > 0) {
       // Let the last copies land before the CTA can leave (bounded).
       const uint32_t last = it - 1;
@@ -132,7 +159,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     constexpr uint32_t id = idesc<K>(kBM, kBN);
     uint32_t it = 0, tl = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+    for (int t = first; t < ntiles && ok; t += stride, ++tl) {
       const uint32_t a = tl & 1;
       const uint32_t aph = (tl >> 1) & 1;
       if (!mbar_wait(&sh->tempty[a], aph ^ 1)) {
@@ -155,7 +182,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)  // 4 x 32 bytes of K per 128-byte row
           mma<K>(d, da + 2 * ks, db + 2 * ks, id, (kb | ks) != 0 ? 1u : 0u);
-        mma_commit(&sh->empty[s]);
+        if (kMC)
+          mma_commit_mc(&sh->empty[s], 0x3);
+        else
+          mma_commit(&sh->empty[s]);
       }
       if (!ok) break;
       mma_commit(&sh->tfull[a]);
@@ -163,8 +193,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     if (!ok) flag_timeout(status);
   } else if (warp >= 2) {
     const int q = warp & 3;  // the TMEM lane quarter this warp may access
+    const int half = (warp - 2) / 4;
     uint32_t tl = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+    for (int t = first; t < ntiles; t += stride, ++tl) {
       const uint32_t a = tl & 1;
       const uint32_t aph = (tl >> 1) & 1;
       if (!mbar_wait(&sh->tfull[a], aph)) {
@@ -172,11 +203,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         break;
       }
       fence_after_sync();
-      const int m0 = (t / tiles_n) * kBM;
+      const int m0 = (kMC ? 2 * (t / tiles_n) + rank : t / tiles_n) * kBM;
       const int n0 = (t % tiles_n) * kBN;
       const int row = m0 + q * 32 + lane;
 #pragma unroll 1
-      for (int c = 0; c < kBN / 32; ++c) {
+      for (int c = half * (kBN / 64); c < (half + 1) * (kBN / 64); ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + c * 32, v);
         tmem_wait_ld();
@@ -187,6 +218,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
   }
   __syncthreads();
+  if (kMC) cluster_sync_all();  // the pair leaves together
   if (warp == 0) {
     fence_after_sync();
     tmem_dealloc(tmem, 2 * kBN);
@@ -195,20 +227,40 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
 int num_sms();
 
-template <Kind K, class Epi>
+// kMC: tB must have been made with a box of kBN / 2 rows (each CTA of a
+// pair loads half of the B tile).
+template <Kind K, class Epi, bool kMC = false>
 cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int N, KMap km, const Epi& epi,
                         int32_t* status, cudaStream_t s) {
   const int tiles_m = (M + kBM - 1) / kBM;
   const int tiles_n = (N + kBN - 1) / kBN;
   const int ntiles = tiles_m * tiles_n;
   if (ntiles == 0 || km.kblocks <= 0) return cudaSuccess;
-  auto kern = gemm_kernel<K, Epi>;
+  auto kern = gemm_kernel<K, Epi, kMC>;
   const size_t smem = gemm_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = ntiles < num_sms() ? ntiles : num_sms();
-  kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, km, epi, status);
-  return cudaGetLastError();
+  if (!kMC) {
+    const int grid = ntiles < num_sms() ? ntiles : num_sms();
+    kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, km, epi, status);
+    return cudaGetLastError();
+  }
+  const int pairs = ((tiles_m + 1) / 2) * tiles_n;
+  const int clusters = pairs < num_sms() / 2 ? pairs : num_sms() / 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * clusters, 1, 1);
+  cfg.blockDim = dim3(kGemmThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, km, epi, status);
+  return e;
 }
 
 }  // namespace tc
