@@ -120,33 +120,99 @@ int cuda_status(cudaError_t e) {
   return BLOCKINV_ERR_CUDA;
 }
 
+// Side stream per device for the look-ahead (highest priority, created once).
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!streams[dev]) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&streams[dev], cudaStreamNonBlocking, hi) != cudaSuccess) streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 // Enqueue the FP64 elimination of the whole matrix on stream s.
+//
+// Large problems use a one-step look-ahead: the Schur update of step k is
+// split into the elements of block row / column k + 1 (the next step's
+// panels) and the rest; as soon as the first part is done, the next pivot
+// inverse and row panel run on a high-priority side stream while the rest of
+// step k's update runs on s. The U panel is double-buffered.
 int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStream_t s) {
   const int n = pl.n;
+  const int p = (int)pl.sizes.size();
+  cudaStream_t t = (n >= 2048 && p >= 3) ? side_stream() : nullptr;
+  const bool ahead = t != nullptr;
   AsyncBuf pinv, ubuf;
   cudaError_t e = pinv.alloc(sizeof(double) * (size_t)pl.bmax * pl.bmax, s);
-  if (e == cudaSuccess) e = ubuf.alloc(sizeof(double) * (size_t)n * pl.bmax, s);
+  if (e == cudaSuccess) e = ubuf.alloc(sizeof(double) * (size_t)n * pl.bmax * (ahead ? 2 : 1), s);
   if (e != cudaSuccess) return cuda_status(e);
   double* Pinv = static_cast<double*>(pinv.ptr);
-  double* U = static_cast<double*>(ubuf.ptr);
-  for (size_t k = 0; k < pl.sizes.size(); ++k) {
-    const int o = pl.offs[k], b = pl.sizes[k];
-    const double bd = b, nd = n, rest = (double)(n - b);
-    {
-      TraceScope t("pivot_inverse_f64", 2.0 * bd * bd * bd, 16.0 * bd * bd, s);
-      e = launch_pivot_inverse<double>(A + (int64_t)o * lda + o, lda, b, Pinv, b, status, (int)k, s);
-    }
-    if (e == cudaSuccess) {
-      TraceScope t("row_panel_f64", 2.0 * bd * bd * rest, 8.0 * (2.0 * bd * nd + bd * bd + 2.0 * rest * bd), s);
-      e = launch_row_panel_f64(A, lda, n, o, b, Pinv, U, status, s);
-    }
-    if (e == cudaSuccess && n > b) {
-      TraceScope t("schur_update_f64", 2.0 * bd * rest * nd, 8.0 * (2.0 * rest * nd + rest * bd + bd * nd), s);
-      e = launch_schur_update_f64(A, lda, n, o, b, U, status, s);
-    }
+  double* Ub[2] = {static_cast<double*>(ubuf.ptr),
+                   static_cast<double*>(ubuf.ptr) + (ahead ? (size_t)n * pl.bmax : 0)};
+  EventPair ev;
+  if (ahead) {
+    e = cudaEventCreateWithFlags(&ev.a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev.b, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  return BLOCKINV_OK;
+  auto panels = [&](int k, cudaStream_t st) -> cudaError_t {
+    const int o = pl.offs[k], b = pl.sizes[k];
+    const double bd = b, nd = n, rest = (double)(n - b);
+    cudaError_t r;
+    {
+      TraceScope tr("pivot_inverse_f64", 2.0 * bd * bd * bd, 16.0 * bd * bd, st);
+      r = launch_pivot_inverse<double>(A + (int64_t)o * lda + o, lda, b, Pinv, b, status, k, st);
+    }
+    if (r == cudaSuccess) {
+      TraceScope tr("row_panel_f64", 2.0 * bd * bd * rest, 8.0 * (2.0 * bd * nd + bd * bd + 2.0 * rest * bd), st);
+      r = launch_row_panel_f64(A, lda, n, o, b, Pinv, Ub[k & 1], status, st);
+    }
+    return r;
+  };
+  e = panels(0, s);
+  for (int k = 0; k < p && e == cudaSuccess; ++k) {
+    const int o = pl.offs[k], b = pl.sizes[k];
+    const double bd = b, nd = n, rest = (double)(n - b);
+    double* U = Ub[k & 1];
+    if (n == b) break;
+    if (!ahead || k + 1 == p) {
+      TraceScope tr("schur_update_f64", 2.0 * bd * rest * nd, 8.0 * (2.0 * rest * nd + rest * bd + bd * nd), s);
+      e = launch_schur_update_f64(A, lda, n, o, b, U, status, s);
+      if (e == cudaSuccess && !ahead && k + 1 < p) e = panels(k + 1, s);
+      continue;
+    }
+    const int o1 = pl.offs[k + 1], b1 = pl.sizes[k + 1];
+    const double b1d = b1;
+    const double next_elems = b1d * nd + (rest - b1d) * b1d;
+    {
+      TraceScope tr("schur_update_f64", 2.0 * bd * next_elems, 8.0 * (2.0 * next_elems), s);
+      e = launch_schur_split_f64(A, lda, n, o, b, U, status, o1, b1, true, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev.a, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(t, ev.a, 0);
+    if (e == cudaSuccess) e = panels(k + 1, t);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.b, t);
+    if (e == cudaSuccess) {
+      const double rest_elems = rest * nd - next_elems;
+      TraceScope tr("schur_update_f64", 2.0 * bd * rest_elems, 8.0 * (2.0 * rest_elems + rest * bd + bd * nd), s);
+      e = launch_schur_split_f64(A, lda, n, o, b, U, status, o1, b1, false, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.b, 0);
+  }
+  return cuda_status(e);
 }
 
 struct Options {

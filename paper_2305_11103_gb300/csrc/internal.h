@@ -90,6 +90,11 @@ cudaError_t launch_row_panel_f64(double* X, int64_t ldx, int n, int o, int b,
 cudaError_t launch_schur_update_f64(double* X, int64_t ldx, int n, int o, int b,
                                     const double* U, const int32_t* status, cudaStream_t s);
 
+// K3 split for look-ahead: next_part = the elements of block row / column
+// B1 = [o1, o1 + b1) (the next step's panels); otherwise every other element.
+cudaError_t launch_schur_split_f64(double* X, int64_t ldx, int n, int o, int b, const double* U,
+                                   const int32_t* status, int o1, int b1, bool next_part, cudaStream_t s);
+
 // Residual pieces (FP64): partial sums of ||A X - I||_F^2, ||A||_F^2, ||X||_F^2.
 cudaError_t launch_residual_f64(int n, const double* A, int64_t lda, const double* X,
                                 int64_t ldx, double* sums3, cudaStream_t s);

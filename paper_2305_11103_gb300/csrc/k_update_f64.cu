@@ -135,8 +135,19 @@ row_panel_grouped_kernel(const GroupStep* __restrict__ items, int count, const i
 constexpr int kTile = 64;
 constexpr int kTileK = 8;
 
+// Write masks for the look-ahead split of one step's update (B1 = the rows /
+// columns of the next pivot block [o1, o1 + b1)):
+//   kAll   every element outside the pivot rows of this step
+//   kRest  elements with row and column outside B1
+//   kNextA elements with row in B1 or column in B1 (row tiles that meet B1)
+//   kNextB elements with column in B1 (row tiles that miss B1)
+enum WriteMask { kAll = 0, kRest = 1, kNextA = 2, kNextB = 3 };
+
+__device__ __forceinline__ bool in_range(int v, int lo, int len) { return v >= lo && v < lo + len; }
+
 __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, int n, int o, int b,
-                                           const double* __restrict__ U, int i0, int j0) {
+                                           const double* __restrict__ U, int i0, int j0, int o1 = 0, int b1 = 0,
+                                           int mask = kAll) {
   __shared__ __align__(16) double Us[kTileK][kTile];
   __shared__ __align__(16) double Vs[kTileK][kTile];
   const int tid = threadIdx.x;
@@ -180,15 +191,59 @@ __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, 
   for (int a = 0; a < 4; ++a) {
     const int i = i0 + ty * 4 + a;
     if (i >= n || (i >= o && i < o + b)) continue;
+    const bool ri = in_range(i, o1, b1);
     double* row = X + (int64_t)i * ldx;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
       const int j = j0 + tx * 4 + d;
       if (j >= n) continue;
+      const bool cj = in_range(j, o1, b1);
+      const bool write = mask == kAll || (mask == kRest && !ri && !cj) || (mask == kNextA && (ri || cj)) ||
+                         (mask == kNextB && cj);
+      if (!write) continue;
       const double base = (j >= o && j < o + b) ? 0.0 : row[j];
       row[j] = base - acc[a][d];
     }
   }
+}
+
+// Look-ahead part of step k: the elements of block row and block column
+// B1 = [o1, o1 + b1). Tiles: row tiles meeting B1 x all column tiles, then
+// the other row tiles x column tiles meeting B1 (disjoint element sets).
+__global__ void __launch_bounds__(256)
+schur_next_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b, const double* __restrict__ U,
+                      const int32_t* status, int o1, int b1) {
+  if (failed(status)) return;
+  const int tn = (n + kTile - 1) / kTile;
+  const int r_lo = o1 / kTile, r_hi = (o1 + b1 + kTile - 1) / kTile;
+  const int c_lo = r_lo, c_hi = r_hi;
+  const int part1 = (r_hi - r_lo) * tn;
+  int t = blockIdx.x;
+  if (t < part1) {
+    const int i0 = (r_lo + t / tn) * kTile, j0 = (t % tn) * kTile;
+    schur_tile(X, ldx, n, o, b, U, i0, j0, o1, b1, kNextA);
+    return;
+  }
+  t -= part1;
+  const int cw = c_hi - c_lo;
+  int rt = t / cw;
+  if (rt >= r_lo) rt += r_hi - r_lo;  // skip the row tiles of part 1
+  const int i0 = rt * kTile, j0 = (c_lo + t % cw) * kTile;
+  if (i0 >= o && i0 + kTile <= o + b) return;
+  schur_tile(X, ldx, n, o, b, U, i0, j0, o1, b1, kNextB);
+}
+
+// The rest of step k after the look-ahead part: elements outside B1.
+__global__ void __launch_bounds__(256)
+schur_rest_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b, const double* __restrict__ U,
+                      const int32_t* status, int o1, int b1) {
+  const int i0 = blockIdx.y * kTile;
+  const int j0 = blockIdx.x * kTile;
+  if (i0 >= o && i0 + kTile <= o + b) return;
+  if (i0 >= o1 && i0 + kTile <= o1 + b1) return;  // whole tile in the next pivot rows
+  if (j0 >= o1 && j0 + kTile <= o1 + b1) return;  // whole tile in the next pivot columns
+  if (failed(status)) return;
+  schur_tile(X, ldx, n, o, b, U, i0, j0, o1, b1, kRest);
 }
 
 __global__ void __launch_bounds__(256)
@@ -345,6 +400,20 @@ cudaError_t launch_schur_update_grouped(const GroupStep* items, int count, const
                                         int total_tiles, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return cudaSuccess;
   schur_update_grouped_kernel<<<total_tiles, 256, 0, s>>>(items, count, tile_start);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schur_split_f64(double* X, int64_t ldx, int n, int o, int b, const double* U,
+                                   const int32_t* status, int o1, int b1, bool next_part, cudaStream_t s) {
+  if (n == b) return cudaSuccess;
+  const int t = (n + kTile - 1) / kTile;
+  if (next_part) {
+    const int r_lo = o1 / kTile, r_hi = (o1 + b1 + kTile - 1) / kTile;
+    const int tiles = (r_hi - r_lo) * t + (t - (r_hi - r_lo)) * (r_hi - r_lo);
+    schur_next_f64_kernel<<<tiles, 256, 0, s>>>(X, ldx, n, o, b, U, status, o1, b1);
+  } else {
+    schur_rest_f64_kernel<<<dim3(t, t), 256, 0, s>>>(X, ldx, n, o, b, U, status, o1, b1);
+  }
   return cudaGetLastError();
 }
 

@@ -190,6 +190,32 @@ def test_gpu_residual_matches_numpy(bi):
     assert abs(r - rho(A, X)) <= 1e-3 * rho(A, X)
 
 
+# Look-ahead (n >= 2048 with 3 or more blocks): the next pivot inverse and row
+# panel run on a side stream while the rest of the current update runs. Each
+# element still sees the same operations in the same order, so the result must
+# equal, bit for bit, that of the plain step sequence, which the no-alloc entry
+# point runs (n <= 2048, blocks <= 256).
+@pytest.mark.parametrize("sizes", [[256] * 8, [200] * 10 + [48], [256] * 7 + [100, 92, 64], [1, 255] * 4 + [256] * 4])
+def test_look_ahead_matches_plain_sequence_bitwise(bi, sizes):
+    n = sum(sizes)
+    assert n == 2048
+    A = inputs.gaussian_shifted(n, 31, sigma=1.5)
+    ref = torch.from_numpy(A).cuda()
+    st, fb = bi.blockinv_invert_noalloc(n, sizes, ref.data_ptr(), n, None)
+    assert st == bi.OK
+    X = gpu_invert(bi, A, sizes)
+    assert np.array_equal(X, ref.cpu().numpy())
+
+
+@pytest.mark.parametrize("sizes", [[256] * 8 + [57], [300, 200, 500, 512, 512, 176], [100] * 21])
+def test_look_ahead_ragged_vs_oracle(bi, sizes):
+    n = sum(sizes)
+    A = inputs.diag_dominant_uniform(n, 41, shift=n)
+    X = gpu_invert(bi, A, sizes)
+    check(A, X, oracle.block_inverse(A, sizes))
+    assert np.array_equal(X, gpu_invert(bi, A, sizes))
+
+
 @pytest.mark.slow
 def test_full_size_8192(bi):
     """n = 8192, 32 x 32 grid of 256-blocks, N(0,1)/sqrt(n) + 1.5 I, seed 2 (the
