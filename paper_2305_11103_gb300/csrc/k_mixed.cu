@@ -160,28 +160,22 @@ struct EpiSchurF32 {
   int n, o, b;
   const int32_t* status;
   __device__ bool skip() const { return failed(status); }
-  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
-    if (row >= n || (row >= o && row < o + b)) return;
-    float* p = X + (int64_t)row * ldx + col0;
-    if (col0 + 32 <= n && (col0 + 32 <= o || col0 >= o + b)) {
+  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+    if (col >= n) return;
+    const bool pivot_col = col >= o && col < o + b;
+    float* p = X + (int64_t)row0 * ldx + col;
+    // all loads before any store, so the 32 reads are in flight together
+    float cur[32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float4 c = reinterpret_cast<float4*>(p)[q];
-        c.x -= __uint_as_float(v[4 * q + 0]);
-        c.y -= __uint_as_float(v[4 * q + 1]);
-        c.z -= __uint_as_float(v[4 * q + 2]);
-        c.w -= __uint_as_float(v[4 * q + 3]);
-        reinterpret_cast<float4*>(p)[q] = c;
-      }
-    } else {
+    for (int r = 0; r < 32; ++r) {
+      const int row = row0 + r;
+      const bool live = row < n && (row < o || row >= o + b);
+      cur[r] = (live && !pivot_col) ? p[(int64_t)r * ldx] : 0.f;
+    }
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int jj = col0 + q;
-        if (jj < n) {
-          const float base = (jj >= o && jj < o + b) ? 0.f : p[q];
-          p[q] = base - __uint_as_float(v[q]);
-        }
-      }
+    for (int r = 0; r < 32; ++r) {
+      const int row = row0 + r;
+      if (row < n && (row < o || row >= o + b)) p[(int64_t)r * ldx] = cur[r] - v[r];
     }
   }
 };

@@ -32,8 +32,8 @@
 // Both products run on the cluster-of-two GEMM that multicasts the shared B
 // tile. The update X += X E uses split TF32 operands (hi + lo for X and E, the
 // three products hi*hi + hi*lo + lo*hi) with the FP32 accumulator added to
-// the FP64 X in the epilogue; E is small, so the correction needs far fewer
-// bits than X itself.
+// the FP64 X in the epilogue, one K-chunk at a time; E is small, so the
+// correction needs far fewer bits than X itself.
 //
 // The iteration is stream-ordered: after each residual a one-thread kernel
 // computes rho = ||E||_F / (||A||_F ||X||_F), records it, and raises a device
@@ -43,6 +43,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "tc_gemm.cuh"
 
@@ -51,7 +52,7 @@ namespace blockinv {
 namespace {
 
 constexpr int kLog2Digit = 4;
-constexpr int kFirstResidualGroups = 7;
+constexpr int kUpdateChunkK = 2048;  // K elements per accumulator hand-off in the update
 
 struct Ctl {
   int32_t done;        // refinement finished (converged or gave up)
@@ -244,20 +245,18 @@ struct EpiAccumI64 {
   const Ctl* ctl;
   const int32_t* status;
   __device__ bool skip() const { return halted(ctl, status); }
-  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
-    if (row >= n) return;
-    long long* p = T + (int64_t)row * ldt + col0;
+  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+    if (col >= n) return;
+    long long* p = T + (int64_t)row0 * ldt + col;
+    // two halves of 16 rows: all loads of a half before its stores
 #pragma unroll
-    for (int q = 0; q < 32; q += 2) {
-      if (col0 + q + 1 < n) {
-        longlong2 cur = first ? make_longlong2(0, 0) : *reinterpret_cast<longlong2*>(p + q);
-        cur.x += static_cast<long long>(__float2ll_rn(__uint_as_float(v[q]))) << shift;
-        cur.y += static_cast<long long>(__float2ll_rn(__uint_as_float(v[q + 1]))) << shift;
-        *reinterpret_cast<longlong2*>(p + q) = cur;
-      } else if (col0 + q < n) {
-        const long long cur = first ? 0 : p[q];
-        p[q] = cur + (static_cast<long long>(__float2ll_rn(__uint_as_float(v[q]))) << shift);
-      }
+    for (int h = 0; h < 32; h += 16) {
+      long long cur[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) cur[r] = (!first && row0 + h + r < n) ? p[(int64_t)(h + r) * ldt] : 0;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (row0 + h + r < n) p[(int64_t)(h + r) * ldt] = cur[r] + (static_cast<long long>(__float2ll_rn(v[h + r])) << shift);
     }
   }
 };
@@ -269,12 +268,18 @@ struct EpiAddF64 {
   const Ctl* ctl;
   const int32_t* status;
   __device__ bool skip() const { return halted(ctl, status); }
-  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
-    if (row >= n) return;
-    double* p = X + (int64_t)row * ldx + col0;
+  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+    if (col >= n) return;
+    double* p = X + (int64_t)row0 * ldx + col;
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-      if (col0 + q < n) p[q] += static_cast<double>(__uint_as_float(v[q]));
+    for (int h = 0; h < 32; h += 16) {
+      double cur[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) cur[r] = (row0 + h + r < n) ? p[(int64_t)(h + r) * ldx] : 0.0;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (row0 + h + r < n) p[(int64_t)(h + r) * ldx] = cur[r] + static_cast<double>(v[h + r]);
+    }
   }
 };
 
@@ -363,21 +368,17 @@ __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n,
   }
 }
 
-// rho for residual `it`; decides whether refinement goes on. A residual with
-// fewer digit groups (can_accept == 0) may continue the iteration but never
-// declare convergence.
+// rho for residual `it`; decides whether refinement goes on.
 __global__ void decide_kernel(const double* sums, int it, double tol, int max_updates, double* hist, Ctl* ctl,
-                              const int32_t* status, int can_accept) {
+                              const int32_t* status) {
   if (ctl->done || *status != 0) return;
   const double a2 = sums[0], e2 = sums[1 + 2 * it], x2 = sums[2 + 2 * it];
   const double rho = sqrt(e2) / (sqrt(a2) * sqrt(x2));
   hist[it] = rho;
   ctl->last = it;
-  if (rho <= tol && can_accept) {
+  if (rho <= tol) {
     ctl->done = 1;
     ctl->code = BLOCKINV_OK;
-  } else if (!can_accept && it < max_updates && rho == rho) {
-    ctl->updates = it + 1;
   } else if (it >= max_updates || !(rho == rho) || (it > 0 && !(rho < 0.25 * hist[it - 1]))) {
     ctl->done = 1;
     ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
@@ -504,10 +505,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
                           status, s);
     }
-    // The first residual only steers the first update (its error is squared
-    // away by the next one), so it keeps fewer digit groups; every later
-    // residual, including the final check, keeps all S.
-    const int groups = (it == 0 && max_updates > 0) ? std::min(S, kFirstResidualGroups) : S;
+    // Every residual keeps all S digit groups: the first one steers the first
+    // update, and its error (not rho_0 squared) bounds rho after that update.
+    const int groups = S;
     for (int g = 0; g < groups && e == cudaSuccess; ++g) {
       tc::KMap km{};
       km.kb_per_pair = Kp / 128;
@@ -529,7 +529,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
                                         it < max_updates ? Eop : nullptr, Kp,
                                         (max_updates == 0) ? Eout : nullptr, lde, ctl, status);
     }
-    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status, groups == S ? 1 : 0);
+    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status);
     if (it == max_updates) break;
     if (host_steps) {
       // Blocking callers stop enqueueing as soon as the device has decided.
@@ -551,8 +551,13 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       km.pa[0] = 0; km.pb[0] = 0;
       km.pa[1] = 0; km.pb[1] = 1;
       km.pa[2] = 1; km.pb[2] = 0;
+      // The tensor-core FP32 accumulator drops bits on every k-step (its
+      // error grows linearly with K, measured), so K is cut into chunks of
+      // kUpdateChunkK, each added into the FP64 X on its own.
+      km.chunk_kb = kUpdateChunkK / 32;
       EpiAddF64 epi{X, ldx, n, ctl, status};
-      TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd + 16.0 * nd * Kp, s);
+      const double chunks = std::ceil(3.0 * Kp / kUpdateChunkK);
+      TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd * chunks + 16.0 * nd * Kp, s);
       e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true>(tXo, tEo, n, n, km, epi, status, s);
     }
   }

@@ -55,12 +55,11 @@ struct EpiStoreF32 {
   int64_t ldc;
   int M, N;
   __device__ bool skip() const { return false; }
-  __device__ void apply(int row, int col0, const uint32_t (&v)[32]) const {
-    if (row >= M) return;
-    float* p = C + (int64_t)row * ldc + col0;
+  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+    if (col >= N) return;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (col0 + j < N) p[j] = __uint_as_float(v[j]);
+    for (int r = 0; r < 32; ++r)
+      if (row0 + r < M) C[(int64_t)(row0 + r) * ldc + col] = v[r];
   }
 };
 

@@ -2,7 +2,9 @@
 // with both operands K-major in global memory, fed by TMA into a 4-stage
 // shared-memory ring (128-byte swizzle), accumulated by tcgen05.mma into one
 // of two TMEM accumulators (128 lanes x 256 columns each), and handed to an
-// epilogue functor that reads the accumulator with tcgen05.ld.
+// epilogue functor that reads the accumulator with tcgen05.ld. The functor's
+// apply_cols(row0, col, v) receives column `col` of rows row0 .. row0 + 31
+// (v[r] = D[row0 + r][col]; the 32 lanes of a warp hold 32 adjacent columns).
 //
 //   warp 0, lane 0   TMA producer            (also allocates/frees TMEM)
 //   warp 1, lane 0   MMA issuer
@@ -47,6 +49,8 @@ struct KMap {
   int kblocks;            // k-blocks per output tile (= pairs * kb_per_pair)
   int kb_per_pair;        // k-blocks per slice pair
   int slice_cols;         // operand columns between consecutive slices
+  int chunk_kb;           // k-blocks per accumulator hand-off (0 = the whole K); > 0 only for
+                          // epilogues that add into their output (each chunk arrives separately)
   int8_t pa[kMaxPairs];   // A slice of pair i
   int8_t pb[kMaxPairs];   // B slice of pair i
 };
@@ -67,7 +71,16 @@ struct GemmShared {
   uint32_t tmem_base;
 };
 
-constexpr size_t gemm_smem_bytes() { return (size_t)kStages * kStageBytes + sizeof(GemmShared) + 1024; }
+// Epilogue staging: each epilogue warp turns its 32 x 32 accumulator block
+// (lane = row) around through shared memory (rows padded to 33 words, no bank
+// conflicts), so that the functor's global accesses run along rows (lane =
+// column) and every warp access covers whole cache lines.
+constexpr int kStagePitch = 33;
+constexpr size_t kSharedBytes = (sizeof(GemmShared) + 15) / 16 * 16;
+constexpr size_t kEpiStageBytes = sizeof(float) * kEpiWarps * 32 * kStagePitch;
+
+constexpr size_t gemm_smem_bytes() { return (size_t)kStages * kStageBytes + kSharedBytes + kEpiStageBytes + 1024; }
+static_assert(gemm_smem_bytes() <= 227 * 1024, "GEMM shared memory above the per-CTA limit");
 
 __device__ __forceinline__ void flag_timeout(int32_t* status) {
   if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
@@ -90,6 +103,12 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int rank = kMC ? (int)cluster_ctarank() : 0;
   const int first = kMC ? (int)cluster_id_x() : (int)blockIdx.x;
   const int stride = kMC ? (int)cluster_count_x() : (int)gridDim.x;
+  // Accumulator hand-offs: each of this CTA's tiles in nch K-chunks of kbc
+  // k-blocks, every chunk accumulated from zero and passed to the epilogue.
+  const int kbc = (km.chunk_kb > 0 && km.chunk_kb < km.kblocks) ? km.chunk_kb : km.kblocks;
+  const int nch = (km.kblocks + kbc - 1) / kbc;
+  const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
+  const int nitems = my_tiles * nch;
   if (epi.skip()) return;  // an earlier kernel of this computation failed (uniform over the grid)
 
   if (threadIdx.x == 0) {
@@ -159,7 +178,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     constexpr uint32_t id = idesc<K>(kBM, kBN);
     uint32_t it = 0, tl = 0;
     bool ok = true;
-    for (int t = first; t < ntiles && ok; t += stride, ++tl) {
+    for (int w = 0; w < nitems && ok; ++w, ++tl) {
+      const int c = w % nch;
       const uint32_t a = tl & 1;
       const uint32_t aph = (tl >> 1) & 1;
       if (!mbar_wait(&sh->tempty[a], aph ^ 1)) {
@@ -168,7 +188,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       fence_after_sync();
       const uint32_t d = tmem + a * kBN;
-      for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
+      const int kb0 = c * kbc, kb1 = min(km.kblocks, kb0 + kbc);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
         if (!mbar_wait(&sh->full[s], ph)) {
@@ -181,7 +202,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint64_t db = sdesc_sw128(sa + kBM * 128);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)  // 4 x 32 bytes of K per 128-byte row
-          mma<K>(d, da + 2 * ks, db + 2 * ks, id, (kb | ks) != 0 ? 1u : 0u);
+          mma<K>(d, da + 2 * ks, db + 2 * ks, id, ((kb - kb0) | ks) != 0 ? 1u : 0u);
         if (kMC)
           mma_commit_mc(&sh->empty[s], 0x3);
         else
@@ -192,10 +213,12 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     if (!ok) flag_timeout(status);
   } else if (warp >= 2) {
+    float* stage = reinterpret_cast<float*>(smem + kStages * kStageBytes + kSharedBytes) + (warp - 2) * 32 * kStagePitch;
     const int q = warp & 3;  // the TMEM lane quarter this warp may access
     const int half = (warp - 2) / 4;
     uint32_t tl = 0;
-    for (int t = first; t < ntiles; t += stride, ++tl) {
+    for (int w = 0; w < nitems; ++w, ++tl) {
+      const int t = first + (w / nch) * stride;
       const uint32_t a = tl & 1;
       const uint32_t aph = (tl >> 1) & 1;
       if (!mbar_wait(&sh->tfull[a], aph)) {
@@ -205,13 +228,20 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       fence_after_sync();
       const int m0 = (kMC ? 2 * (t / tiles_n) + rank : t / tiles_n) * kBM;
       const int n0 = (t % tiles_n) * kBN;
-      const int row = m0 + q * 32 + lane;
+      const int row0 = m0 + q * 32;
 #pragma unroll 1
       for (int c = half * (kBN / 64); c < (half + 1) * (kBN / 64); ++c) {
         uint32_t v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + c * 32, v);
         tmem_wait_ld();
-        epi.apply(row, n0 + c * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * kStagePitch + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        float col[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) col[r] = stage[r * kStagePitch + lane];
+        __syncwarp();
+        epi.apply_cols(row0, n0 + c * 32 + lane, col);
       }
       fence_before_sync();
       mbar_arrive(&sh->tempty[a]);
