@@ -52,7 +52,9 @@ extern "C" {
  *                      products on TF32 tensor cores (FP32 accumulation),
  *                      then Newton-Schulz refinement X <- X + X (I - A X) with
  *                      an FP64-accurate residual until rho <= tol.
- *  BLOCKINV_MIXED_BF16 the same with BF16 tensor-core products. */
+ *  BLOCKINV_MIXED_BF16 the same with BF16 tensor-core products.
+ * Mixed modes accept n <= 16384 (the refinement residual's digit products are
+ * exact up to that order); larger n returns BLOCKINV_ERR_INVALID. */
 typedef enum {
   BLOCKINV_F64 = 0,
   BLOCKINV_MIXED_TF32 = 1,
@@ -268,8 +270,9 @@ int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X,
 
 /* FP64-accurate residual on the tensor cores: E = I - A X and
  * rho = ||E||_F / (||A||_F ||X||_F). The diagonal terms are exact FP64
- * products; the off-diagonal product comes from `slices` (9..13, 0 = 12)
- * base-16 FP8 digits of A (by rows) and X (by columns) whose products
+ * products; the off-diagonal product comes from `slices` (7..9, 0 = 9)
+ * base-32 FP8 digits of A (by rows) and X (by columns), 5 slices - 1 bits
+ * of each entry relative to its row or column maximum, whose products
  * accumulate exactly. This is the residual the mixed modes' Newton-Schulz
  * refinement uses; blockinv_residual is the plain FP64 reference. Device
  * pointers; E (leading dimension lde) may be NULL. n <= 16384. Blocking. */

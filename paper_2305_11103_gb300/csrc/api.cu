@@ -72,8 +72,11 @@ void default_partition(int n, std::vector<int>* out) {
   out->back() = n - kDefaultBlock * (p - 1);
 }
 
-bool valid_mode(int mode) {
-  return mode == BLOCKINV_F64 || mode == BLOCKINV_MIXED_TF32 || mode == BLOCKINV_MIXED_BF16;
+// Mixed modes stop at the order up to which the refinement's digit products
+// are exact (FP32 group sums below 2^24, int64 accumulator below 2^63).
+bool valid_mode(int mode, int64_t n) {
+  if (mode == BLOCKINV_F64) return true;
+  return (mode == BLOCKINV_MIXED_TF32 || mode == BLOCKINV_MIXED_BF16) && n <= kMixedMaxOrder;
 }
 
 int make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* plan) {
@@ -341,7 +344,7 @@ struct ServeJob {
 };
 
 int serve_make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, int mode, Plan* pl) {
-  if (!valid_mode(mode)) return BLOCKINV_ERR_INVALID;
+  if (!valid_mode(mode, n)) return BLOCKINV_ERR_INVALID;
   return make_plan(n, p, block_sizes, lda, pl);
 }
 
@@ -427,7 +430,7 @@ int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, doub
   Plan pl;
   int st = make_plan(n, p, block_sizes, lda, &pl);
   if (st != BLOCKINV_OK) return record(st, -1);
-  if (!A || !status_dev || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  if (!A || !status_dev || !valid_mode(mode, n)) return record(BLOCKINV_ERR_INVALID, -1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
@@ -444,7 +447,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
   }
   Plan pl;
   int st = make_plan(n, p, block_sizes, lda, &pl);
-  if (st == BLOCKINV_OK && (!A || !valid_mode(mode))) st = BLOCKINV_ERR_INVALID;
+  if (st == BLOCKINV_OK && (!A || !valid_mode(mode, n))) st = BLOCKINV_ERR_INVALID;
   if (st != BLOCKINV_OK) {
     if (info) info->status = st;
     return record(st, -1);
@@ -493,7 +496,7 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
   Plan pl;
   int st = make_plan(n, p, block_sizes, lda, &pl);
   if (st != BLOCKINV_OK) return record(st, -1);
-  if (!A_host || !valid_mode(mode)) return record(BLOCKINV_ERR_INVALID, -1);
+  if (!A_host || !valid_mode(mode, n)) return record(BLOCKINV_ERR_INVALID, -1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   AsyncBuf dbuf, sbuf;
   const size_t row = sizeof(double) * (size_t)n;
@@ -536,8 +539,8 @@ int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X, 
 int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, double* E,
                          int64_t lde, int slices, double* rho_out, void* stream) {
   if (slices == 0) slices = kResidualSlices;
-  if (n < 1 || n > 16384 || lda < n || ldx < n || !A || !X || !rho_out || (E && lde < n) || slices < 9 ||
-      slices > 13)
+  if (n < 1 || n > kMixedMaxOrder || lda < n || ldx < n || !A || !X || !rho_out || (E && lde < n) ||
+      slices < kMinResidualSlices || slices > kMaxResidualSlices)
     return record(BLOCKINV_ERR_INVALID, -1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   AsyncBuf ws, hist, ctl, sbuf;

@@ -125,7 +125,10 @@ int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda
                            cudaStream_t s);
 
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
-constexpr int kResidualSlices = 11;
+constexpr int kResidualSlices = 9;      // base-32 digits per operand (44 bits)
+constexpr int kMinResidualSlices = 7;
+constexpr int kMaxResidualSlices = 9;    // int64 accumulator bound at n = 16384
+constexpr int64_t kMixedMaxOrder = 16384;
 size_t refine_workspace_bytes(int n, int S, int max_updates);
 cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,

@@ -436,7 +436,8 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
       m.pr[e] = (l < w) ? m.cols[(size_t)lc * b + m.perm[k * kPanel + l]] : T(0);
     }
     __syncthreads();
-    // rank-w update of my columns (skipping the panel itself on the owner)
+    // rank-w update of my columns (skipping the panel itself on the owner),
+    // four columns per pass so that four accumulator chains run side by side
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int r = h ? r1 : r0;
@@ -445,24 +446,36 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
 #pragma unroll
       for (int l = 0; l < kPanel; ++l) pv[l] = (l < w) ? m.panel[(size_t)l * b + r] : T(0);
       const bool piv_row = m.inpanel[r] != 0;
-      for (int lc = 0; lc < my_cols; ++lc) {
-        const int gk = (lc / kPanel) * nranks + rank;  // global panel of this local column
+      for (int lp = 0; lp < ncl / kPanel; ++lp) {
+        const int gk = lp * nranks + rank;  // global panel of my local panel lp
         if (gk >= npanels || (rank == owner && gk == k)) continue;
-        if ((lc % kPanel) >= min(kPanel, b - gk * kPanel)) continue;
-        T acc = piv_row ? T(0) : m.cols[(size_t)lc * b + r];
-        const T* prc = m.pr + (size_t)lc * kPanel;
-        if constexpr (sizeof(T) == 4) {
-          const float4* p4 = reinterpret_cast<const float4*>(prc);
+        const int wg = min(kPanel, b - gk * kPanel);
+        for (int c0 = 0; c0 < wg; c0 += 4) {
+          const int lc = lp * kPanel + c0;
+          T acc[4];
 #pragma unroll
-          for (int q = 0; q < kPanel / 4; ++q) {
-            const float4 v = p4[q];
-            acc += pv[4 * q] * v.x + pv[4 * q + 1] * v.y + pv[4 * q + 2] * v.z + pv[4 * q + 3] * v.w;
+          for (int u = 0; u < 4; ++u)
+            acc[u] = (piv_row || c0 + u >= wg) ? T(0) : m.cols[(size_t)(lc + u) * b + r];
+          const T* prc = m.pr + (size_t)lc * kPanel;
+          if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int q = 0; q < kPanel / 4; ++q) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float4 v = reinterpret_cast<const float4*>(prc + u * kPanel)[q];
+                acc[u] += pv[4 * q] * v.x + pv[4 * q + 1] * v.y + pv[4 * q + 2] * v.z + pv[4 * q + 3] * v.w;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l < kPanel; ++l)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[u] += pv[l] * prc[u * kPanel + l];
           }
-        } else {
 #pragma unroll
-          for (int l = 0; l < kPanel; ++l) acc += pv[l] * prc[l];
+          for (int u = 0; u < 4; ++u)
+            if (c0 + u < wg) m.cols[(size_t)(lc + u) * b + r] = acc[u];
         }
-        m.cols[(size_t)lc * b + r] = acc;
       }
     }
     __syncthreads();
@@ -490,11 +503,15 @@ size_t blocked_smem_bytes(int b, int ncl, int elem) {
          sizeof(int) * (8 + 2 * (size_t)b + 4) + b + 64;
 }
 
-// Cluster size for the blocked kernel: the fewest CTAs (1, 2, 4, 8) whose
-// columns fit in 225 KiB of shared memory each.
+// Cluster size for the blocked kernel: one 32-column panel per CTA where
+// possible (the rank updates of each panel step then run on as many SMs as
+// there are panels), at most 8 CTAs, more panels per CTA only when needed;
+// each CTA's columns must fit in 225 KiB of shared memory.
 bool plan_blocked(int b, int elem, int* ctas, int* ncl, size_t* smem) {
   const int npanels = (b + kPanel - 1) / kPanel;
-  for (int c = 1; c <= 8; c *= 2) {
+  int c0 = 1;
+  while (c0 < npanels && c0 < 8) c0 *= 2;
+  for (int c = c0; c <= 8; c *= 2) {
     const int per = (npanels + c - 1) / c;
     const size_t bytes = blocked_smem_bytes(b, per * kPanel, elem);
     if (bytes <= 225 * 1024) {

@@ -14,20 +14,23 @@
 // diagonal, keeps the bits of the off-diagonal entries. Every row i of O_A is
 // scaled by a power of two 2^-e_i (e_i the smallest integer with
 // max_k |a_ik| < 2^e_i, k != i) and every column j of O_X by 2^-f_j; the
-// scaled values, as fixed-point numbers with 4S fraction bits, are cut into S
-// signed base-16 digits (the leading digit in [-16, 16], the others in
-// [-8, 7]), each exact in FP8 E4M3. Then
+// scaled values, as fixed-point numbers with F = 5S - 1 fraction bits, are cut
+// into S signed base-32 digits (the leading digit in [-16, 16], the others in
+// [-16, 15]); every digit is an integer of magnitude <= 16, exact in FP8 E4M3.
+// Then
 //
-//   (O_A O_X)_ij ~= 2^(e_i + f_j - 8) sum_g 2^(-4g) G_g(i, j),
+//   (O_A O_X)_ij ~= 2^(e_i + f_j - 2F) sum_g 32^(2S - 2 - g) G_g(i, j),
 //   G_g = sum_{p + q = g} Adigits_p Xdigits_q^T      (g = 0 .. S - 1),
 //
-// where each G_g is an integer matrix whose entries stay below 2^24 for
-// K <= 16384, so the FP32 tensor-core accumulator holds it exactly. Each group
-// is one GEMM over its digit pairs; its epilogue adds G_g << 4 (S - 1 - g)
-// into an int64 accumulator, again exactly. The finalize kernel converts to
-// FP64, forms E = I - A X, its Frobenius norm and the operands of the update.
-// Dropped groups (p + q >= S) and truncated digits leave an error of order
-// 2^(-4S - 8) S sqrt(K) relative to the row and column scales.
+// where each digit product is at most 2^8 in magnitude, so a GEMM over P digit
+// pairs with n <= 2^16 / P terms each keeps every partial sum below 2^24 and
+// the FP32 tensor-core accumulator holds it exactly. Group g is one GEMM (or
+// several, when g + 1 pairs exceed that bound); the epilogue adds its result
+// << 5 (S - 1 - g) into an int64 accumulator, again exactly: with S <= 9 and
+// n <= 16384 every sum stays below 2^(22 + 40 + 0.1) < 2^63. The finalize kernel converts to FP64, forms E = I - A X, its
+// Frobenius norm and the operands of the update. Dropped groups (p + q >= S)
+// and the rounding of the fixed-point values leave an error of order
+// 2^(-F) S sqrt(K) relative to the row and column scales.
 //
 // Both products run on the cluster-of-two GEMM that multicasts the shared B
 // tile. The update X += X E uses split TF32 operands (hi + lo for X and E, the
@@ -51,7 +54,8 @@ namespace blockinv {
 
 namespace {
 
-constexpr int kLog2Digit = 4;
+constexpr int kLog2Digit = 5;  // base-32 digits
+constexpr int kHeadroom = 1;   // fraction bits F = 5 S - 1 keep the leading digit within [-16, 16]
 constexpr int kUpdateChunkK = 2048;  // K elements per accumulator hand-off in the update
 
 struct Ctl {
@@ -72,14 +76,15 @@ __device__ __forceinline__ int exp_bound(double v) {
   return static_cast<int>((bits >> 52) & 0x7FF) - 1022;
 }
 
-// Fixed-point integer round(v * 2^(4S - e)) from the bit pattern, |v| < 2^e.
+// Fixed-point integer round(v * 2^(F - e)), F = 5S - 1, from the bit pattern,
+// |v| < 2^e.
 __device__ __forceinline__ long long fixed_point(double v, int e, int S) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
   const int ef = static_cast<int>((bits >> 52) & 0x7FF);
   if (ef == 0) return 0;  // zero or subnormal: below every digit kept
   const long long m = static_cast<long long>((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-  // v = m * 2^(ef - 1075); shift = ef - 1075 + 4S - e (always negative here)
-  const int sh = ef - 1075 + kLog2Digit * S - e;
+  // v = m * 2^(ef - 1075); shift = ef - 1075 + F - e (always negative here)
+  const int sh = ef - 1075 + kLog2Digit * S - kHeadroom - e;
   long long q;
   if (sh >= 0) {
     q = m << sh;
@@ -95,15 +100,16 @@ __device__ __forceinline__ uint8_t e4m3(int d) {
   return static_cast<uint8_t>(__nv_cvt_float_to_fp8(static_cast<float>(d), __NV_SATFINITE, __NV_E4M3));
 }
 
-// Balanced base-16 digits of q, most significant first: d[0] in [-16, 16],
-// d[1..S-1] in [-8, 7], q = sum_p d[p] 16^(S-1-p).
+// Balanced base-32 digits of q (|q| <= 2^(5S - 1)), most significant first:
+// d[1..S-1] in [-16, 15], and d[0] in [-16, 16] since the lower digits sum to
+// less than half a unit of the leading one; q = sum_p d[p] 32^(S-1-p).
 template <int S>
 __device__ __forceinline__ void digits(long long q, int (&d)[S]) {
 #pragma unroll
   for (int p = S - 1; p >= 1; --p) {
-    const int r = static_cast<int>(((q + 8) & 15)) - 8;
+    const int r = static_cast<int>(((q + 16) & 31)) - 16;
     d[p] = r;
-    q = (q - r) >> 4;
+    q = (q - r) >> kLog2Digit;
   }
   d[0] = static_cast<int>(q);
 }
@@ -295,7 +301,8 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
 }
 
-// E = I - a_ii x_ij - [i != j] a_ij x_jj - 2^(e_i + f_j - 8 - 4 (S - 1)) T;
+// E = I - a_ii x_ij - [i != j] a_ij x_jj - 2^(e_i + f_j + 2 - 5 (S + 1)) T
+// (S = the digit groups summed in T: 2^(-2F) 32^(2S' - 1 - S) with F = 5S' - 1);
 // ||E||^2; E^T split into TF32 hi/lo (rows j of Eop, columns i and Kp + i);
 // optionally E itself in FP64.
 __global__ void __launch_bounds__(256)
@@ -314,7 +321,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     const int i = i0 + ii;
     double e = 0.0;
     if (i < n && j < n) {
-      const int ex = rexp[i] + cexp[j] - 8 - kLog2Digit * (S - 1);
+      const int ex = rexp[i] + cexp[j] + 2 * kHeadroom - kLog2Digit * (S + 1);
       const long long t = T[(int64_t)i * ldt + j];
       const double r = (t == 0) ? 0.0 : static_cast<double>(t) * pow2(ex);
       const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
@@ -422,11 +429,9 @@ cudaError_t slices_dispatch(int S, const double* A0, int64_t ld0, const double* 
                             const int32_t* rexp, int32_t* cexp, uint8_t* Asl, uint8_t* Xsl, double* x2, bool rows,
                             const Ctl* ctl, const int32_t* status, cudaStream_t s) {
   switch (S) {
+    case 7: return launch_slices<7>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 8: return launch_slices<8>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
     case 9: return launch_slices<9>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 10: return launch_slices<10>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 11: return launch_slices<11>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 12: return launch_slices<12>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 13: return launch_slices<13>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -458,7 +463,9 @@ size_t refine_workspace_bytes(int n, int S, int max_updates) {
 cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx, int n, double tol,
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
                            double* Eout, int64_t lde, cudaStream_t s, bool report, bool host_steps) {
-  if (S < 9 || S > 13 || n < 1) return cudaErrorInvalidValue;
+  if (S < kMinResidualSlices || S > kMaxResidualSlices || n < 1 || n > kMixedMaxOrder) return cudaErrorInvalidValue;
+  // digit pairs per GEMM launch: pairs * n * 2^8 <= 2^24
+  const int max_pairs = std::min(tc::kMaxPairs, (1 << 16) / n);
   Ctl* ctl = reinterpret_cast<Ctl*>(ctl_words);
   const int Kp = (n + 127) / 128 * 128;
   const int64_t ldt = (n + 31) / 32 * 32;
@@ -509,17 +516,20 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     // update, and its error (not rho_0 squared) bounds rho after that update.
     const int groups = S;
     for (int g = 0; g < groups && e == cudaSuccess; ++g) {
-      tc::KMap km{};
-      km.kb_per_pair = Kp / 128;
-      km.slice_cols = Kp;
-      km.kblocks = (g + 1) * km.kb_per_pair;
-      for (int p = 0; p <= g; ++p) {
-        km.pa[p] = (int8_t)p;
-        km.pb[p] = (int8_t)(g - p);
+      for (int p0 = 0; p0 <= g && e == cudaSuccess; p0 += max_pairs) {
+        const int np = std::min(max_pairs, g + 1 - p0);
+        tc::KMap km{};
+        km.kb_per_pair = Kp / 128;
+        km.slice_cols = Kp;
+        km.kblocks = np * km.kb_per_pair;
+        for (int i = 0; i < np; ++i) {
+          km.pa[i] = (int8_t)(p0 + i);
+          km.pb[i] = (int8_t)(g - p0 - i);
+        }
+        EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0, ctl, status};
+        TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
+        e = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
       }
-      EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), g == 0 ? 1 : 0, ctl, status};
-      TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * (g + 1), (double)(g + 1) * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-      e = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
     }
     if (e != cudaSuccess) break;
     {

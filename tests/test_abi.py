@@ -71,3 +71,13 @@ def test_null_pointer_rejected(lib):
 
 def test_unknown_mode_rejected_before_gpu_work(lib):
     assert blockinv.blockinv_invert(8, [8], 0x1000, 8, 7, None) == blockinv.ERR_INVALID
+
+
+def test_mixed_modes_reject_orders_above_16384(lib):
+    # the refinement residual's digit products are exact only up to n = 16384
+    for mode in (1, 2):
+        assert blockinv.blockinv_invert(16385, None, 0x1000, 16385, mode, None) == blockinv.ERR_INVALID
+    st, _ = blockinv.blockinv_residual_tc(16385, 0x1000, 16385, 0x2000, 16385)
+    assert st == blockinv.ERR_INVALID
+    st, _ = blockinv.blockinv_residual_tc(64, 0x1000, 64, 0x2000, 64, slices=10)
+    assert st == blockinv.ERR_INVALID
