@@ -262,9 +262,8 @@ struct BlockedSmem {
   T* cols;      // ncl x b, column-major
   T* panel;     // kPanel x b, column-major: copy of the current panel
   T* pr;        // ncl x kPanel: old pivot rows restricted to my columns
-  T* prow;      // kPanel
-  T* wv;        // 8 warp candidates
-  int* wi;      // 8
+  T* cand;      // 2 x 8 x kPanel: each warp's candidate pivot row (double-buffered by column)
+  unsigned long long* key;  // 2 x 8 warp pivot keys (value bits, ~row), double-buffered by column
   int* perm;    // b: pivot row of each global column
   int* srow;    // b: column at which each row was the pivot (-1: not yet)
   unsigned char* inpanel;  // b
@@ -277,10 +276,9 @@ __device__ __forceinline__ BlockedSmem<T> blocked_layout(unsigned char* raw, int
   m.cols = reinterpret_cast<T*>(raw);
   m.panel = m.cols + (size_t)ncl * b;
   m.pr = m.panel + (size_t)kPanel * b;
-  m.prow = m.pr + (size_t)ncl * kPanel;
-  m.wv = m.prow + kPanel;
-  m.wi = reinterpret_cast<int*>(m.wv + 8);
-  m.perm = m.wi + 8;
+  m.cand = m.pr + (size_t)ncl * kPanel;
+  m.key = reinterpret_cast<unsigned long long*>(m.cand + 16 * kPanel);
+  m.perm = reinterpret_cast<int*>(m.key + 16);
   m.srow = m.perm + b;
   m.flags = m.srow + b;
   m.inpanel = reinterpret_cast<unsigned char*>(m.flags + 4);
@@ -291,6 +289,7 @@ template <typename T, bool kCluster>
 __global__ void __launch_bounds__(kPivotThreads, 1)
 pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __restrict__ out, int64_t ldo,
                      int32_t* status, int block_index) {
+  static_assert(sizeof(T) == 4, "the blocked pivot kernel serves the FP32 mixed path");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockedSmem<T> m = blocked_layout<T>(smem_raw, b, ncl);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -347,61 +346,120 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
       bool free0 = r0 < b && m.srow[r0] < 0;
       bool free1 = r1 < b && m.srow[r1] < 0;
       bool stop = false;
+      const bool two = b > kPivotThreads;  // a second row per thread only above 256 rows
+      // One CTA barrier per column. Pivot search: |x| of a free row as its
+      // FP32 bit pattern (ordered like the value; NaN above infinity) and the
+      // row index form a 64-bit key (value, ~row): the largest key is the
+      // largest magnitude, lowest row on ties. Each warp reduces its keys with
+      // two redux operations and publishes its key and its candidate row's raw
+      // values; after the barrier every thread takes the largest of the 8 keys
+      // and reads the pivot row from the winner's slot. Keys and slots
+      // alternate by column, so nothing is rewritten before its readers pass
+      // the next barrier. Columns are taken four at a time in registers 0..3,
+      // then the registers rotate by four (eight rotations restore the order).
+#pragma unroll 1
+      for (int cb = 0; cb < kPanel; cb += 4) {
 #pragma unroll
-      for (int c = 0; c < kPanel; ++c) {
-        if (c < w && !stop) {
-          T bv = T(-1);
-          int bi = INT_MAX;
-          if (free0) {
-            bv = fabs(x0[c]);
-            bi = r0;
-          }
-          if (free1) argmax_step(bv, bi, T(fabs(x1[c])), r1);
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, bv, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            argmax_step(bv, bi, ov, oi);
-          }
-          if (lane == 0) {
-            m.wv[warp] = bv;
-            m.wi[warp] = bi;
-          }
-          __syncthreads();
-          T gv = (lane < 8) ? m.wv[lane] : T(-1);
-          int gi = (lane < 8) ? m.wi[lane] : INT_MAX;
-#pragma unroll
-          for (int off = 4; off > 0; off >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, gv, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, gi, off);
-            argmax_step(gv, gi, ov, oi);
-          }
-          gv = __shfl_sync(0xffffffffu, gv, 0);
-          gi = __shfl_sync(0xffffffffu, gi, 0);
-          if (gi == INT_MAX || !(gv > T(0)) || !isfinite(gv)) {
-            if (tid == 0) m.flags[(gi == INT_MAX || !(gv > T(0))) ? 1 : 2] = 1;
-            stop = true;
-          } else {
-            const int p = gi;
-            if (p == r0 || p == r1) {  // the thread holding the pivot row publishes it, scaled
-              const bool h = (p == r1);
-              const T inv = recip(h ? x1[c] : x0[c]);
-#pragma unroll
-              for (int l = 0; l < kPanel; ++l)
-                if (l < w) m.prow[l] = (l == c) ? inv : (h ? x1[l] : x0[l]) * inv;
-              m.perm[k * kPanel + c] = p;
-              m.srow[p] = k * kPanel + c;
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = cb + cc;
+          if (c < w && !stop) {
+            const int buf = c & 1;
+            unsigned vb = free0 ? __float_as_uint(fabsf(x0[cc])) : 0u;
+            unsigned vi = static_cast<unsigned>(r0);
+            if (two && free1) {
+              const unsigned v1 = __float_as_uint(fabsf(x1[cc]));
+              if (v1 > vb) {
+                vb = v1;
+                vi = static_cast<unsigned>(r1);
+              }
             }
+            const unsigned wmax = __reduce_max_sync(0xffffffffu, vb);
+            const unsigned wrow = __reduce_min_sync(0xffffffffu, vb == wmax ? vi : 0xffffffffu);
+            if (static_cast<int>(wrow) == r0 || static_cast<int>(wrow) == r1) {  // the warp's candidate row
+              const bool h = static_cast<int>(wrow) == r1;
+              float4* slot = reinterpret_cast<float4*>(m.cand + (buf * 8 + warp) * kPanel);
+#pragma unroll
+              for (int q = 0; q < kPanel / 4; ++q)
+                slot[q] = h ? make_float4(x1[4 * q], x1[4 * q + 1], x1[4 * q + 2], x1[4 * q + 3])
+                            : make_float4(x0[4 * q], x0[4 * q + 1], x0[4 * q + 2], x0[4 * q + 3]);
+            }
+            if (lane == 0)
+              m.key[buf * 8 + warp] = (static_cast<unsigned long long>(wmax) << 32) | static_cast<unsigned>(~wrow);
             __syncthreads();
-            const T f0 = x0[c], f1 = x1[c];
-#pragma unroll
-            for (int l = 0; l < kPanel; ++l) {
-              const T pl = m.prow[l];
-              x0[l] = (r0 == p) ? pl : ((l == c) ? T(0) : x0[l]) - f0 * pl;
-              x1[l] = (r1 == p) ? pl : ((l == c) ? T(0) : x1[l]) - f1 * pl;
+            unsigned long long kk;
+            {
+              const ulonglong2* kp = reinterpret_cast<const ulonglong2*>(m.key + buf * 8);
+              const ulonglong2 k01 = kp[0], k23 = kp[1], k45 = kp[2], k67 = kp[3];
+              const unsigned long long a = k01.x > k01.y ? k01.x : k01.y;
+              const unsigned long long b2 = k23.x > k23.y ? k23.x : k23.y;
+              const unsigned long long c2 = k45.x > k45.y ? k45.x : k45.y;
+              const unsigned long long d = k67.x > k67.y ? k67.x : k67.y;
+              const unsigned long long ab = a > b2 ? a : b2, cd = c2 > d ? c2 : d;
+              kk = ab > cd ? ab : cd;
             }
-            free0 = free0 && r0 != p;
-            free1 = free1 && r1 != p;
+            const float gv = __uint_as_float(static_cast<unsigned>(kk >> 32));
+            const int p = static_cast<int>(~static_cast<unsigned>(kk));
+            if (!(gv > 0.f) || !isfinite(gv)) {
+              if (tid == 0) m.flags[!(gv > 0.f) && !isnan(gv) ? 1 : 2] = 1;
+              stop = true;
+            } else {
+              const float* prow = m.cand + (buf * 8 + ((p & (kPivotThreads - 1)) >> 5)) * kPanel;
+              float pr[kPanel];
+#pragma unroll
+              for (int q = 0; q < kPanel / 4; ++q) {
+                const float4 v = reinterpret_cast<const float4*>(prow)[q];
+                pr[4 * q] = v.x;
+                pr[4 * q + 1] = v.y;
+                pr[4 * q + 2] = v.z;
+                pr[4 * q + 3] = v.w;
+              }
+              const float inv = recip(pr[cc]);
+              // pivot row: P[p][l] * inv (l != c), inv at l = c; every other
+              // row: x[l] - (x[c] inv) P[p][l] (l != c), -x[c] inv at l = c
+              if (r0 == p) {
+                m.perm[k * kPanel + c] = p;
+                m.srow[p] = k * kPanel + c;
+#pragma unroll
+                for (int l = 0; l < kPanel; ++l) x0[l] = (l == cc) ? inv : pr[l] * inv;
+              } else {
+                const float f0 = x0[cc] * inv;
+#pragma unroll
+                for (int l = 0; l < kPanel; ++l) x0[l] = (l == cc) ? -f0 : x0[l] - f0 * pr[l];
+              }
+              if (two) {
+                if (r1 == p) {
+                  m.perm[k * kPanel + c] = p;
+                  m.srow[p] = k * kPanel + c;
+#pragma unroll
+                  for (int l = 0; l < kPanel; ++l) x1[l] = (l == cc) ? inv : pr[l] * inv;
+                } else {
+                  const float f1 = x1[cc] * inv;
+#pragma unroll
+                  for (int l = 0; l < kPanel; ++l) x1[l] = (l == cc) ? -f1 : x1[l] - f1 * pr[l];
+                }
+              }
+              free0 = free0 && r0 != p;
+              free1 = free1 && r1 != p;
+            }
+          }
+        }
+        // rotate by four: the next four columns move into registers 0..3
+        {
+          float t0[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) t0[u] = x0[u];
+#pragma unroll
+          for (int l = 0; l < kPanel - 4; ++l) x0[l] = x0[l + 4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x0[kPanel - 4 + u] = t0[u];
+          if (two) {
+            float t1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) t1[u] = x1[u];
+#pragma unroll
+            for (int l = 0; l < kPanel - 4; ++l) x1[l] = x1[l + 4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x1[kPanel - 4 + u] = t1[u];
           }
         }
       }
@@ -411,23 +469,69 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
         if (l < w && r1 < b) pc[(size_t)l * b + r1] = x1[l];
       }
       __syncthreads();
+      if constexpr (kCluster) {
+        // publish the panel through L2 for the other CTAs (see below)
+        float4* xg = reinterpret_cast<float4*>(out + (size_t)(k & 1) * kPanel * b);
+        const float4* pc4 = reinterpret_cast<const float4*>(pc);
+        for (int e4 = tid; e4 < (w * b) / 4; e4 += kPivotThreads) xg[e4] = pc4[e4];
+        for (int e = (w * b) / 4 * 4 + tid; e < w * b; e += kPivotThreads) out[(size_t)(k & 1) * kPanel * b + e] = pc[e];
+      }
     }
     cluster_or_block_sync<kCluster>();
-    // everyone: pivot rows and panel of step k from the owner
-    const int* rflags = peer<kCluster>(m.flags, owner);
-    if (rflags[1] || rflags[2]) {
-      failed = rflags[1] ? BLOCKINV_ERR_SINGULAR : BLOCKINV_ERR_NONFINITE;
-      break;
+    // everyone: pivot rows and panel of step k from the owner. The flags, the
+    // panel's pivot rows and the first (for b <= 256 the only) batch of the
+    // panel are loaded together, so the remote reads cost one round trip. The
+    // other CTAs read the panel from the copy the owner left in global memory
+    // (the output buffer, free until the end; two alternating panel slots, so
+    // a slot is rewritten only after every CTA has passed the next cluster
+    // barrier): seven CTAs pulling it from the owner's shared memory at once
+    // would queue on that one SM. The cluster barrier orders those writes
+    // before these reads; the loads bypass L1, which may hold an older panel.
+    {
+      const int* rflags = peer<kCluster>(m.flags, owner);
+      const int* rperm = peer<kCluster>(m.perm, owner);
+      const bool via_l2 = kCluster && rank != owner;
+      const float4* rpanel4 = via_l2 ? reinterpret_cast<const float4*>(out + (size_t)(k & 1) * kPanel * b)
+                                     : reinterpret_cast<const float4*>(m.cols + (size_t)kslot * kPanel * b);
+      const int n4 = (w * b) / 4;  // float4 part; a remainder of w * b % 4 floats follows
+      constexpr int kPer = 8;      // float4 loads in flight per thread
+      float4 v[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int e4 = tid + q * kPivotThreads;
+        if (e4 < n4) v[q] = via_l2 ? __ldcg(rpanel4 + e4) : rpanel4[e4];
+      }
+      const int f1 = rflags[1], f2 = rflags[2];
+      const int rr = (tid < w) ? rperm[k * kPanel + tid] : 0;
+      if (f1 || f2) {
+        failed = f1 ? BLOCKINV_ERR_SINGULAR : BLOCKINV_ERR_NONFINITE;
+        break;
+      }
+      if (tid < w) {
+        m.perm[k * kPanel + tid] = rr;
+        m.srow[rr] = k * kPanel + tid;
+        m.inpanel[rr] = 1;
+      }
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int e4 = tid + q * kPivotThreads;
+        if (e4 < n4) reinterpret_cast<float4*>(m.panel)[e4] = v[q];
+      }
+      for (int base = kPer * kPivotThreads; base < n4; base += kPer * kPivotThreads) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          const int e4 = base + tid + q * kPivotThreads;
+          if (e4 < n4) v[q] = via_l2 ? __ldcg(rpanel4 + e4) : rpanel4[e4];
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          const int e4 = base + tid + q * kPivotThreads;
+          if (e4 < n4) reinterpret_cast<float4*>(m.panel)[e4] = v[q];
+        }
+      }
+      const float* rpanel = reinterpret_cast<const float*>(rpanel4);
+      for (int e = n4 * 4 + tid; e < w * b; e += kPivotThreads) m.panel[e] = via_l2 ? __ldcg(rpanel + e) : rpanel[e];
     }
-    const int* rperm = peer<kCluster>(m.perm, owner);
-    const T* rpanel = peer<kCluster>(m.cols, owner) + (size_t)kslot * kPanel * b;
-    if (tid < w) {
-      const int rr = rperm[k * kPanel + tid];
-      m.perm[k * kPanel + tid] = rr;
-      m.srow[rr] = k * kPanel + tid;
-      m.inpanel[rr] = 1;
-    }
-    for (int e = tid; e < w * b; e += kPivotThreads) m.panel[e] = rpanel[e];
     __syncthreads();
     // old pivot rows in my columns outside the panel
     const int my_cols = ncl;
@@ -499,8 +603,8 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
 }
 
 size_t blocked_smem_bytes(int b, int ncl, int elem) {
-  return (size_t)elem * ((size_t)ncl * b + (size_t)kPanel * b + (size_t)ncl * kPanel + kPanel + 8) +
-         sizeof(int) * (8 + 2 * (size_t)b + 4) + b + 64;
+  return (size_t)elem * ((size_t)ncl * b + (size_t)kPanel * b + (size_t)ncl * kPanel + 16 * kPanel) +
+         sizeof(unsigned long long) * 16 + sizeof(int) * (2 * (size_t)b + 4) + b + 64;
 }
 
 // Cluster size for the blocked kernel: one 32-column panel per CTA where

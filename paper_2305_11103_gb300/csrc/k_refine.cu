@@ -316,7 +316,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int j = j0 + tx;
-  double s2 = 0.0;
+  float s2 = 0.f;  // ||E||^2 needs a few digits only: FP32 keeps the FP64 pipe for E itself
   for (int ii = ty; ii < 32; ii += 8) {
     const int i = i0 + ii;
     double e = 0.0;
@@ -330,14 +330,16 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
       } else {
         e = -fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx) - r;   // (O_A D_X)_ij
       }
-      s2 = fma(e, e, s2);
+      const float ef = static_cast<float>(e);
+      s2 = fmaf(ef, ef, s2);
       if (Eout) Eout[(int64_t)i * lde + j] = e;
     }
     tile[ii][tx] = e;
   }
+  double s2d = s2;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-  if (tx == 0) red[ty] = s2;
+  for (int off = 16; off > 0; off >>= 1) s2d += __shfl_xor_sync(0xffffffffu, s2d, off);
+  if (tx == 0) red[ty] = s2d;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -350,9 +352,10 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     const int jg = j0 + jj;
     const int i = i0 + tx;
     if (jg < n && i < n) {
+      // hi + lo keep 22 bits, within FP32's 24: the split can start from FP32
       const float v = static_cast<float>(tile[tx][jj]);
       const float hi = tf32_rn(v);
-      const float lo = tf32_rn(static_cast<float>(tile[tx][jj] - static_cast<double>(hi)));
+      const float lo = tf32_rn(v - hi);
       Eop[(int64_t)jg * 2 * Kp + i] = hi;
       Eop[(int64_t)jg * 2 * Kp + Kp + i] = lo;
     }
