@@ -66,11 +66,13 @@ CPU_SAMPLE_N = 4096
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel source
 # it was measured on; reported as null once that source changes.
 NCU_TRAFFIC = {
-    # 6144 capture: 537.1 MB per launch (303.1 read + 234.0 write) for 5888 x 6144
-    # updated elements; scaled by units to 7936 x 8192 elements per launch at 8192.
-    ("schur_update_f64", "f64_8192"): {"bytes_per_launch": 537.1e6 * (7936 * 8192) / (5888 * 6144),
-                                       "src": "45a7462097825344"},
-    ("schur_update_f64", "f64_6144"): {"bytes_per_launch": 537.1e6, "src": "45a7462097825344"},
+    # 6144 capture of one elimination step with look-ahead: the next-block part
+    # (48.3 + 0.2 MB) and the rest (277.6 + 209.6 MB), 5888 x 6144 updated
+    # elements per step; per launch = the step's total over its two launches,
+    # scaled by updated elements to 7936 x 8192 per step at 8192.
+    ("schur_update_f64", "f64_8192"): {"bytes_per_launch": 535.7e6 / 2 * (7936 * 8192) / (5888 * 6144),
+                                       "src": "d214f7693a76c8d3"},
+    ("schur_update_f64", "f64_6144"): {"bytes_per_launch": 535.7e6 / 2, "src": "d214f7693a76c8d3"},
 }
 
 
@@ -259,6 +261,13 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def whole_job(ms_local, flops_per_rank, world):
+    """(ms, TFLOP/s) of the whole job: every rank did flops_per_rank of work;
+    the job takes as long as its slowest rank."""
+    ms = max_over_ranks(ms_local, world)
+    return ms, world * flops_per_rank / (ms / 1e3) / 1e12
+
+
 def src_hash(*names):
     h = hashlib.sha256()
     for nm in names:
@@ -380,30 +389,50 @@ def run_batched(args, bi, torch, stream):
     src = [torch.from_numpy(M).cuda() for M in mats]
     dst = [torch.empty_like(t) for t in src]
     ns = [t.shape[0] for t in src]
-    plan = bi.BatchPlan(ns, None, [t.data_ptr() for t in dst], ns)
     stt = torch.empty(len(mats), dtype=torch.int32, device="cuda")
 
     def refresh():
         torch._foreach_copy_(dst, src)
 
-    for _ in range(args.warmup):
-        refresh()
-        plan.run(stream, stt.data_ptr())
-    torch.cuda.synchronize()
-    bi.blockinv_trace_enable(True)
-    per = []
-    for _ in range(args.steps):
-        refresh()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        plan.run(stream, stt.data_ptr())
-        b.record(stream)
+    def time_plan():
+        plan = bi.BatchPlan(ns, None, [t.data_ptr() for t in dst], ns)
+        for _ in range(args.warmup):
+            refresh()
+            plan.run(stream, stt.data_ptr())
         torch.cuda.synchronize()
-        per.append(a.elapsed_time(b))
-    bi.blockinv_trace_enable(False)
-    tr = bi.blockinv_trace_summary()["batched_grouped_f64"]
+        bi.blockinv_trace_enable(True)
+        per = []
+        for _ in range(args.steps):
+            refresh()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(stream, stt.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            per.append(a.elapsed_time(b))
+        bi.blockinv_trace_enable(False)
+        tr = bi.blockinv_trace_summary()["batched_grouped_f64"]
+        plan.close()
+        return per, tr
+
+    # default partitions (four blocks of n/4), then the autotuner's choice per size class
+    bi.blockinv_batch_tuning_clear()
+    per_default, _ = time_plan()
+    t0 = time.time()
+    st_tune = bi.blockinv_batch_tune(ns, 3, stream)
+    tune_s = time.time() - t0
+    if st_tune != bi.OK:
+        raise bi.BlockinvError(st_tune, -1, "blockinv_batch_tune")
+    table = {}
+    for c in range(3, 10):
+        _, pc, tile = bi.blockinv_batch_tuning(c)
+        if pc:
+            table[f"{2 ** c}-{2 ** (c + 1) - 1}"] = {"blocks": pc, "tile": tile}
+    per, tr = time_plan()
+    bi.blockinv_batch_tuning_clear()
     ms = sum(per) / len(per)
+    ms_default = sum(per_default) / len(per_default)
     flops = sum(2.0 * m ** 3 for m in ns)
     g = inputs.rng(66)
     rhos = []
@@ -411,14 +440,16 @@ def run_batched(args, bi, torch, stream):
         Xi = dst[i].cpu().numpy()
         Ai = mats[i]
         rhos.append(np.linalg.norm(Ai @ Xi - np.eye(Ai.shape[0])) / (np.linalg.norm(Ai) * np.linalg.norm(Xi)))
-    plan.close()
     tfs = flops / (ms / 1e3) / 1e12
     out["uneven_2000"] = {
-        "workload": "2000 FP64 matrices, n log-uniform in [8, 512], U[-1,1] + n I (seed 6), 4 blocks of n/4",
+        "workload": "2000 FP64 matrices, n log-uniform in [8, 512], U[-1,1] + n I (seed 6); partitions and "
+                    "Schur tiles from the autotuner",
         "ms_per_batch": ms, "inverses_per_s": len(mats) / (ms / 1e3), "value": tfs, "unit": "TFLOP/s",
         "latency_ms": percentiles(per), "max_rho_sampled": float(max(rhos)),
         "failed": int((stt != 0).sum().item()),
         "launches_per_batch": tr["launches"] / args.steps,
+        "default_partition_ms_per_batch": ms_default,
+        "autotune": {"seconds": tune_s, "table": table},
         "roofline": {"bound": "alu", "kernel": "batched_grouped_f64 (graph)", "achieved": tfs,
                      "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "frac": tfs / FP64_PEAK_TFLOPS},
     }
@@ -536,11 +567,9 @@ def run_ours(args):
     bi.blockinv_trace_enable(False)
     clk = clocks.stop()
     trace = bi.blockinv_trace_summary()
-    ms = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms, world)
-    fp64_ms = ms
     flops = 2.0 * n ** 3
-    value = world * flops / (ms / 1e3) / 1e12
+    ms, value = whole_job(e0.elapsed_time(e1) / args.steps, flops, world)
+    fp64_ms = ms
     rho = bi.residual(dA, dX)
 
     top = max(trace.items(), key=lambda kv: kv[1]["ms"])
@@ -572,8 +601,8 @@ def run_ours(args):
                 raise bi.BlockinvError(st, -1, "blockinv_invert_host")
             if it >= args.warmup:
                 tot += t1 - t0
-        e2e_s = max_over_ranks(tot / args.steps, world)
-        e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
+        e2e_ms, e2e_value = whole_job(tot / args.steps * 1e3, flops, world)
+        e2e = {"value": e2e_value, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 8,
                "api": "blockinv_invert_host (pinned host buffer, copies inside the timed region)"}
         del hA, hX

@@ -175,6 +175,30 @@ int blockinv_batch_plan_create(int32_t count, const int32_t* n, const int32_t* p
 int blockinv_batch_plan_run(blockinv_batch_plan* plan, void* stream, int32_t* status_dev);
 int blockinv_batch_plan_destroy(blockinv_batch_plan* plan);
 
+/* Batch autotuner. Matrices of order n >= 8 fall into size classes
+ * c = floor(log2 n) (3 <= c <= 16). blockinv_batch_tune times, for every class
+ * present in n[count], each candidate partition (p near-equal blocks, every
+ * block of order 4..128) and Schur-update tile (64 x 64 or 32 x 32) on
+ * synthetic diagonally dominant matrices of that class's orders (up to 512
+ * of them; device memory allocated and freed inside; best of `reps` graph
+ * replays after one warm-up, 1 <= reps <= 100), and keeps the fastest in a
+ * process-wide table. Plans and blockinv_invert_batched calls made without
+ * explicit partitions then use the table (explicit partitions keep their
+ * blocks and take the class's tile). Blocking. Not part of the paper's
+ * method: it chooses among partitions the method allows.
+ * blockinv_batch_tuning reads a class's entry (nblocks 0 = not tuned);
+ * blockinv_batch_tuning_set writes one (nblocks 0 clears it); _clear forgets
+ * all; _save / _load write / read the table as text ("blockinv-batch-tuning 1"
+ * then one "class nblocks tile" line per tuned class; load replaces the whole
+ * table and leaves it unchanged on a malformed file). These five touch no
+ * GPU state. */
+int blockinv_batch_tune(int32_t count, const int32_t* n, int32_t reps, void* stream);
+int blockinv_batch_tuning(int32_t size_class, int32_t* nblocks, int32_t* tile);
+int blockinv_batch_tuning_set(int32_t size_class, int32_t nblocks, int32_t tile);
+int blockinv_batch_tuning_clear(void);
+int blockinv_batch_tuning_save(const char* path);
+int blockinv_batch_tuning_load(const char* path);
+
 /* ------------------------------------------------------------- serving ---
  * A serving context inverts independent requests (one matrix each, any
  * order and mode) as they arrive. A worker thread admits queued requests
@@ -234,7 +258,10 @@ typedef struct {
   int32_t split;       /* mixed modes: 0 or 2 (default) = split each Schur-update operand */
                        /* into hi + lo and run hi*hi + hi*lo + lo*hi on the tensor cores; */
                        /* 1 = a single product                                           */
-  int32_t reserved[3];
+  int32_t pivot_f64;   /* mixed modes: 0 (default) = invert again in FP64 arithmetic the */
+                       /* pivot blocks whose estimate ||P||_inf ||P^-1||_inf from the    */
+                       /* FP32 inverse exceeds 1e5; 1 = every pivot block; -1 = none     */
+  int32_t reserved[2];
 } blockinv_options;
 
 typedef struct {
@@ -245,7 +272,8 @@ typedef struct {
   double rho_initial;     /* rho of the unrefined low-precision inverse, else -1       */
   int32_t used_fallback;  /* 1 if the FP64 path produced the result after a failed     */
                           /* refinement                                                */
-  int32_t reserved[7];
+  int32_t fp64_pivots;    /* mixed modes: pivot blocks inverted again in FP64          */
+  int32_t reserved[6];
 } blockinv_info;
 
 /* blockinv_invert with options and a report (either pointer may be NULL). */

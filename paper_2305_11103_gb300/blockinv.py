@@ -40,6 +40,12 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "blockinv_batch_plan_run": (_int, [_vp, _vp, _vp]),
     "blockinv_batch_plan_destroy": (_int, [_vp]),
+    "blockinv_batch_tune": (_int, [_i32, _i32p, _i32, _vp]),
+    "blockinv_batch_tuning": (_int, [_i32, _i32p, _i32p]),
+    "blockinv_batch_tuning_set": (_int, [_i32, _i32, _i32]),
+    "blockinv_batch_tuning_clear": (_int, []),
+    "blockinv_batch_tuning_save": (_int, [ctypes.c_char_p]),
+    "blockinv_batch_tuning_load": (_int, [ctypes.c_char_p]),
     "blockinv_ctx_create": (_int, [_int, ctypes.c_size_t, _int, ctypes.POINTER(ctypes.c_void_p)]),
     "blockinv_submit": (_int, [_vp, _i64, _i32, _i32p, _vp, _i64, _int, _int, ctypes.POINTER(ctypes.c_uint64)]),
     "blockinv_poll": (_int, [_vp, ctypes.c_uint64, _vp]),
@@ -64,13 +70,13 @@ SIGNATURES = {
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("fallback", ctypes.c_int32),
-                ("split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("split", ctypes.c_int32), ("pivot_f64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("refine_iters", ctypes.c_int32), ("failing_block", ctypes.c_int64),
                 ("rho", ctypes.c_double), ("rho_initial", ctypes.c_double), ("used_fallback", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("fp64_pivots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -133,10 +139,10 @@ def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_p
 
 
 def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1,
-                       split=0):
+                       split=0, pivot_f64=0):
     """Returns (status, Info)."""
     p, arr, _ = _sizes(block_sizes)
-    opt = Options(tol=tol, max_refine=max_refine, fallback=fallback, split=split)
+    opt = Options(tol=tol, max_refine=max_refine, fallback=fallback, split=split, pivot_f64=pivot_f64)
     info = Info()
     st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
                                   ctypes.byref(info))
@@ -169,6 +175,34 @@ def blockinv_invert_batched(ns, partitions, A_ptrs, ldas, mode=F64, stream=None,
     count, n_arr, p_arr, s_arr, a_arr, l_arr = _batch_args(ns, partitions, A_ptrs, ldas)
     return lib().blockinv_invert_batched(count, n_arr, p_arr, s_arr, a_arr, l_arr, _mode(mode),
                                          _stream_ptr(stream), status_ptr)
+
+
+def blockinv_batch_tune(ns, reps=3, stream=None):
+    n_arr = (ctypes.c_int32 * len(ns))(*ns)
+    return lib().blockinv_batch_tune(len(ns), n_arr, reps, _stream_ptr(stream))
+
+
+def blockinv_batch_tuning(size_class):
+    """(status, nblocks, tile) of one size class (nblocks 0: not tuned)."""
+    p, t = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = lib().blockinv_batch_tuning(size_class, ctypes.byref(p), ctypes.byref(t))
+    return st, p.value, t.value
+
+
+def blockinv_batch_tuning_set(size_class, nblocks, tile):
+    return lib().blockinv_batch_tuning_set(size_class, nblocks, tile)
+
+
+def blockinv_batch_tuning_clear():
+    return lib().blockinv_batch_tuning_clear()
+
+
+def blockinv_batch_tuning_save(path):
+    return lib().blockinv_batch_tuning_save(str(path).encode())
+
+
+def blockinv_batch_tuning_load(path):
+    return lib().blockinv_batch_tuning_load(str(path).encode())
 
 
 class BatchPlan:

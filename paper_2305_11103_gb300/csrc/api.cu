@@ -223,7 +223,17 @@ struct Options {
   int max_refine = 5;
   bool fallback = true;
   int split = 2;  // operand slices of the mixed Schur update (1 or 2)
+  int pivot_f64 = 0;  // 0: FP64 re-inversion of ill-conditioned pivot blocks; 1: of all; -1: none
 };
+
+// Pivot blocks whose estimate ||P||_inf ||P^-1||_inf exceeds this are inverted
+// again in FP64 arithmetic by the mixed path (the FP32 Gauss-Jordan's own
+// error grows with that estimate times the FP32 unit roundoff).
+constexpr float kPivotCondLimit = 1e5f;
+
+float pivot_cond_limit(const Options& o) {
+  return o.pivot_f64 > 0 ? -1.f : (o.pivot_f64 < 0 ? 0.f : kPivotCondLimit);
+}
 
 Options resolve(const blockinv_options* o) {
   Options r;
@@ -232,14 +242,15 @@ Options resolve(const blockinv_options* o) {
     if (o->max_refine >= 0) r.max_refine = o->max_refine;
     r.fallback = o->fallback != 0;
     if (o->split == 1) r.split = 1;
+    r.pivot_f64 = o->pivot_f64 > 0 ? 1 : (o->pivot_f64 < 0 ? -1 : 0);
   }
   return r;
 }
 
 // Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
 // of the low-precision inverse).
-int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int nsl, int32_t* status,
-                       cudaStream_t s) {
+int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int nsl, float cond_limit,
+                       int32_t* piv_words, int32_t* status, cudaStream_t s) {
   const int n = pl.n;
   const int64_t ld32 = (n + 31) / 32 * 32;
   const int kpad = mixed_kpad(pl.bmax);
@@ -256,7 +267,8 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int ns
     e = launch_cast_f64_to_f32(A, lda, X32, ld32, n, s);
   }
   if (e == cudaSuccess)
-    e = mixed_elimination(pl, bf16, nsl, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, status, s);
+    e = mixed_elimination(pl, bf16, nsl, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, cond_limit,
+                          piv_words, status, s);
   if (e == cudaSuccess) {
     TraceScope t("cast_f32_to_f64", 0, 12.0 * n * (double)n, s);
     e = launch_cast_f32_to_f64(X32, ld32, A, lda, n, s);
@@ -268,7 +280,7 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int ns
 // residuals and the FP64 fallback), the refinement workspace, the rho history
 // and the refinement control words. Released in stream order.
 struct MixedState {
-  AsyncBuf a0, ws, hist, ctl;
+  AsyncBuf a0, ws, hist, ctl, piv;
   int max_refine = 0;
   double* A0() const { return static_cast<double*>(a0.ptr); }
 };
@@ -282,11 +294,14 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
   if (e == cudaSuccess) e = ms.hist.alloc(sizeof(double) * (opt.max_refine + 1), s);
   if (e == cudaSuccess) e = ms.ctl.alloc(4 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.ctl.ptr, 0, 4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = ms.piv.alloc(2 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ms.piv.ptr, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.hist.ptr, 0xFF, sizeof(double) * (opt.max_refine + 1), s);
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(ms.a0.ptr, row, A, sizeof(double) * lda, row, n, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, status, s);
+  int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, pivot_cond_limit(opt), static_cast<int32_t*>(ms.piv.ptr),
+                              status, s);
   if (st != BLOCKINV_OK || opt.max_refine == 0) return st;
   e = ms.ws.alloc(refine_workspace_bytes(n, kResidualSlices, opt.max_refine), s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -317,10 +332,13 @@ void read_mixed_info(const MixedState& ms, cudaStream_t s, blockinv_info* info) 
   if (!info || !ms.hist.ptr) return;
   std::vector<double> hist(ms.max_refine + 1, -1.0);
   int32_t ctl[4] = {0, 0, 0, -1};
+  int32_t piv[2] = {0, 0};
   cudaMemcpyAsync(hist.data(), ms.hist.ptr, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(ctl, ms.ctl.ptr, sizeof(ctl), cudaMemcpyDeviceToHost, s);
+  if (ms.piv.ptr) cudaMemcpyAsync(piv, ms.piv.ptr, sizeof(piv), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return;
   info->refine_iters = ctl[1];
+  info->fp64_pivots = piv[1];
   if (ctl[3] >= 0) {
     info->rho_initial = hist[0];
     info->rho = hist[ctl[3]];

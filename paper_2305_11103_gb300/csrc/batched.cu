@@ -1,17 +1,27 @@
 // Batched inversion of many independent matrices of uneven orders (FP64).
 //
-// Elimination step k of every matrix runs in three grouped launches over the
-// whole batch: one pivot-block Gauss-Jordan CTA per matrix, one row-panel CTA
-// per 32-column strip, one Schur-update CTA per 64 x 64 tile, with the
-// matrix of each CTA found from prefix sums in a device descriptor table. A
-// batch of 2000 matrices of 4 blocks each thus costs 12 launches, not 24000.
-// A plan builds the descriptor tables and the per-matrix workspace once; its
-// first run captures the launch sequence in a CUDA graph, and later runs
-// replay the graph on the caller's stream.
+// Elimination step k of every matrix runs in grouped launches over the whole
+// batch: one pivot-block Gauss-Jordan CTA per matrix, one row-panel CTA per
+// 32-column strip, one Schur-update CTA per 64 x 64 (or 32 x 32) tile, with
+// the matrix of each CTA found from prefix sums in a device descriptor table.
+// A batch of 2000 matrices of 4 blocks each thus costs about 12 launches, not
+// 24000. A plan builds the descriptor tables and the per-matrix workspace
+// once; its first run captures the launch sequence in a CUDA graph, and later
+// runs replay the graph on the caller's stream.
 //
 // Pivot blocks of order <= 128 use the grouped one-CTA kernel; larger ones
 // (rare in a batch) use the per-matrix cluster kernel, inside the same graph.
+//
+// Autotuner. Matrices fall into size classes c = floor(log2 n) (n >= 8). For
+// each class present in a batch, the tuner times every candidate (number of
+// near-equal blocks p, Schur tile 64 or 32) on synthetic diagonally dominant
+// matrices of that class's orders, and keeps the fastest in a process-wide
+// table (which can be saved to and loaded from a text file). Plans built
+// without explicit partitions use the table.
 #include <algorithm>
+#include <cstdio>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "batched.h"
@@ -26,6 +36,49 @@ __global__ void gather_status_kernel(const int32_t* __restrict__ words, int coun
 }
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+constexpr int kMinClass = 3;   // orders 8..15
+constexpr int kMaxClass = 16;  // orders up to 2^17 - 1 (plans accept n <= 2^16)
+
+struct Tuned {
+  int p = 0;      // blocks (0 = not tuned)
+  int tile = 64;  // Schur tile
+};
+
+std::mutex g_tune_mu;
+Tuned g_tune[kMaxClass + 1];
+
+int size_class(int n) {
+  if (n < 8) return -1;
+  int c = 0;
+  while ((2 << c) <= n) ++c;
+  return c;  // 2^c <= n < 2^(c+1)
+}
+
+// n split into p near-equal blocks, the last (n mod p) one larger.
+void equal_partition(int n, int p, std::vector<int>* out) {
+  out->clear();
+  const int q = n / p, r = n % p;
+  for (int i = 0; i < p; ++i) out->push_back(q + (i >= p - r ? 1 : 0));
+}
+
+// Synthetic diagonally dominant matrices for timing: a[i][j] = h(m, i, j) in
+// [-1, 1) plus n on the diagonal (h: a 64-bit integer mix of the indices).
+__global__ void fill_tune_kernel(double* const* __restrict__ A, const int32_t* __restrict__ n) {
+  const int m = blockIdx.x;
+  double* a = A[m];
+  const int nn = n[m];
+  for (int64_t e = threadIdx.x; e < (int64_t)nn * nn; e += blockDim.x) {
+    unsigned long long z = (static_cast<unsigned long long>(m) << 40) ^ static_cast<unsigned long long>(e);
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    const int i = static_cast<int>(e / nn), j = static_cast<int>(e - (int64_t)i * nn);
+    a[e] = u + (i == j ? static_cast<double>(nn) : 0.0);
+  }
+}
 
 }  // namespace
 
@@ -48,12 +101,25 @@ void batch_default_partition(int n, std::vector<int>* out) {
     return;
   }
   const int p = std::max(4, (n + kGroupedMaxB - 1) / kGroupedMaxB);
-  const int q = n / p, r = n % p;
-  for (int i = 0; i < p; ++i) out->push_back(q + (i >= p - r ? 1 : 0));
+  equal_partition(n, p, out);
+}
+
+void batch_partition(int n, std::vector<int>* out, int* tile) {
+  const int c = size_class(n);
+  Tuned t;
+  if (c >= kMinClass && c <= kMaxClass) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    t = g_tune[c];
+  }
+  *tile = t.tile;
+  if (t.p > 0 && t.p <= n && (n + t.p - 1) / t.p <= BLOCKINV_MAX_BLOCK)
+    equal_partition(n, t.p, out);
+  else
+    batch_default_partition(n, out);
 }
 
 int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
-                      double* const* A, const int64_t* lda, BatchPlan** out) {
+                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile) {
   *out = nullptr;
   if (count < 1 || !n || !A || !lda || (block_sizes && !p)) return BLOCKINV_ERR_INVALID;
   BatchPlan tmp;
@@ -62,13 +128,17 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
   size_t scur = 0;
   for (int m = 0; m < count; ++m) {
     if (n[m] < 1 || n[m] > (1 << 16) || lda[m] < n[m] || !A[m]) return BLOCKINV_ERR_INVALID;
+    int tile = 64;
     if (block_sizes) {
       if (p[m] < 1 || p[m] > n[m]) return BLOCKINV_ERR_INVALID;
       part.assign(block_sizes + scur, block_sizes + scur + p[m]);
       scur += p[m];
+      std::vector<int> unused;
+      batch_partition(n[m], &unused, &tile);  // the class's tuned tile, if any
     } else {
-      batch_default_partition(n[m], &part);
+      batch_partition(n[m], &part, &tile);
     }
+    if (force_tile) tile = force_tile;
     int64_t sum = 0;
     for (int b : part) {
       if (b < 1 || b > BLOCKINV_MAX_BLOCK) return BLOCKINV_ERR_INVALID;
@@ -78,6 +148,7 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
     tmp.n.push_back(n[m]);
     tmp.p.push_back((int)part.size());
     tmp.off.push_back((int)tmp.sizes.size());
+    tmp.tile.push_back(tile);
     tmp.sizes.insert(tmp.sizes.end(), part.begin(), part.end());
     tmp.A.push_back(A[m]);
     tmp.lda.push_back(lda[m]);
@@ -92,7 +163,7 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
     ws_off[m] = ws_total;
     ws_total = align256(ws_total + sizeof(double) * ((size_t)bm[m] * bm[m] + (size_t)tmp.n[m] * bm[m]));
   }
-  // descriptor tables, step by step
+  // descriptor tables, step by step: the 64-tile items, then the 32-tile ones
   std::vector<GroupStep> items;
   std::vector<int32_t> starts;
   tmp.steps.resize(tmp.max_steps);
@@ -101,38 +172,46 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
     BatchStep& st = tmp.steps[k];
     st.item_off = (int)items.size();
     st.cs_off = (int)starts.size();
-    int cols = 0, tiles = 0;
-    std::vector<int32_t> ts{0};
+    int cols = 0;
     starts.push_back(0);
-    for (int m = 0; m < count; ++m) {
-      if (k >= tmp.p[m]) continue;
-      const int b = tmp.sizes[tmp.off[m] + k];
-      int o = 0;
-      for (int q = 0; q < k; ++q) o += tmp.sizes[tmp.off[m] + q];
-      GroupStep g{};
-      g.X = tmp.A[m];
-      g.ldx = tmp.lda[m];
-      g.n = tmp.n[m];
-      g.o = o;
-      g.b = b;
-      g.k = k;
-      items.push_back(g);
-      item_m.push_back(m);
-      const int nn = tmp.n[m];
-      cols += (nn + 31) / 32;
-      tiles += ((nn + 63) / 64) * ((nn + 63) / 64);
-      starts.push_back(cols);
-      ts.push_back(tiles);
-      st.bmax = std::max(st.bmax, b);
-      ++st.count;
-      const double bd = b, nd = nn, rest = nn - b;
-      tmp.flops += 2.0 * bd * bd * bd + 2.0 * bd * bd * rest + 2.0 * bd * rest * nd;
-      tmp.bytes += 8.0 * (2.0 * bd * bd + 2.0 * bd * nd + 2.0 * rest * nd + 2.0 * rest * bd);
+    std::vector<int32_t> ts[2] = {{0}, {0}};
+    int tiles[2] = {0, 0};
+    for (int grp = 0; grp < 2; ++grp) {
+      const int want = grp == 0 ? 64 : 32;
+      for (int m = 0; m < count; ++m) {
+        if (k >= tmp.p[m] || tmp.tile[m] != want) continue;
+        const int b = tmp.sizes[tmp.off[m] + k];
+        int o = 0;
+        for (int q = 0; q < k; ++q) o += tmp.sizes[tmp.off[m] + q];
+        GroupStep g{};
+        g.X = tmp.A[m];
+        g.ldx = tmp.lda[m];
+        g.n = tmp.n[m];
+        g.o = o;
+        g.b = b;
+        g.k = k;
+        items.push_back(g);
+        item_m.push_back(m);
+        const int nn = tmp.n[m];
+        cols += (nn + 31) / 32;
+        tiles[grp] += ((nn + want - 1) / want) * ((nn + want - 1) / want);
+        starts.push_back(cols);
+        ts[grp].push_back(tiles[grp]);
+        st.bmax = std::max(st.bmax, b);
+        ++st.count;
+        if (grp == 0) ++st.count64;
+        const double bd = b, nd = nn, rest = nn - b;
+        tmp.flops += 2.0 * bd * bd * bd + 2.0 * bd * bd * rest + 2.0 * bd * rest * nd;
+        tmp.bytes += 8.0 * (2.0 * bd * bd + 2.0 * bd * nd + 2.0 * rest * nd + 2.0 * rest * bd);
+      }
     }
     st.cols = cols;
-    st.tiles = tiles;
-    st.ts_off = (int)starts.size();
-    starts.insert(starts.end(), ts.begin(), ts.end());
+    st.tiles64 = tiles[0];
+    st.tiles32 = tiles[1];
+    st.ts_off64 = (int)starts.size();
+    starts.insert(starts.end(), ts[0].begin(), ts[0].end());
+    st.ts_off32 = (int)starts.size();
+    starts.insert(starts.end(), ts[1].begin(), ts[1].end());
   }
   const size_t o_items = 0;
   const size_t o_starts = align256(sizeof(GroupStep) * items.size());
@@ -179,7 +258,11 @@ cudaError_t batch_enqueue(const BatchPlan& pl, cudaStream_t s) {
                                        s);
     }
     if (e == cudaSuccess) e = launch_row_panel_grouped(it, st.count, pl.starts + st.cs_off, st.cols, st.bmax, s);
-    if (e == cudaSuccess) e = launch_schur_update_grouped(it, st.count, pl.starts + st.ts_off, st.tiles, s);
+    if (e == cudaSuccess)
+      e = launch_schur_update_grouped(it, st.count64, pl.starts + st.ts_off64, st.tiles64, 64, s);
+    if (e == cudaSuccess)
+      e = launch_schur_update_grouped(it + st.count64, st.count - st.count64, pl.starts + st.ts_off32, st.tiles32,
+                                      32, s);
   }
   return e;
 }
@@ -219,6 +302,109 @@ void batch_plan_destroy(BatchPlan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->dev) cudaFree(pl->dev);
   delete pl;
+}
+
+namespace {
+
+// Time one candidate (p blocks, Schur tile) on the synthetic matrices of one
+// class: graph replay, best of `reps` after one warm-up; the matrices are
+// refilled before every run (an inverse is not inverted again).
+int time_candidate(const std::vector<int32_t>& ns, double* const* hA, double* const* dA, const int32_t* dn,
+                   int p, int tile, int reps, cudaStream_t s, float* best_ms) {
+  const int count = (int)ns.size();
+  std::vector<int32_t> pp(count, p), sizes;
+  std::vector<int64_t> lda(ns.begin(), ns.end());
+  std::vector<int> part;
+  for (int m = 0; m < count; ++m) {
+    equal_partition(ns[m], p, &part);
+    sizes.insert(sizes.end(), part.begin(), part.end());
+  }
+  BatchPlan* pl = nullptr;
+  const int st = batch_plan_create(count, ns.data(), pp.data(), sizes.data(), hA, lda.data(), &pl, tile);
+  if (st != BLOCKINV_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = cudaSuccess;
+  *best_ms = 1e30f;
+  for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+    fill_tune_kernel<<<count, 256, 0, s>>>(dA, dn);
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = batch_run(*pl, s, nullptr, true);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess && r >= 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) *best_ms = std::min(*best_ms, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_plan_destroy(pl);
+  return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+}
+
+}  // namespace
+
+int batch_tune(int32_t count, const int32_t* n, int reps, cudaStream_t s) {
+  if (count < 1 || !n || reps < 1 || reps > 100) return BLOCKINV_ERR_INVALID;
+  std::map<int, std::vector<int32_t>> classes;
+  for (int m = 0; m < count; ++m) {
+    if (n[m] < 1 || n[m] > (1 << 16)) return BLOCKINV_ERR_INVALID;
+    const int c = size_class(n[m]);
+    if (c >= kMinClass && c <= kMaxClass && classes[c].size() < 512) classes[c].push_back(n[m]);
+  }
+  for (auto& kv : classes) {
+    const int c = kv.first;
+    const std::vector<int32_t>& ns = kv.second;
+    const int nmin = *std::min_element(ns.begin(), ns.end());
+    const int nmax = *std::max_element(ns.begin(), ns.end());
+    // synthetic matrices of the class's orders
+    size_t total = 0;
+    std::vector<size_t> off(ns.size());
+    for (size_t m = 0; m < ns.size(); ++m) {
+      off[m] = total;
+      total += align256(sizeof(double) * (size_t)ns[m] * ns[m]);
+    }
+    const size_t o_ptr = total, o_n = o_ptr + align256(sizeof(double*) * ns.size());
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, o_n + sizeof(int32_t) * ns.size()) != cudaSuccess) return BLOCKINV_ERR_NOMEM;
+    char* base = static_cast<char*>(buf);
+    std::vector<double*> hA(ns.size());
+    for (size_t m = 0; m < ns.size(); ++m) hA[m] = reinterpret_cast<double*>(base + off[m]);
+    cudaError_t e = cudaMemcpy(base + o_ptr, hA.data(), sizeof(double*) * ns.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_n, ns.data(), sizeof(int32_t) * ns.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(buf);
+      return BLOCKINV_ERR_CUDA;
+    }
+    double* const* dA = reinterpret_cast<double* const*>(base + o_ptr);
+    const int32_t* dn = reinterpret_cast<const int32_t*>(base + o_n);
+    // candidates: p near-equal blocks (every block of every order in 4..128,
+    // the grouped pivot kernel's range), Schur tiles 64 and 32
+    Tuned best;
+    float best_ms = 1e30f;
+    int st = BLOCKINV_OK;
+    for (int p : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+      if (p > nmin || (nmax + p - 1) / p > kGroupedMaxB || nmin / p < 4) continue;
+      for (int tile : {64, 32}) {
+        float ms = 0.f;
+        st = time_candidate(ns, hA.data(), dA, dn, p, tile, reps, s, &ms);
+        if (st != BLOCKINV_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.p = p;
+          best.tile = tile;
+        }
+      }
+      if (st != BLOCKINV_OK) break;
+    }
+    cudaFree(buf);
+    if (st != BLOCKINV_OK) return st;
+    if (best.p > 0) {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tune[c] = best;
+    }
+  }
+  return BLOCKINV_OK;
 }
 
 }  // namespace blockinv
@@ -269,6 +455,72 @@ int blockinv_invert_batched(int32_t count, const int32_t* n, const int32_t* p, c
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   batch_plan_destroy(pl);
   return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+}
+
+int blockinv_batch_tune(int32_t count, const int32_t* n, int32_t reps, void* stream) {
+  return batch_tune(count, n, reps, static_cast<cudaStream_t>(stream));
+}
+
+int blockinv_batch_tuning(int32_t size_class, int32_t* nblocks, int32_t* tile) {
+  if (size_class < kMinClass || size_class > kMaxClass || !nblocks || !tile) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  *nblocks = g_tune[size_class].p;
+  *tile = g_tune[size_class].tile;
+  return BLOCKINV_OK;
+}
+
+int blockinv_batch_tuning_set(int32_t size_class, int32_t nblocks, int32_t tile) {
+  if (size_class < kMinClass || size_class > kMaxClass || nblocks < 0 || nblocks > (1 << 16) ||
+      (tile != 32 && tile != 64))
+    return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[size_class].p = nblocks;
+  g_tune[size_class].tile = tile;
+  return BLOCKINV_OK;
+}
+
+int blockinv_batch_tuning_clear(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (Tuned& t : g_tune) t = Tuned();
+  return BLOCKINV_OK;
+}
+
+int blockinv_batch_tuning_save(const char* path) {
+  if (!path) return BLOCKINV_ERR_INVALID;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return BLOCKINV_ERR_INVALID;
+  std::fprintf(f, "blockinv-batch-tuning 1\n");
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (int c = kMinClass; c <= kMaxClass; ++c)
+      if (g_tune[c].p > 0) std::fprintf(f, "%d %d %d\n", c, g_tune[c].p, g_tune[c].tile);
+  }
+  return std::fclose(f) == 0 ? BLOCKINV_OK : BLOCKINV_ERR_INVALID;
+}
+
+int blockinv_batch_tuning_load(const char* path) {
+  if (!path) return BLOCKINV_ERR_INVALID;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return BLOCKINV_ERR_INVALID;
+  int version = 0, st = BLOCKINV_OK;
+  Tuned table[kMaxClass + 1];
+  if (std::fscanf(f, "blockinv-batch-tuning %d", &version) != 1 || version != 1) st = BLOCKINV_ERR_INVALID;
+  int c, p, tile;
+  while (st == BLOCKINV_OK) {
+    const int got = std::fscanf(f, "%d %d %d", &c, &p, &tile);
+    if (got == EOF) break;
+    if (got != 3 || c < kMinClass || c > kMaxClass || p < 0 || p > (1 << 16) || (tile != 32 && tile != 64)) {
+      st = BLOCKINV_ERR_INVALID;
+      break;
+    }
+    table[c].p = p;
+    table[c].tile = tile;
+  }
+  std::fclose(f);
+  if (st != BLOCKINV_OK) return st;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (int k = 0; k <= kMaxClass; ++k) g_tune[k] = table[k];
+  return BLOCKINV_OK;
 }
 
 }  // extern "C"

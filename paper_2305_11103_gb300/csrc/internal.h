@@ -66,17 +66,26 @@ struct GroupStep {
 constexpr int kGroupedMaxB = 128;
 cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s);
 // Grouped K2 / K3 over `count` items; col_start / tile_start are exclusive
-// prefix sums (count + 1 entries) of each item's column strips / 64 x 64 tiles.
+// prefix sums (count + 1 entries) of each item's column strips / tile x tile
+// tiles (tile = 64 or 32).
 cudaError_t launch_row_panel_grouped(const GroupStep* items, int count, const int32_t* col_start,
                                      int total_cols, int bmax, cudaStream_t s);
 cudaError_t launch_schur_update_grouped(const GroupStep* items, int count, const int32_t* tile_start,
-                                        int total_tiles, cudaStream_t s);
+                                        int total_tiles, int tile, cudaStream_t s);
 
 // K1: P^-1 of the b x b pivot block at P (leading dimension ldp) into Pinv
 // (leading dimension ldo). T = double (FP64 path) or float (mixed path).
 template <typename T>
 cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
                                  int32_t* status, int block_index, cudaStream_t s);
+
+// Mixed path, after the FP32 pivot inverse Pinv of the FP32 block P: estimate
+// kappa = ||P||_inf ||Pinv||_inf on the device; if kappa > cond_limit (always
+// when cond_limit < 0), set *gate, count the block in *count and invert P again
+// in FP64 arithmetic (FP32 in and out). gate and count are device int32.
+cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
+                                     int block_index, float cond_limit, int32_t* gate, int32_t* count,
+                                     cudaStream_t s);
 
 // K2 (FP64): row panel X[o:o+b, j] <- Pinv X[o:o+b, j] for j outside the
 // pivot columns, X[o:o+b, o:o+b] <- Pinv, and U <- X[:, o:o+b] for rows
@@ -107,8 +116,11 @@ int mixed_kpad(int bmax);
 // bmax^2 floats; U and Vt are n x (nsl * mixed_kpad(bmax)) operands of 4
 // (TF32) or 2 (BF16) bytes per element; nsl = 2 splits each operand into
 // hi + lo and runs the three products hi*hi + hi*lo + lo*hi.
+// pivot_cond_limit: > 0, pivot blocks whose condition estimate exceeds it are
+// inverted again in FP64 arithmetic (launch_pivot_f64_for_ill); < 0, every
+// block; 0, none. piv_words: device int32[2] (gate, count of FP64 pivots).
 cudaError_t mixed_elimination(const Plan& pl, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
-                              void* Vt, int32_t* status, cudaStream_t s);
+                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s);
 
 // Batched small matrices, order 1..8, one thread per matrix (k_small.cu).
 cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* status, cudaStream_t s);

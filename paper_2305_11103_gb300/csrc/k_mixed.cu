@@ -238,7 +238,7 @@ cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64
 int mixed_kpad(int bmax) { return (bmax + 63) / 64 * 64; }
 
 cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
-                              void* Vt, int32_t* status, cudaStream_t s) {
+                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s) {
   const int n = mp.n;
   const int kpad = mixed_kpad(mp.bmax);
   const int eb = bf16 ? 2 : 4;
@@ -255,6 +255,12 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     {
       TraceScope t("pivot_inverse_f32", 2.0 * bd * bd * bd, 8.0 * bd * bd, s);
       e = launch_pivot_inverse<float>(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, (int)k, s);
+    }
+    if (e == cudaSuccess && pivot_cond_limit != 0.f && piv_words) {
+      // FP64 arithmetic for the pivot blocks that the condition estimate flags
+      TraceScope t("pivot_f64_if_ill", 0, 8.0 * bd * bd, s);
+      e = launch_pivot_f64_for_ill(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, (int)k, pivot_cond_limit,
+                                   piv_words, piv_words + 1, s);
     }
     if (e != cudaSuccess) break;
     {

@@ -74,9 +74,11 @@ __device__ __forceinline__ void argmax_step(T& bv, int& bi, T ov, int oi) {
   }
 }
 
-template <typename T, bool kCluster>
-__device__ __forceinline__ void pivot_gj_body(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog,
-                                              T* __restrict__ out, int64_t ldo, int32_t* status,
+// T: arithmetic type; TIO: the type of P and of the output (FP32 blocks of the
+// mixed path can be inverted in FP64).
+template <typename T, typename TIO, bool kCluster>
+__device__ __forceinline__ void pivot_gj_body(const TIO* __restrict__ P, int64_t ldp, int b, int R, int jlog,
+                                              TIO* __restrict__ out, int64_t ldo, int32_t* status,
                                               int block_index) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* rows = reinterpret_cast<T*>(smem_raw);   // R x b, this CTA's rows
@@ -108,7 +110,7 @@ __device__ __forceinline__ void pivot_gj_body(const T* __restrict__ P, int64_t l
   int bad = 0;
   for (int r = rr; r < nloc; r += rstep) {
     for (int j = jj; j < b; j += jw) {
-      T v = P[(int64_t)(r0 + r) * ldp + j];
+      T v = static_cast<T>(P[(int64_t)(r0 + r) * ldp + j]);
       if (!isfinite(v)) bad = 1;
       rows[(size_t)r * b + j] = v;
     }
@@ -212,15 +214,60 @@ __device__ __forceinline__ void pivot_gj_body(const T* __restrict__ P, int64_t l
   for (int r = rr; r < nloc; r += rstep) {
     const int i = step_of_row[r];
     const T* row = rows + (size_t)r * b;
-    for (int j = jj; j < b; j += jw) out[(int64_t)i * ldo + perm[j]] = row[j];
+    for (int j = jj; j < b; j += jw) out[(int64_t)i * ldo + perm[j]] = static_cast<TIO>(row[j]);
   }
 }
 
-template <typename T, bool kCluster>
+// gate (may be null): the kernel runs only if *gate != 0 (read by every CTA
+// before any cluster barrier, so the whole cluster leaves together).
+template <typename T, typename TIO, bool kCluster>
 __global__ void __launch_bounds__(kPivotThreads)
-pivot_gj_kernel(const T* __restrict__ P, int64_t ldp, int b, int R, int jlog, T* __restrict__ out, int64_t ldo,
-                int32_t* status, int block_index) {
-  pivot_gj_body<T, kCluster>(P, ldp, b, R, jlog, out, ldo, status, block_index);
+pivot_gj_kernel(const TIO* __restrict__ P, int64_t ldp, int b, int R, int jlog, TIO* __restrict__ out,
+                int64_t ldo, int32_t* status, int block_index, const int32_t* gate) {
+  if (gate && *(volatile const int32_t*)gate == 0) return;
+  pivot_gj_body<T, TIO, kCluster>(P, ldp, b, R, jlog, out, ldo, status, block_index);
+}
+
+// Condition estimate of an FP32 pivot block after its FP32 inverse:
+// kappa = ||P||_inf ||P^-1||_inf. *gate = 1 when kappa > limit (or is not
+// finite), and then *count is incremented; limit < 0 sets the gate always.
+__global__ void __launch_bounds__(kPivotThreads)
+pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restrict__ Pinv, int64_t ldo, int b,
+                  float limit, int32_t* gate, int32_t* count, const int32_t* status) {
+  __shared__ float red[2][kPivotThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float mp = 0.f, mi = 0.f;
+  for (int r = warp; r < b; r += kPivotThreads / 32) {
+    float sp = 0.f, si = 0.f;
+    for (int j = lane; j < b; j += 32) {
+      sp += fabsf(P[(int64_t)r * ldp + j]);
+      si += fabsf(Pinv[(int64_t)r * ldo + j]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sp += __shfl_xor_sync(0xffffffffu, sp, off);
+      si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    mp = fmaxf(mp, sp);
+    mi = fmaxf(mi, si);
+  }
+  if (lane == 0) {
+    red[0][warp] = mp;
+    red[1][warp] = mi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float a = 0.f, c = 0.f;
+    for (int w = 0; w < kPivotThreads / 32; ++w) {
+      a = fmaxf(a, red[0][w]);
+      c = fmaxf(c, red[1][w]);
+    }
+    const float kappa = a * c;
+    const bool ill = limit < 0.f || !(kappa <= limit);
+    const bool live = *(volatile const int32_t*)status == 0;
+    *gate = (ill && live) ? 1 : 0;
+    if (ill && live) atomicAdd(count, 1);
+  }
 }
 
 // Grouped form: one CTA per matrix of a batch, block order <= kGroupedMaxB,
@@ -236,8 +283,8 @@ pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count) {
     jw <<= 1;
     ++jlog;
   }
-  pivot_gj_body<double, false>(it.X + (int64_t)it.o * it.ldx + it.o, it.ldx, it.b, it.b, jlog, it.Pinv, it.b,
-                               it.status, it.k);
+  pivot_gj_body<double, double, false>(it.X + (int64_t)it.o * it.ldx + it.o, it.ldx, it.b, it.b, jlog, it.Pinv,
+                                       it.b, it.status, it.k);
 }
 
 // ------------------------------------------------------------------------
@@ -634,9 +681,9 @@ size_t pivot_smem_bytes(int b, int R, int elem) {
   return t * elem + i * sizeof(int) + 16;
 }
 
-template <typename T, bool kCluster>
+template <typename T, typename TIO, bool kCluster>
 cudaError_t configure(size_t smem) {
-  auto k = pivot_gj_kernel<T, kCluster>;
+  auto k = pivot_gj_kernel<T, TIO, kCluster>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (kCluster) {
@@ -705,16 +752,11 @@ cudaError_t launch_pivot_blocked(const T* P, int64_t ldp, int b, T* Pinv, int64_
   return e;
 }
 
-template <typename T>
-cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
-                                 int32_t* status, int block_index, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    if (b > 64) {
-      bool done = false;
-      cudaError_t e = launch_pivot_blocked<T>(P, ldp, b, Pinv, ldo, status, block_index, s, &done);
-      if (e != cudaSuccess || done) return e;
-    }
-  }
+// Row-distributed Gauss-Jordan (pivot_gj_kernel) in arithmetic T on blocks of
+// type TIO, optionally gated.
+template <typename T, typename TIO>
+cudaError_t launch_gj(const TIO* P, int64_t ldp, int b, TIO* Pinv, int64_t ldo, int32_t* status, int block_index,
+                      const int32_t* gate, cudaStream_t s) {
   PivotPlan plan;
   if (!plan_pivot(b, (int)sizeof(T), &plan)) return cudaErrorInvalidValue;
   int jw = 1, jlog = 0;
@@ -729,7 +771,7 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   if (plan.ctas > 1) {
-    cudaError_t e = configure<T, true>(plan.smem);
+    cudaError_t e = configure<T, TIO, true>(plan.smem);
     if (e != cudaSuccess) return e;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = plan.ctas;
@@ -737,13 +779,35 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, pivot_gj_kernel<T, true>, P, ldp, b, plan.rows, jlog, Pinv, ldo,
-                              status, block_index);
+    return cudaLaunchKernelEx(&cfg, pivot_gj_kernel<T, TIO, true>, P, ldp, b, plan.rows, jlog, Pinv, ldo, status,
+                              block_index, gate);
   }
-  cudaError_t e = configure<T, false>(plan.smem);
+  cudaError_t e = configure<T, TIO, false>(plan.smem);
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, pivot_gj_kernel<T, false>, P, ldp, b, plan.rows, jlog, Pinv, ldo,
-                            status, block_index);
+  return cudaLaunchKernelEx(&cfg, pivot_gj_kernel<T, TIO, false>, P, ldp, b, plan.rows, jlog, Pinv, ldo, status,
+                            block_index, gate);
+}
+
+template <typename T>
+cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
+                                 int32_t* status, int block_index, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (b > 64) {
+      bool done = false;
+      cudaError_t e = launch_pivot_blocked<T>(P, ldp, b, Pinv, ldo, status, block_index, s, &done);
+      if (e != cudaSuccess || done) return e;
+    }
+  }
+  return launch_gj<T, T>(P, ldp, b, Pinv, ldo, status, block_index, nullptr, s);
+}
+
+cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
+                                     int block_index, float cond_limit, int32_t* gate, int32_t* count,
+                                     cudaStream_t s) {
+  pivot_cond_kernel<<<1, kPivotThreads, 0, s>>>(P, ldp, Pinv, ldo, b, cond_limit, gate, count, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
 }
 
 cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s) {

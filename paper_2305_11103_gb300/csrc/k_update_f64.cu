@@ -145,57 +145,62 @@ enum WriteMask { kAll = 0, kRest = 1, kNextA = 2, kNextB = 3 };
 
 __device__ __forceinline__ bool in_range(int v, int lo, int len) { return v >= lo && v < lo + len; }
 
+// One TILE x TILE output tile (TILE = 64 or 32) by 256 threads, each holding
+// (TILE / 16) x (TILE / 16) outputs.
+template <int TILE = kTile>
 __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, int n, int o, int b,
                                            const double* __restrict__ U, int i0, int j0, int o1 = 0, int b1 = 0,
                                            int mask = kAll) {
-  __shared__ __align__(16) double Us[kTileK][kTile];
-  __shared__ __align__(16) double Vs[kTileK][kTile];
+  constexpr int PT = TILE / 16;              // outputs per thread along each side
+  constexpr int LOADS = TILE * kTileK / 256;  // tile elements per thread per k chunk
+  __shared__ __align__(16) double Us[kTileK][TILE];
+  __shared__ __align__(16) double Vs[kTileK][TILE];
   const int tid = threadIdx.x;
   const int tx = tid & 15;
   const int ty = tid >> 4;
-  double acc[4][4];
+  double acc[PT][PT];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < PT; ++a)
 #pragma unroll
-    for (int d = 0; d < 4; ++d) acc[a][d] = 0.0;
+    for (int d = 0; d < PT; ++d) acc[a][d] = 0.0;
 
   for (int kc = 0; kc < b; kc += kTileK) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < LOADS; ++h) {
       const int e = tid + h * 256;
-      // U tile: 64 rows x 8 k
+      // U tile: TILE rows x 8 k
       const int ui = e >> 3, uk = e & 7;
       const int gi = i0 + ui;
       Us[uk][ui] = (gi < n && kc + uk < b) ? U[(int64_t)gi * b + kc + uk] : 0.0;
-      // V tile: 8 k x 64 columns of row panel k
-      const int vk = e >> 6, vj = e & 63;
+      // V tile: 8 k x TILE columns of row panel k
+      const int vk = e / TILE, vj = e % TILE;
       const int gj = j0 + vj;
       Vs[vk][vj] = (gj < n && kc + vk < b) ? X[(int64_t)(o + kc + vk) * ldx + gj] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kTileK; ++kk) {
-      double u[4], v[4];
+      double u[PT], v[PT];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) u[a] = Us[kk][ty * 4 + a];
+      for (int a = 0; a < PT; ++a) u[a] = Us[kk][ty * PT + a];
 #pragma unroll
-      for (int d = 0; d < 4; ++d) v[d] = Vs[kk][tx * 4 + d];
+      for (int d = 0; d < PT; ++d) v[d] = Vs[kk][tx * PT + d];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < PT; ++a)
 #pragma unroll
-        for (int d = 0; d < 4; ++d) acc[a][d] = fma(u[a], v[d], acc[a][d]);
+        for (int d = 0; d < PT; ++d) acc[a][d] = fma(u[a], v[d], acc[a][d]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = i0 + ty * 4 + a;
+  for (int a = 0; a < PT; ++a) {
+    const int i = i0 + ty * PT + a;
     if (i >= n || (i >= o && i < o + b)) continue;
     const bool ri = in_range(i, o1, b1);
     double* row = X + (int64_t)i * ldx;
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int j = j0 + tx * 4 + d;
+    for (int d = 0; d < PT; ++d) {
+      const int j = j0 + tx * PT + d;
       if (j >= n) continue;
       const bool cj = in_range(j, o1, b1);
       const bool write = mask == kAll || (mask == kRest && !ri && !cj) || (mask == kNextA && (ri || cj)) ||
@@ -256,19 +261,21 @@ schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b
   schur_tile(X, ldx, n, o, b, U, i0, j0);
 }
 
-// Grouped Schur update: tile t of the batch belongs to item m.
+// Grouped Schur update: tile t of the batch belongs to item m (TILE x TILE
+// tiles, TILE = 64 or 32).
+template <int TILE>
 __global__ void __launch_bounds__(256)
 schur_update_grouped_kernel(const GroupStep* __restrict__ items, int count, const int32_t* __restrict__ tile_start) {
   const int t = blockIdx.x;
   const int m = find_item(tile_start, count, t);
   const GroupStep it = items[m];
-  const int tiles_row = (it.n + kTile - 1) / kTile;
+  const int tiles_row = (it.n + TILE - 1) / TILE;
   const int local = t - tile_start[m];
-  const int i0 = (local / tiles_row) * kTile;
-  const int j0 = (local % tiles_row) * kTile;
-  if (i0 >= it.o && i0 + kTile <= it.o + it.b) return;
+  const int i0 = (local / tiles_row) * TILE;
+  const int j0 = (local % tiles_row) * TILE;
+  if (i0 >= it.o && i0 + TILE <= it.o + it.b) return;
   if (failed(it.status)) return;
-  schur_tile(it.X, it.ldx, it.n, it.o, it.b, it.U, i0, j0);
+  schur_tile<TILE>(it.X, it.ldx, it.n, it.o, it.b, it.U, i0, j0);
 }
 
 // --------------------------------------------------------- residual -------
@@ -397,9 +404,14 @@ cudaError_t launch_row_panel_grouped(const GroupStep* items, int count, const in
 }
 
 cudaError_t launch_schur_update_grouped(const GroupStep* items, int count, const int32_t* tile_start,
-                                        int total_tiles, cudaStream_t s) {
+                                        int total_tiles, int tile, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return cudaSuccess;
-  schur_update_grouped_kernel<<<total_tiles, 256, 0, s>>>(items, count, tile_start);
+  if (tile == 32)
+    schur_update_grouped_kernel<32><<<total_tiles, 256, 0, s>>>(items, count, tile_start);
+  else if (tile == 64)
+    schur_update_grouped_kernel<64><<<total_tiles, 256, 0, s>>>(items, count, tile_start);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

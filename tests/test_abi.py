@@ -81,3 +81,29 @@ def test_mixed_modes_reject_orders_above_16384(lib):
     assert st == blockinv.ERR_INVALID
     st, _ = blockinv.blockinv_residual_tc(64, 0x1000, 64, 0x2000, 64, slices=10)
     assert st == blockinv.ERR_INVALID
+
+
+def test_batch_tuning_table_roundtrip(lib, tmp_path):
+    """The tuning table is host state: set, read, save, clear, load."""
+    assert blockinv.blockinv_batch_tuning_clear() == blockinv.OK
+    assert blockinv.blockinv_batch_tuning(5) == (blockinv.OK, 0, 64)
+    assert blockinv.blockinv_batch_tuning_set(5, 4, 32) == blockinv.OK
+    assert blockinv.blockinv_batch_tuning_set(9, 8, 64) == blockinv.OK
+    assert blockinv.blockinv_batch_tuning(5) == (blockinv.OK, 4, 32)
+    path = tmp_path / "tuning.txt"
+    assert blockinv.blockinv_batch_tuning_save(path) == blockinv.OK
+    assert path.read_text().splitlines() == ["blockinv-batch-tuning 1", "5 4 32", "9 8 64"]
+    assert blockinv.blockinv_batch_tuning_clear() == blockinv.OK
+    assert blockinv.blockinv_batch_tuning(9) == (blockinv.OK, 0, 64)
+    assert blockinv.blockinv_batch_tuning_load(path) == blockinv.OK
+    assert blockinv.blockinv_batch_tuning(9) == (blockinv.OK, 8, 64)
+    # malformed files and arguments are rejected and leave the table as it was
+    bad = tmp_path / "bad.txt"
+    bad.write_text("blockinv-batch-tuning 1\n5 4 48\n")
+    assert blockinv.blockinv_batch_tuning_load(bad) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_batch_tuning(5) == (blockinv.OK, 4, 32)
+    assert blockinv.blockinv_batch_tuning_set(2, 4, 64) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_batch_tuning_set(5, 4, 16) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_batch_tuning(17)[0] == blockinv.ERR_INVALID
+    assert blockinv.blockinv_batch_tuning_load(tmp_path / "missing.txt") == blockinv.ERR_INVALID
+    assert blockinv.blockinv_batch_tuning_clear() == blockinv.OK

@@ -184,3 +184,68 @@ def test_batched_argument_errors(bi):
     assert bi.blockinv_invert_batched([8], [[4, 3]], [t.data_ptr()], [8]) == bi.ERR_INVALID
     assert bi.blockinv_invert_batched([8], None, [t.data_ptr()], [7]) == bi.ERR_INVALID
     assert bi.blockinv_invert_batched([8], None, [t.data_ptr()], [8], mode="tf32") == bi.ERR_INVALID
+
+
+def _check_batch(mats, ts, parts=None, sample=None):
+    idx = range(len(mats)) if sample is None else sample
+    for i in idx:
+        A, X = mats[i], ts[i].cpu().numpy()
+        n = A.shape[0]
+        assert np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e-12
+        Xo = oracle.block_inverse(A, parts[i] if parts else quarter(n))
+        kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64
+
+
+def _size_class(n):
+    return int(np.floor(np.log2(n)))
+
+
+def test_table_partition_and_32_tiles_vs_oracle(bi):
+    """Table entries set by hand: p near-equal blocks and 32 x 32 Schur tiles."""
+    mats = inputs.uneven_batch(80, 8, 300, 65)
+    ns = [A.shape[0] for A in mats]
+    assert bi.blockinv_batch_tuning_clear() == bi.OK
+    for c in range(3, 9):
+        assert bi.blockinv_batch_tuning_set(c, 2 if c < 5 else 5, 32 if c % 2 else 64) == bi.OK
+    try:
+        ts, ptrs, _ = device_batch(mats)
+        st = torch.full((80,), 7, dtype=torch.int32, device="cuda")
+        assert bi.blockinv_invert_batched(ns, None, ptrs, ns, bi.F64, None, st.data_ptr()) == bi.OK
+        assert torch.all(st == 0)
+        parts = []
+        for n in ns:
+            p = 2 if _size_class(n) < 5 else 5
+            q, r = divmod(n, p)
+            parts.append([q + (1 if i >= p - r else 0) for i in range(p)])
+        _check_batch(mats, ts, parts)
+    finally:
+        bi.blockinv_batch_tuning_clear()
+
+
+def test_autotuner_choices_are_valid_and_exact(bi):
+    mats = inputs.uneven_batch(300, 8, 520, 64)
+    ns = [A.shape[0] for A in mats]
+    assert bi.blockinv_batch_tuning_clear() == bi.OK
+    try:
+        assert bi.blockinv_batch_tune(ns, 2) == bi.OK
+        for c in sorted({_size_class(n) for n in ns}):
+            st, p, tile = bi.blockinv_batch_tuning(c)
+            members = [n for n in ns if _size_class(n) == c]
+            assert st == bi.OK and tile in (32, 64) and 1 <= p <= min(members)
+            assert -(-max(members) // p) <= 128 and min(members) // p >= 4 or p == 1
+        ts, ptrs, _ = device_batch(mats)
+        st = torch.full((300,), 7, dtype=torch.int32, device="cuda")
+        plan = bi.BatchPlan(ns, None, ptrs, ns)
+        assert plan.run(None, st.data_ptr()) == bi.OK
+        torch.cuda.synchronize()
+        plan.close()
+        assert torch.all(st == 0)
+        parts = []
+        for n in ns:
+            p = bi.blockinv_batch_tuning(_size_class(n))[1]
+            q, r = divmod(n, p)
+            parts.append([q + (1 if i >= p - r else 0) for i in range(p)])
+        _check_batch(mats, ts, parts, sample=inputs.rng(67).choice(300, size=40, replace=False))
+    finally:
+        bi.blockinv_batch_tuning_clear()

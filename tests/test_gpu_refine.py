@@ -180,3 +180,55 @@ def test_full_size_16384_mixed(bi, mode, sigma, seed):
     kappa = nA * nX
     for t, j in enumerate(cols):
         assert np.linalg.norm(X[:, j] - S[:, t]) / np.linalg.norm(S[:, t]) <= 4 * n * kappa * U64
+
+
+def _ill_block(n, kappa, seed):
+    """Q diag(logspace(0, -log10 kappa)) Q^T, rounded to FP32 values (so the
+    mixed path's FP32 copy is exact)."""
+    g = inputs.rng(seed)
+    Q, _ = np.linalg.qr(g.standard_normal((n, n)))
+    d = np.logspace(0, -np.log10(kappa), n)
+    return ((Q * d) @ Q.T).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_ill_conditioned_pivot_block_inverted_in_fp64(bi, mode):
+    """A single 256-block with kappa ~ 1e6: the FP32 Gauss-Jordan leaves an error
+    near kappa * 2^-24; FP64 arithmetic (chosen by the condition estimate, or
+    forced) leaves only the FP32 rounding of the result."""
+    n = 256
+    A = _ill_block(n, 1e6, 91)
+    Ainv = np.linalg.inv(A)
+    got = {}
+    for pf in (-1, 0, 1):
+        d = torch.from_numpy(A).cuda()
+        st, info = bi.blockinv_invert_ex(n, [n], d.data_ptr(), n, mode, None, max_refine=0, pivot_f64=pf)
+        assert st == bi.OK
+        got[pf] = (np.linalg.norm(d.cpu().numpy() - Ainv) / np.linalg.norm(Ainv), info.fp64_pivots)
+    assert [got[pf][1] for pf in (-1, 0, 1)] == [0, 1, 1], got
+    assert got[0][0] <= 1e-6 and got[1][0] <= 1e-6, got
+    assert got[-1][0] >= 100 * got[0][0], got
+
+
+def test_well_conditioned_pivots_stay_fp32(bi):
+    n = 1024
+    A = inputs.gaussian_shifted(n, 5, sigma=1.5)
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(n, [256] * 4, d.data_ptr(), n, "tf32", None)
+    assert st == bi.OK and info.fp64_pivots == 0 and 0 <= info.rho <= 1e-12
+
+
+def test_ill_conditioned_first_block_refines(bi):
+    """An ill-conditioned leading 256-block inside a 768 matrix: the block is
+    flagged and inverted in FP64; the solve still meets the gate."""
+    n, b = 768, 256
+    A = inputs.gaussian_shifted(n, 93, sigma=1.5)
+    A[:b, :b] = _ill_block(b, 1e5 * 3, 94) * 4.0
+    A[:b, b:] *= 1e-2
+    A[b:, :b] *= 1e-2
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(n, [b] * 3, d.data_ptr(), n, "tf32", None)
+    assert st == bi.OK and info.fp64_pivots >= 1
+    X = d.cpu().numpy()
+    r = np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X))
+    assert r <= 1e-12, (r, info.as_dict())
