@@ -27,6 +27,7 @@
 // The pivot row is scaled by multiplying with the correctly rounded
 // reciprocal of the pivot (within an ulp of dividing; exact for unit pivots).
 #include <climits>
+#include <mutex>
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -231,13 +232,16 @@ pivot_gj_kernel(const TIO* __restrict__ P, int64_t ldp, int b, int R, int jlog, 
 // Condition estimate of an FP32 pivot block after its FP32 inverse:
 // kappa = ||P||_inf ||P^-1||_inf. *gate = 1 when kappa > limit (or is not
 // finite), and then *count is incremented; limit < 0 sets the gate always.
-__global__ void __launch_bounds__(kPivotThreads)
+// One CTA of 1024 threads: a warp per row at a time, all of a lane's loads of
+// both blocks in flight together (the kernel is latency-bound otherwise).
+constexpr int kCondThreads = 1024;
+__global__ void __launch_bounds__(kCondThreads)
 pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restrict__ Pinv, int64_t ldo, int b,
                   float limit, int32_t* gate, int32_t* count, const int32_t* status) {
-  __shared__ float red[2][kPivotThreads / 32];
+  __shared__ float red[2][kCondThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float mp = 0.f, mi = 0.f;
-  for (int r = warp; r < b; r += kPivotThreads / 32) {
+  for (int r = warp; r < b; r += kCondThreads / 32) {
     float sp = 0.f, si = 0.f;
     for (int j = lane; j < b; j += 32) {
       sp += fabsf(P[(int64_t)r * ldp + j]);
@@ -258,7 +262,7 @@ pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restr
   __syncthreads();
   if (tid == 0) {
     float a = 0.f, c = 0.f;
-    for (int w = 0; w < kPivotThreads / 32; ++w) {
+    for (int w = 0; w < kCondThreads / 32; ++w) {
       a = fmaxf(a, red[0][w]);
       c = fmaxf(c, red[1][w]);
     }
@@ -681,14 +685,25 @@ size_t pivot_smem_bytes(int b, int R, int elem) {
   return t * elem + i * sizeof(int) + 16;
 }
 
+// Kernel attributes are per device; the largest shared-memory size set so far
+// for each instantiation and device is remembered, so the attribute calls run
+// only when a launch needs more.
 template <typename T, typename TIO, bool kCluster>
 cudaError_t configure(size_t smem) {
+  static std::mutex mu;
+  static size_t done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev >= 0 && dev < 64 && done[dev] >= smem) return cudaSuccess;
   auto k = pivot_gj_kernel<T, TIO, kCluster>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (kCluster) {
     e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = smem;
   return e;
 }
 
@@ -717,6 +732,22 @@ bool plan_pivot(int b, int elem_bytes, PivotPlan* plan) {
   return true;
 }
 
+// The dynamic shared-memory attribute of kernel K, set only when a launch on
+// this device needs more than was set before (one record per kernel).
+template <auto K>
+cudaError_t set_smem_once(size_t smem) {
+  static std::mutex mu;
+  static size_t done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev >= 0 && dev < 64 && done[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = smem;
+  return e;
+}
+
 template <typename T>
 cudaError_t launch_pivot_blocked(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo, int32_t* status,
                                  int block_index, cudaStream_t s, bool* done) {
@@ -733,7 +764,7 @@ cudaError_t launch_pivot_blocked(const T* P, int64_t ldp, int b, T* Pinv, int64_
   cudaError_t e;
   if (ctas > 1) {
     auto k = pivot_blocked_kernel<T, true>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once<pivot_blocked_kernel<T, true>>(smem);
     if (e != cudaSuccess) return e;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ctas;
@@ -744,7 +775,7 @@ cudaError_t launch_pivot_blocked(const T* P, int64_t ldp, int b, T* Pinv, int64_
     e = cudaLaunchKernelEx(&cfg, k, P, ldp, b, ncl, Pinv, ldo, status, block_index);
   } else {
     auto k = pivot_blocked_kernel<T, false>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_smem_once<pivot_blocked_kernel<T, false>>(smem);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernelEx(&cfg, k, P, ldp, b, ncl, Pinv, ldo, status, block_index);
   }
@@ -804,7 +835,7 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
 cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
                                      int block_index, float cond_limit, int32_t* gate, int32_t* count,
                                      cudaStream_t s) {
-  pivot_cond_kernel<<<1, kPivotThreads, 0, s>>>(P, ldp, Pinv, ldo, b, cond_limit, gate, count, status);
+  pivot_cond_kernel<<<1, kCondThreads, 0, s>>>(P, ldp, Pinv, ldo, b, cond_limit, gate, count, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);

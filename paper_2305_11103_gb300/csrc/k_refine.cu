@@ -565,11 +565,13 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       km.pa[1] = 0; km.pb[1] = 1;
       km.pa[2] = 1; km.pb[2] = 0;
       // The tensor-core FP32 accumulator drops bits on every k-step (its
-      // error grows linearly with K, measured), so K is cut into chunks of
-      // kUpdateChunkK, each added into the FP64 X on its own.
+      // error grows linearly with K, measured), so the hi*hi product's K is
+      // cut into chunks of kUpdateChunkK, each added into the FP64 X on its
+      // own; the hi*lo and lo*hi products (2^-11 smaller) form one more chunk.
       km.chunk_kb = kUpdateChunkK / 32;
+      km.chunk_end = km.kb_per_pair;
       EpiAddF64 epi{X, ldx, n, ctl, status};
-      const double chunks = std::ceil(3.0 * Kp / kUpdateChunkK);
+      const double chunks = std::ceil((double)Kp / kUpdateChunkK) + 1.0;
       TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd * chunks + 16.0 * nd * Kp, s);
       e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true>(tXo, tEo, n, n, km, epi, status, s);
     }

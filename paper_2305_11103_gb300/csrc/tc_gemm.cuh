@@ -51,6 +51,8 @@ struct KMap {
   int slice_cols;         // operand columns between consecutive slices
   int chunk_kb;           // k-blocks per accumulator hand-off (0 = the whole K); > 0 only for
                           // epilogues that add into their output (each chunk arrives separately)
+  int chunk_end;          // chunks of chunk_kb cover k-blocks [0, chunk_end) (0 = all of K);
+                          // the k-blocks after it form one more chunk
   int8_t pa[kMaxPairs];   // A slice of pair i
   int8_t pb[kMaxPairs];   // B slice of pair i
 };
@@ -86,6 +88,20 @@ __device__ __forceinline__ void flag_timeout(int32_t* status) {
   if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
 }
 
+// Work item t -> (row unit um, column tile tn), row units taken kGroupUnits
+// at a time: consecutive items walk down a group's rows before the next
+// column, so the items in flight together share A and B panels through L2.
+// A row unit is one 128-row tile, or (kMC) a pair of them.
+__device__ __forceinline__ void item_coords(int t, int units_m, int tiles_n, int group, int& um, int& tn) {
+  const int per_group = group * tiles_n;
+  const int g = t / per_group;
+  const int first = g * group;
+  const int gsize = min(units_m - first, group);
+  const int r = t - g * per_group;
+  um = first + r % gsize;
+  tn = r / gsize;
+}
+
 template <Kind K, class Epi, bool kMC = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int tiles_m,
@@ -99,14 +115,18 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int lane = threadIdx.x & 31;
   // Work items: single tiles, or (kMC) pairs of vertically adjacent tiles per cluster.
   const int tiles_mp = kMC ? (tiles_m + 1) / 2 : tiles_m;
+  constexpr int kGroupUnits = kMC ? 8 : 16;  // 16 row tiles per group either way
   const int ntiles = tiles_mp * tiles_n;
   const int rank = kMC ? (int)cluster_ctarank() : 0;
   const int first = kMC ? (int)cluster_id_x() : (int)blockIdx.x;
   const int stride = kMC ? (int)cluster_count_x() : (int)gridDim.x;
-  // Accumulator hand-offs: each of this CTA's tiles in nch K-chunks of kbc
-  // k-blocks, every chunk accumulated from zero and passed to the epilogue.
+  // Accumulator hand-offs: each of this CTA's tiles in nch K-chunks (kbc
+  // k-blocks each up to kend, then the rest as one), every chunk accumulated
+  // from zero and passed to the epilogue.
   const int kbc = (km.chunk_kb > 0 && km.chunk_kb < km.kblocks) ? km.chunk_kb : km.kblocks;
-  const int nch = (km.kblocks + kbc - 1) / kbc;
+  const int kend = (km.chunk_end > 0 && km.chunk_end < km.kblocks) ? km.chunk_end : km.kblocks;
+  const int nch_a = (kend + kbc - 1) / kbc;
+  const int nch = nch_a + (kend < km.kblocks ? 1 : 0);
   const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
   const int nitems = my_tiles * nch;
   if (epi.skip()) return;  // an earlier kernel of this computation failed (uniform over the grid)
@@ -140,8 +160,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint32_t it = 0;
     bool ok = true;
     for (int t = first; t < ntiles && ok; t += stride) {
-      const int m0 = (kMC ? 2 * (t / tiles_n) + rank : t / tiles_n) * kBM;
-      const int n0 = (t % tiles_n) * kBN;
+      int um, tn;
+      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
+      const int m0 = (kMC ? 2 * um + rank : um) * kBM;
+      const int n0 = tn * kBN;
       for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
@@ -188,7 +210,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       fence_after_sync();
       const uint32_t d = tmem + a * kBN;
-      const int kb0 = c * kbc, kb1 = min(km.kblocks, kb0 + kbc);
+      const int kb0 = c < nch_a ? c * kbc : kend;
+      const int kb1 = c < nch_a ? min(kend, kb0 + kbc) : km.kblocks;
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
@@ -226,8 +249,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         break;
       }
       fence_after_sync();
-      const int m0 = (kMC ? 2 * (t / tiles_n) + rank : t / tiles_n) * kBM;
-      const int n0 = (t % tiles_n) * kBN;
+      int um, tn;
+      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
+      const int m0 = (kMC ? 2 * um + rank : um) * kBM;
+      const int n0 = tn * kBN;
       const int row0 = m0 + q * 32;
 #pragma unroll 1
       for (int c = half * (kBN / 64); c < (half + 1) * (kBN / 64); ++c) {
