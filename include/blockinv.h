@@ -249,6 +249,32 @@ int blockinv_ctx_stats(blockinv_ctx* ctx, int64_t* queued, int64_t* running, siz
 /* Finish running requests, cancel queued ones, release everything. */
 int blockinv_ctx_destroy(blockinv_ctx* ctx);
 
+/* ------------------------------------------- step ranges and checkpoints ---
+ * The paper's stop-and-resume by step (Sec. 5): the FP64 in-place
+ * elimination after k steps leaves the whole state in A, so it can stop
+ * between steps and continue later, in this or another process.
+ *
+ * blockinv_invert_steps applies elimination steps k0 .. k1 - 1
+ * (0 <= k0 <= k1 <= number of blocks) of the FP64 path to A in place
+ * (arguments as blockinv_invert; block_sizes NULL = the default partition).
+ * Steps 0 .. p - 1 in one call or in consecutive ranges give the same bits as
+ * blockinv_invert(..., BLOCKINV_F64, ...). Blocking; status as
+ * blockinv_invert (SINGULAR / NONFINITE name the global block index).
+ *
+ * blockinv_checkpoint_write saves A (device, n x n, lda) with k_done and the
+ * partition to `path`: "BLKINVC1", int64 n, int32 p, int32 k_done,
+ * int32 sizes[p], uint64 FNV-1a hash of the matrix bytes, n * n doubles row by
+ * row (little-endian). blockinv_checkpoint_read checks the file against n and
+ * the partition and the hash on the host, then copies the matrix into A and
+ * sets *k_done; any mismatch or damage returns BLOCKINV_ERR_INVALID with A
+ * untouched. Both blocking (they synchronise `stream`). */
+int blockinv_invert_steps(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int32_t k0,
+                          int32_t k1, void* stream);
+int blockinv_checkpoint_write(const char* path, int64_t n, int32_t p, const int32_t* block_sizes, const double* A,
+                              int64_t lda, int32_t k_done, void* stream);
+int blockinv_checkpoint_read(const char* path, int64_t n, int32_t p, const int32_t* block_sizes, double* A,
+                             int64_t lda, int32_t* k_done, void* stream);
+
 /* Options and per-call report for blockinv_invert_ex. */
 typedef struct {
   double tol;          /* refinement target for rho (mixed modes); <= 0 means 1e-12     */

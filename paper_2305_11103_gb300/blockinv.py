@@ -40,6 +40,9 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "blockinv_batch_plan_run": (_int, [_vp, _vp, _vp]),
     "blockinv_batch_plan_destroy": (_int, [_vp]),
+    "blockinv_invert_steps": (_int, [_i64, _i32, _i32p, _vp, _i64, _i32, _i32, _vp]),
+    "blockinv_checkpoint_write": (_int, [ctypes.c_char_p, _i64, _i32, _i32p, _vp, _i64, _i32, _vp]),
+    "blockinv_checkpoint_read": (_int, [ctypes.c_char_p, _i64, _i32, _i32p, _vp, _i64, _i32p, _vp]),
     "blockinv_batch_tune": (_int, [_i32, _i32p, _i32, _vp]),
     "blockinv_batch_tuning": (_int, [_i32, _i32p, _i32p]),
     "blockinv_batch_tuning_set": (_int, [_i32, _i32, _i32]),
@@ -175,6 +178,25 @@ def blockinv_invert_batched(ns, partitions, A_ptrs, ldas, mode=F64, stream=None,
     count, n_arr, p_arr, s_arr, a_arr, l_arr = _batch_args(ns, partitions, A_ptrs, ldas)
     return lib().blockinv_invert_batched(count, n_arr, p_arr, s_arr, a_arr, l_arr, _mode(mode),
                                          _stream_ptr(stream), status_ptr)
+
+
+def blockinv_invert_steps(n, block_sizes, A_ptr, lda, k0, k1, stream=None):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_invert_steps(n, p, arr, A_ptr, lda, k0, k1, _stream_ptr(stream))
+
+
+def blockinv_checkpoint_write(path, n, block_sizes, A_ptr, lda, k_done, stream=None):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_checkpoint_write(str(path).encode(), n, p, arr, A_ptr, lda, k_done, _stream_ptr(stream))
+
+
+def blockinv_checkpoint_read(path, n, block_sizes, A_ptr, lda, stream=None):
+    """(status, k_done)."""
+    p, arr, _ = _sizes(block_sizes)
+    k = ctypes.c_int32(-1)
+    st = lib().blockinv_checkpoint_read(str(path).encode(), n, p, arr, A_ptr, lda, ctypes.byref(k),
+                                        _stream_ptr(stream))
+    return st, k.value
 
 
 def blockinv_batch_tune(ns, reps=3, stream=None):

@@ -153,10 +153,17 @@ struct EventPair {
 // panels) and the rest; as soon as the first part is done, the next pivot
 // inverse and row panel run on a high-priority side stream while the rest of
 // step k's update runs on s. The U panel is double-buffered.
-int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStream_t s) {
+//
+// Steps k0 .. k1 - 1 only (0 .. p - 1 for a whole inversion): the state
+// between steps is A alone, so a range picks up where the previous one
+// stopped, and splitting the steps over several calls gives the same bits.
+int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStream_t s, int k0 = 0,
+                int k1 = -1) {
   const int n = pl.n;
-  const int p = (int)pl.sizes.size();
-  cudaStream_t t = (n >= 2048 && p >= 3) ? side_stream() : nullptr;
+  if (k1 < 0) k1 = (int)pl.sizes.size();
+  const int p = k1;
+  if (k0 >= k1) return BLOCKINV_OK;
+  cudaStream_t t = (n >= 2048 && k1 - k0 >= 3) ? side_stream() : nullptr;
   const bool ahead = t != nullptr;
   AsyncBuf pinv, ubuf;
   cudaError_t e = pinv.alloc(sizeof(double) * (size_t)pl.bmax * pl.bmax, s);
@@ -185,8 +192,8 @@ int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStr
     }
     return r;
   };
-  e = panels(0, s);
-  for (int k = 0; k < p && e == cudaSuccess; ++k) {
+  e = panels(k0, s);
+  for (int k = k0; k < p && e == cudaSuccess; ++k) {
     const int o = pl.offs[k], b = pl.sizes[k];
     const double bd = b, nd = n, rest = (double)(n - b);
     double* U = Ub[k & 1];
@@ -355,6 +362,25 @@ int finish(const int32_t* status_dev, cudaStream_t s) {
 }
 
 }  // namespace
+
+// ------------------------------------------ step ranges and checkpoints --
+int plan_for(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* pl) {
+  return make_plan(n, p, block_sizes, lda, pl);
+}
+
+int invert_steps(const Plan& pl, double* A, int64_t lda, int k0, int k1, cudaStream_t s) {
+  AsyncBuf sbuf;
+  cudaError_t e = sbuf.alloc(2 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  int32_t* status = static_cast<int32_t*>(sbuf.ptr);
+  const int st = enqueue_f64(pl, A, lda, status, s, k0, k1);
+  if (st != BLOCKINV_OK) {
+    cudaStreamSynchronize(s);
+    return record(st, -1);
+  }
+  return finish(status, s);
+}
 
 // ---------------------------------------------- hooks for the serving loop --
 struct ServeJob {

@@ -127,6 +127,10 @@ cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* statu
 
 // Hooks the serving loop (serve.cu) uses to run one request (api.cu).
 struct ServeJob;
+// Partition plan (the checks of blockinv_invert); FP64 elimination steps
+// k0 .. k1 - 1 in place, blocking, status as blockinv_invert.
+int plan_for(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* pl);
+int invert_steps(const Plan& pl, double* A, int64_t lda, int k0, int k1, cudaStream_t s);
 int serve_make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, int mode, Plan* pl);
 size_t serve_footprint(const Plan& pl, int mode);
 int serve_enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, cudaStream_t s, double tol,

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2305_11103_gb300 import blockinv
@@ -107,3 +108,40 @@ def test_batch_tuning_table_roundtrip(lib, tmp_path):
     assert blockinv.blockinv_batch_tuning(17)[0] == blockinv.ERR_INVALID
     assert blockinv.blockinv_batch_tuning_load(tmp_path / "missing.txt") == blockinv.ERR_INVALID
     assert blockinv.blockinv_batch_tuning_clear() == blockinv.OK
+
+
+def _checkpoint_bytes(n, sizes, k, data, magic=b"BLKINVC1", hash_delta=0):
+    import struct
+    payload = np.ascontiguousarray(data, dtype="<f8").tobytes()
+    h = 1469598103934665603
+    for byte in payload:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return (magic + struct.pack("<qii", n, len(sizes), k) + struct.pack(f"<{len(sizes)}i", *sizes)
+            + struct.pack("<Q", (h + hash_delta) & 0xFFFFFFFFFFFFFFFF) + payload)
+
+
+def test_checkpoint_read_rejects_bad_files_before_gpu_work(lib, tmp_path):
+    """Every check of a checkpoint file happens on the host: a file that does
+    not match is refused before any device copy (the target pointer is fake)."""
+    n, sizes = 6, [2, 4]
+    data = np.arange(36.0).reshape(6, 6)
+    cases = {
+        "magic": _checkpoint_bytes(n, sizes, 1, data, magic=b"BLKINVC0"),
+        "order": _checkpoint_bytes(7, sizes, 1, np.zeros((7, 7))),
+        "partition": _checkpoint_bytes(n, [3, 3], 1, data),
+        "hash": _checkpoint_bytes(n, sizes, 1, data, hash_delta=1),
+        "truncated": _checkpoint_bytes(n, sizes, 1, data)[:-8],
+        "trailing": _checkpoint_bytes(n, sizes, 1, data) + b"x",
+        "steps": _checkpoint_bytes(n, sizes, 3, data),
+    }
+    for name, blob in cases.items():
+        path = tmp_path / f"{name}.ck"
+        path.write_bytes(blob)
+        st, k = blockinv.blockinv_checkpoint_read(path, n, sizes, 0x1000, n)
+        assert st == blockinv.ERR_INVALID and k == -1, name
+    assert blockinv.blockinv_checkpoint_read(tmp_path / "none.ck", n, sizes, 0x1000, n)[0] == blockinv.ERR_INVALID
+
+
+def test_step_range_argument_errors(lib):
+    for k0, k1 in [(-1, 1), (2, 1), (0, 3)]:
+        assert blockinv.blockinv_invert_steps(6, [2, 4], 0x1000, 6, k0, k1) == blockinv.ERR_INVALID
