@@ -287,7 +287,12 @@ typedef struct {
   int32_t pivot_f64;   /* mixed modes: 0 (default) = invert again in FP64 arithmetic the */
                        /* pivot blocks whose estimate ||P||_inf ||P^-1||_inf from the    */
                        /* FP32 inverse exceeds 1e5; 1 = every pivot block; -1 = none     */
-  int32_t reserved[2];
+  int32_t pivot_order; /* 0 (default) = pivot blocks first to last (Eq. (a) at every    */
+                       /* step); 1 = last to first (Eq. (d): D and S_D = A - B D^-1 C)  */
+  int32_t singular_fallback; /* FP64 mode: 1 = when a pivot block is singular, retry  */
+                       /* from a saved copy of A with the other pivot order, then with  */
+                       /* the failing block merged into a neighbour (up to order 512),  */
+                       /* repeatedly; 0 (default) = return BLOCKINV_ERR_SINGULAR        */
 } blockinv_options;
 
 typedef struct {
@@ -299,7 +304,10 @@ typedef struct {
   int32_t used_fallback;  /* 1 if the FP64 path produced the result after a failed     */
                           /* refinement                                                */
   int32_t fp64_pivots;    /* mixed modes: pivot blocks inverted again in FP64          */
-  int32_t reserved[6];
+  int32_t partition_fallback; /* 0: the requested partition and order; 1: the other  */
+                          /* pivot order; 2: merged blocks (singular_fallback)          */
+  int32_t blocks_used;    /* pivot blocks of the partition that produced the result    */
+  int32_t reserved[4];
 } blockinv_info;
 
 /* blockinv_invert with options and a report (either pointer may be NULL). */

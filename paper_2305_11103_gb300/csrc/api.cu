@@ -231,6 +231,8 @@ struct Options {
   bool fallback = true;
   int split = 2;  // operand slices of the mixed Schur update (1 or 2)
   int pivot_f64 = 0;  // 0: FP64 re-inversion of ill-conditioned pivot blocks; 1: of all; -1: none
+  bool reverse = false;           // pivot blocks last to first (Eq. (d))
+  bool singular_fallback = false;  // FP64: retry singular pivots with another order / merged blocks
 };
 
 // Pivot blocks whose estimate ||P||_inf ||P^-1||_inf exceeds this are inverted
@@ -250,8 +252,38 @@ Options resolve(const blockinv_options* o) {
     r.fallback = o->fallback != 0;
     if (o->split == 1) r.split = 1;
     r.pivot_f64 = o->pivot_f64 > 0 ? 1 : (o->pivot_f64 < 0 ? -1 : 0);
+    r.reverse = o->pivot_order == 1;
+    r.singular_fallback = o->singular_fallback != 0;
   }
   return r;
+}
+
+// The same blocks taken last to first. Block Gauss-Jordan reaches A^-1 for
+// any order in which every block is the pivot once; last to first applies
+// Eq. (d) (D^-1 and S_D = A - B D^-1 C) at every step.
+Plan reversed(const Plan& pl) {
+  Plan r = pl;
+  std::reverse(r.sizes.begin(), r.sizes.end());
+  std::reverse(r.offs.begin(), r.offs.end());
+  return r;
+}
+
+// The spatial partition of a plan (blocks in index order).
+std::vector<int> spatial_sizes(const Plan& pl) {
+  std::vector<std::pair<int, int>> v;
+  for (size_t i = 0; i < pl.sizes.size(); ++i) v.emplace_back(pl.offs[i], pl.sizes[i]);
+  std::sort(v.begin(), v.end());
+  std::vector<int> out;
+  for (auto& q : v) out.push_back(q.second);
+  return out;
+}
+
+// Spatial block of pivot step k.
+int spatial_block(const Plan& pl, int k) {
+  int j = 0;
+  for (size_t i = 0; i < pl.sizes.size(); ++i)
+    if (pl.offs[i] < pl.offs[k]) ++j;
+  return j;
 }
 
 // Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
@@ -497,10 +529,18 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
     return record(st, -1);
   }
   const Options opt = resolve(options);
+  if (opt.reverse) pl = reversed(pl);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  AsyncBuf sbuf;
+  AsyncBuf sbuf, keep;
   cudaError_t e = sbuf.alloc(2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
+  const size_t row = sizeof(double) * (size_t)n;
+  const bool may_retry = mode == BLOCKINV_F64 && opt.singular_fallback;
+  if (e == cudaSuccess && may_retry) {  // the input, for retries after a singular pivot block
+    e = keep.alloc(row * (size_t)n, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(keep.ptr, row, A, sizeof(double) * lda, row, (size_t)n, cudaMemcpyDeviceToDevice, s);
+  }
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
   MixedState ms;
@@ -511,23 +551,72 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
     return record(st, -1);
   }
   st = finish(status, s);
-  const int64_t fb = g_last_block;
+  int64_t fb = g_last_block;
   read_mixed_info(ms, s, info);
   if (st == BLOCKINV_ERR_NOT_CONVERGED && opt.fallback && ms.a0.ptr) {
     // The low-precision elimination or its refinement failed: redo in FP64.
-    const size_t row = sizeof(double) * (size_t)n;
     e = cudaMemcpy2DAsync(A, sizeof(double) * lda, ms.a0.ptr, row, row, n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
     if (e != cudaSuccess) return record(cuda_status(e), -1);
     st = enqueue_f64(pl, A, lda, status, s);
     if (st == BLOCKINV_OK) st = finish(status, s);
+    fb = g_last_block;
     if (info) info->used_fallback = 1;
   }
+  // A singular pivot block: the other pivot order first, then the failing
+  // block merged into a neighbour, again and again (each run from the input).
+  Plan cur = pl;
+  int kind = 0;
+  auto rerun = [&](const Plan& q) -> int {
+    cudaError_t e2 = cudaMemcpy2DAsync(A, sizeof(double) * lda, keep.ptr, row, row, (size_t)n,
+                                       cudaMemcpyDeviceToDevice, s);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
+    if (e2 != cudaSuccess) return cuda_status(e2);
+    int r = enqueue_f64(q, A, lda, status, s);
+    if (r == BLOCKINV_OK) r = finish(status, s);
+    return r;
+  };
+  if (st == BLOCKINV_ERR_SINGULAR && may_retry) {
+    int failed_at = spatial_block(cur, (int)fb);
+    const Plan alt = reversed(cur);
+    const int r = rerun(alt);
+    if (r == BLOCKINV_OK) {
+      cur = alt;
+      kind = 1;
+      st = BLOCKINV_OK;
+    } else if (r != BLOCKINV_ERR_SINGULAR) {
+      st = r;
+    }
+    std::vector<int> part = spatial_sizes(pl);
+    while (st == BLOCKINV_ERR_SINGULAR && part.size() > 1) {
+      const int j = failed_at;
+      const int a = (j + 1 < (int)part.size()) ? j : j - 1;  // merge blocks a and a + 1
+      if (a < 0 || part[a] + part[a + 1] > BLOCKINV_MAX_BLOCK) break;
+      part[a] += part[a + 1];
+      part.erase(part.begin() + a + 1);
+      Plan q;
+      if (make_plan(n, (int32_t)part.size(), part.data(), lda, &q) != BLOCKINV_OK) break;
+      const int r2 = rerun(q);
+      cur = q;
+      kind = 2;
+      if (r2 == BLOCKINV_ERR_SINGULAR) {
+        failed_at = spatial_block(cur, (int)g_last_block);
+        continue;
+      }
+      st = r2;
+    }
+    if (st == BLOCKINV_ERR_SINGULAR) fb = g_last_block;
+  }
+  const int64_t failing = (st == BLOCKINV_ERR_SINGULAR || st == BLOCKINV_ERR_NONFINITE) && fb >= 0
+                              ? spatial_block(cur, (int)fb)
+                              : -1;
   if (info) {
     info->status = st;
-    info->failing_block = (st == BLOCKINV_OK) ? -1 : (st == BLOCKINV_ERR_NOT_CONVERGED ? -1 : fb);
+    info->failing_block = failing;
+    info->partition_fallback = kind;
+    info->blocks_used = (int32_t)cur.sizes.size();
   }
-  return record(st, info ? info->failing_block : g_last_block);
+  return record(st, failing);
 }
 
 int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda, int mode,

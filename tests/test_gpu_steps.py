@@ -69,3 +69,63 @@ def test_singular_block_reported_by_its_step(bi):
     assert bi.blockinv_invert_steps(n, sizes, d.data_ptr(), n, 0, 1) == bi.OK
     assert bi.blockinv_invert_steps(n, sizes, d.data_ptr(), n, 1, 3) == bi.ERR_SINGULAR
     assert bi.blockinv_last_error_detail() == (bi.ERR_SINGULAR, 1)
+
+
+# ---------------------------------------------- pivot order and fallbacks ---
+def rho(A, X):
+    return np.linalg.norm(A @ X - np.eye(A.shape[0])) / (np.linalg.norm(A) * np.linalg.norm(X))
+
+
+def ex(bi, A, sizes, **kw):
+    n = A.shape[0]
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, bi.F64, None, **kw)
+    return st, info, d.cpu().numpy()
+
+
+def test_reverse_pivot_order_is_eq_d(bi):
+    """Blocks last to first (Eq. (d) at every step) reach the same inverse."""
+    A = inputs.gaussian_shifted(700, 72, sigma=1.5)
+    sizes = [256, 256, 188]
+    st, info, X = ex(bi, A, sizes, pivot_order=1)
+    assert st == bi.OK and info.partition_fallback == 0 and info.blocks_used == 3
+    Xo = oracle.block_inverse(A, sizes)
+    kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+    assert rho(A, X) <= 1e-12
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * 700 * kappa * 2.0 ** -53
+
+
+def test_singular_leading_block_falls_back_to_eq_d(bi):
+    """A11 = 0 (Eq. (a) cannot start) but D and S_D = -B D^-1 C are invertible."""
+    g = inputs.rng(73)
+    b, m = 100, 200
+    A = np.zeros((b + m, b + m))
+    A[:b, b:] = g.standard_normal((b, m))
+    A[b:, :b] = g.standard_normal((m, b))
+    A[b:, b:] = g.uniform(-1, 1, (m, m)) + m * np.eye(m)
+    sizes = [b, m]
+    st, info, _ = ex(bi, A, sizes)
+    assert st == bi.ERR_SINGULAR and info.failing_block == 0
+    st, info, X = ex(bi, A, sizes, singular_fallback=1)
+    assert st == bi.OK and info.partition_fallback == 1 and info.blocks_used == 2
+    assert rho(A, X) <= 1e-12
+    Xo = oracle.block_inverse(A, [b + m])   # one block: Gauss-Jordan with partial pivoting
+    kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * (b + m) * kappa * 2.0 ** -53
+
+
+@pytest.mark.parametrize("sizes", [[64, 64], [40, 40, 40, 40]])
+def test_block_permutation_needs_merged_blocks(bi, sizes):
+    """Every principal block of a block-reversal permutation is singular in both
+    orders; merged blocks with partial pivoting inside invert it exactly."""
+    n = sum(sizes)
+    A = np.fliplr(np.eye(n)).copy()
+    st, info, X = ex(bi, A, sizes, singular_fallback=1)
+    assert st == bi.OK and info.partition_fallback == 2 and info.blocks_used < len(sizes)
+    assert np.array_equal(X, A.T)
+
+
+def test_singular_matrix_still_reported(bi):
+    A = np.ones((300, 300))
+    st, info, _ = ex(bi, A, [100, 100, 100], singular_fallback=1)
+    assert st == bi.ERR_SINGULAR and info.partition_fallback == 2 and info.failing_block >= 0
