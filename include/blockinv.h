@@ -143,6 +143,23 @@ int blockinv_invert_noalloc(int64_t n, int32_t p, const int32_t* block_sizes, do
  * returned at once. */
 int blockinv_invert_batched_small(int64_t count, int32_t n, double* A, int32_t* status_dev, void* stream);
 
+/* Batched inversion of `count` matrices of one order n <= 32 with one
+ * partition: the paper's tau-neutrino workload (Sec. 2: 11 x 11 matrices
+ * split into blocks of 5 and 6) and its relatives. block_sizes (host, p
+ * entries summing to n) or NULL for the paper's Table 2 rule. Eq. (a) block
+ * by block: each pivot block's Gauss-Jordan with partial pivoting inside the
+ * block, its row operations applied to whole rows (forming the row panel,
+ * the Schur complement and the column panel). A: device, count contiguous
+ * row-major n x n matrices. flags: BLOCKINV_BATCH_SPD for symmetric positive
+ * definite inputs (diagonal pivots without a search; the result is made
+ * exactly symmetric from its upper triangle). status_dev: device int32 per
+ * matrix (may be NULL): 0, SINGULAR or NONFINITE; a failed matrix is left
+ * unchanged. One matrix per 16 lanes (n <= 16) or per warp. Stream-ordered;
+ * argument errors are returned at once. */
+#define BLOCKINV_BATCH_SPD 1
+int blockinv_invert_batched_fixed(int64_t count, int32_t n, int32_t p, const int32_t* block_sizes, int32_t flags,
+                                  double* A, int32_t* status_dev, void* stream);
+
 /* Batched inversion of `count` independent FP64 matrices of uneven orders,
  * each in place (the paper's method applied to every matrix; matrices do not
  * interact). For each elimination step k, the pivot inverses, row panels and

@@ -34,6 +34,7 @@ SIGNATURES = {
     "blockinv_invert_async": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp]),
     "blockinv_invert_host": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp]),
     "blockinv_invert_batched_small": (_int, [_i64, _i32, _vp, _vp, _vp]),
+    "blockinv_invert_batched_fixed": (_int, [_i64, _i32, _i32, _i32p, _i32, _vp, _vp, _vp]),
     "blockinv_invert_batched": (_int, [_i32, _i32p, _i32p, _i32p, _vp, ctypes.POINTER(ctypes.c_int64), _int, _vp,
                                         _vp]),
     "blockinv_batch_plan_create": (_int, [_i32, _i32p, _i32p, _i32p, _vp, ctypes.POINTER(ctypes.c_int64),
@@ -161,6 +162,14 @@ def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream
 
 def blockinv_invert_batched_small(count, n, A_ptr, status_ptr=None, stream=None):
     return lib().blockinv_invert_batched_small(count, n, A_ptr, status_ptr, _stream_ptr(stream))
+
+
+BATCH_SPD = 1
+
+
+def blockinv_invert_batched_fixed(count, n, block_sizes, A_ptr, flags=0, status_ptr=None, stream=None):
+    p, arr, _ = _sizes(block_sizes)
+    return lib().blockinv_invert_batched_fixed(count, n, p, arr, flags, A_ptr, status_ptr, _stream_ptr(stream))
 
 
 def _batch_args(ns, partitions, A_ptrs, ldas):

@@ -3,6 +3,7 @@
 // per-step kernel sequence of the blockwise inversion (Eq. (a) applied once
 // per diagonal block, in place).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,28 +50,40 @@ std::vector<TraceRec> g_trace;
 // remainder handed to the last blocks); larger ones use blocks of order 256
 // with the last block taking the remainder.
 void default_partition(int n, std::vector<int>* out) {
+  if (n <= 16) {
+    paper_partition(n, out);
+    return;
+  }
+  out->clear();
+  const int p = (n + kDefaultBlock - 1) / kDefaultBlock;
+  out->assign(p, kDefaultBlock);
+  out->back() = n - kDefaultBlock * (p - 1);
+}
+
+}  // namespace
+
+// The paper's partition rule (Table 2, Eq. (blocking)): n <= 3 is one block;
+// otherwise N_k = 2^(floor(log2 n) - 1) blocks of order 2, the remainder
+// handed out one by one from the last block backwards (blocks of order 2..4).
+void paper_partition(int n, std::vector<int>* out) {
   out->clear();
   if (n <= 3) {
     out->push_back(n);
     return;
   }
-  if (n <= 16) {
-    int e = 0;
-    while ((2 << e) <= n) ++e;  // e = floor(log2 n)
-    const int nk = 1 << (e - 1);
-    out->assign(nk, 2);
-    int r = n - 2 * nk;
-    int pos = nk - 1;
-    while (r-- > 0) {
-      (*out)[pos] += 1;
-      pos = (pos == 0) ? nk - 1 : pos - 1;
-    }
-    return;
+  int e = 0;
+  while ((2 << e) <= n) ++e;  // e = floor(log2 n)
+  const int nk = 1 << (e - 1);
+  out->assign(nk, 2);
+  int r = n - 2 * nk;
+  int pos = nk - 1;
+  while (r-- > 0) {
+    (*out)[pos] += 1;
+    pos = (pos == 0) ? nk - 1 : pos - 1;
   }
-  const int p = (n + kDefaultBlock - 1) / kDefaultBlock;
-  out->assign(p, kDefaultBlock);
-  out->back() = n - kDefaultBlock * (p - 1);
 }
+
+namespace {
 
 // Mixed modes stop at the order up to which the refinement's digit products
 // are exact (FP32 group sums below 2^24, int64 accumulator below 2^63).
@@ -706,6 +719,35 @@ int blockinv_invert_batched_small(int64_t count, int32_t n, double* A, int32_t* 
     const double nd = n;
     TraceScope t("small_batched_f64", 2.0 * nd * nd * nd * (double)count, 16.0 * nd * nd * (double)count, s);
     e = launch_small_batched(n, A, count, status_dev, s);
+  }
+  return record(cuda_status(e), -1);
+}
+
+int blockinv_invert_batched_fixed(int64_t count, int32_t n, int32_t p, const int32_t* block_sizes, int32_t flags,
+                                  double* A, int32_t* status_dev, void* stream) {
+  if (count < 0 || n < 1 || n > 32 || (count > 0 && !A) || (flags & ~BLOCKINV_BATCH_SPD) ||
+      count >= (int64_t)INT32_MAX * 4)
+    return record(BLOCKINV_ERR_INVALID, -1);
+  std::vector<int> part;
+  if (block_sizes) {
+    if (p < 1 || p > n) return record(BLOCKINV_ERR_INVALID, -1);
+    int sum = 0;
+    for (int i = 0; i < p; ++i) {
+      if (block_sizes[i] < 1) return record(BLOCKINV_ERR_INVALID, -1);
+      sum += block_sizes[i];
+      part.push_back(block_sizes[i]);
+    }
+    if (sum != n) return record(BLOCKINV_ERR_INVALID, -1);
+  } else {
+    paper_partition(n, &part);
+  }
+  if (count == 0) return record(BLOCKINV_OK, -1);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  {
+    const double nd = n;
+    TraceScope t("tiny_batched_f64", 2.0 * nd * nd * nd * (double)count, 16.0 * nd * nd * (double)count, s);
+    e = launch_tiny_batched(n, part, (flags & BLOCKINV_BATCH_SPD) != 0, A, count, status_dev, s);
   }
   return record(cuda_status(e), -1);
 }

@@ -127,6 +127,13 @@ cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* statu
 
 // Hooks the serving loop (serve.cu) uses to run one request (api.cu).
 struct ServeJob;
+// The paper's partition rule (Table 2) for any order (blocks of order 2..4).
+void paper_partition(int n, std::vector<int>* out);
+
+// Batched matrices of one order n <= 32 with one partition (k_tiny.cu).
+cudaError_t launch_tiny_batched(int n, const std::vector<int>& sizes, bool spd, double* A, int64_t count,
+                                int32_t* status, cudaStream_t s);
+
 // Partition plan (the checks of blockinv_invert); FP64 elimination steps
 // k0 .. k1 - 1 in place, blocking, status as blockinv_invert.
 int plan_for(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* pl);

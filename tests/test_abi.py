@@ -145,3 +145,13 @@ def test_checkpoint_read_rejects_bad_files_before_gpu_work(lib, tmp_path):
 def test_step_range_argument_errors(lib):
     for k0, k1 in [(-1, 1), (2, 1), (0, 3)]:
         assert blockinv.blockinv_invert_steps(6, [2, 4], 0x1000, 6, k0, k1) == blockinv.ERR_INVALID
+
+
+def test_fixed_batched_argument_errors(lib):
+    f = blockinv.blockinv_invert_batched_fixed
+    assert f(10, 33, None, 0x1000) == blockinv.ERR_INVALID          # order above 32
+    assert f(10, 11, [5, 5], 0x1000) == blockinv.ERR_INVALID        # partition does not sum to n
+    assert f(10, 11, [5, 6, 0], 0x1000) == blockinv.ERR_INVALID
+    assert f(10, 11, [5, 6], 0x1000, flags=2) == blockinv.ERR_INVALID
+    assert f(10, 11, [5, 6], None) == blockinv.ERR_INVALID
+    assert f(0, 11, [5, 6], None) == blockinv.OK

@@ -249,3 +249,78 @@ def test_autotuner_choices_are_valid_and_exact(bi):
         _check_batch(mats, ts, parts, sample=inputs.rng(67).choice(300, size=40, replace=False))
     finally:
         bi.blockinv_batch_tuning_clear()
+
+
+# ------------------------------------- one order <= 32, one partition ---
+def run_fixed(bi, A, sizes, flags=0):
+    count, n, _ = A.shape
+    d = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    st = torch.full((count,), 99, dtype=torch.int32, device="cuda")
+    assert bi.blockinv_invert_batched_fixed(count, n, sizes, d.data_ptr(), flags, st.data_ptr()) == bi.OK
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), st.cpu().numpy()
+
+
+def _vs_oracle(A, X, sizes, idx):
+    for i in idx:
+        n = A.shape[1]
+        Xo = oracle.block_inverse(A[i], sizes)
+        kappa = np.linalg.norm(A[i]) * np.linalg.norm(Xo)
+        assert np.linalg.norm(X[i] - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * U64, i
+
+
+def test_tau_11x11_spd_blocks_5_6(bi):
+    """The paper's 11 x 11 systematics matrices with blocks of 5 and 6 (Sec. 2):
+    SPD B B^T + 0.1 I; exact symmetry of the result."""
+    g = inputs.rng(80)
+    B = g.standard_normal((3000, 11, 11))
+    A = B @ B.transpose(0, 2, 1) + 0.1 * np.eye(11)[None]
+    X, st = run_fixed(bi, A, [5, 6], bi.BATCH_SPD)
+    assert np.all(st == 0)
+    assert np.array_equal(X, X.transpose(0, 2, 1))
+    assert np.all(batched_rho(A, X) <= 1e-12)
+    _vs_oracle(A, X, [5, 6], range(0, 3000, 97))
+    # the general path (pivot search) on the same inputs agrees within rounding
+    Xg, stg = run_fixed(bi, A, [5, 6])
+    assert np.all(stg == 0) and np.all(batched_rho(A, Xg) <= 1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 11, 16, 17, 24, 32])
+def test_fixed_orders_paper_partition_vs_oracle(bi, n):
+    g = inputs.rng(81 + n)
+    A = g.uniform(-1, 1, size=(257, n, n)) + n * np.eye(n)[None]
+    X, st = run_fixed(bi, A, None)
+    assert np.all(st == 0)
+    assert np.all(batched_rho(A, X) <= 1e-12)
+    _vs_oracle(A, X, oracle.paper_partition(n) if n >= 2 else [1], range(0, 257, 16))
+
+
+def test_fixed_pivoting_inside_blocks(bi):
+    """Rows permuted inside each block: the diagonal pivots are zero-free only
+    after the search inside the block."""
+    g = inputs.rng(82)
+    n, sizes = 13, [4, 4, 5]
+    base = g.uniform(-1, 1, size=(200, n, n)) + n * np.eye(n)[None]
+    A = base.copy()
+    o = 0
+    for b in sizes:
+        A[:, o:o + b] = A[:, o:o + b][:, ::-1]   # reverse the block's rows
+        o += b
+    X, st = run_fixed(bi, A, sizes)
+    assert np.all(st == 0) and np.all(batched_rho(A, X) <= 1e-12)
+    _vs_oracle(A, X, sizes, range(0, 200, 11))
+
+
+def test_fixed_status_and_untouched_failures(bi):
+    g = inputs.rng(83)
+    n = 11
+    A = g.uniform(-1, 1, size=(100, n, n)) + n * np.eye(n)[None]
+    A[3, :5, :5] = 0.0          # singular first block
+    A[7, 2, 9] = np.inf
+    keep = A.copy()
+    X, st = run_fixed(bi, A, [5, 6])
+    assert st[3] == bi.ERR_SINGULAR and st[7] == bi.ERR_NONFINITE
+    ok = np.ones(100, bool)
+    ok[[3, 7]] = False
+    assert np.all(st[ok] == 0) and np.all(batched_rho(A[ok], X[ok]) <= 1e-12)
+    assert np.array_equal(X[3], keep[3]) and np.array_equal(X[7], keep[7])
