@@ -358,6 +358,12 @@ int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X,
 int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx, double* E,
                          int64_t lde, int slices, double* rho_out, void* stream);
 
+/* Workspace of the calls above comes from a device memory pool of the
+ * library's own (one per device), which keeps what it has handed out so that
+ * repeated calls do not map their workspace again. blockinv_release_memory
+ * synchronises the current device and returns the pool's unused memory. */
+int blockinv_release_memory(void);
+
 /* Human-readable name of a status code (static string). */
 const char* blockinv_status_str(int status);
 

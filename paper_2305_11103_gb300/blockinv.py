@@ -65,6 +65,7 @@ SIGNATURES = {
     "blockinv_status_str": (ctypes.c_char_p, [_int]),
     "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_version": (_int, []),
+    "blockinv_release_memory": (_int, []),
     "blockinv_invert_ex": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp, _vp]),
     "blockinv_diag_gemm": (_int, [_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "blockinv_trace_enable": (_int, [_int]),

@@ -123,12 +123,52 @@ struct AsyncBuf {
   cudaStream_t s = nullptr;
   cudaError_t alloc(size_t bytes, cudaStream_t stream) {
     s = stream;
-    return cudaMallocAsync(&ptr, bytes ? bytes : 16, stream);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = workspace_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(&ptr, bytes ? bytes : 16, pool, stream);
   }
   ~AsyncBuf() {
     if (ptr) cudaFreeAsync(ptr, s);
   }
 };
+
+}  // namespace
+
+// Workspace comes from a memory pool of the library's own per device, which
+// keeps the memory it has handed out (release threshold: unlimited) so that
+// repeated solves do not map their workspace again; blockinv_release_memory
+// gives it back. The caller's default pool is left as it is.
+cudaError_t workspace_pool(cudaMemPool_t* out) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    pools[dev] = p;
+  }
+  *out = pools[dev];
+  return cudaSuccess;
+}
+
+namespace {
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return BLOCKINV_OK;
@@ -775,6 +815,14 @@ int blockinv_last_error_detail(int64_t* failing_block) {
 }
 
 int blockinv_version(void) { return 100; }
+
+int blockinv_release_memory(void) {
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = workspace_pool(&pool);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+  return cuda_status(e);
+}
 
 int blockinv_trace_enable(int on) {
   std::vector<TraceRec> old;

@@ -127,6 +127,9 @@ cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* statu
 
 // Hooks the serving loop (serve.cu) uses to run one request (api.cu).
 struct ServeJob;
+// The library's device memory pool for workspace on the current device.
+cudaError_t workspace_pool(cudaMemPool_t* out);
+
 // The paper's partition rule (Table 2) for any order (blocks of order 2..4).
 void paper_partition(int n, std::vector<int>* out);
 

@@ -12,6 +12,8 @@
 // recovered afterwards by Newton-Schulz refinement against the FP64 input.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "tc_gemm.cuh"
 
 namespace blockinv {
@@ -70,7 +72,7 @@ __global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx,
 // rounded, to Vt[j][0..kpad) (zero beyond b). Extra CTAs pack
 // U[i][l] = X32[i][o + l] for rows outside block k (zero elsewhere).
 constexpr int kCols = 32;
-constexpr int kKc = 8;
+constexpr int kKc = 8;  // k columns of P^-1 per shared-memory chunk (double-buffered)
 
 // Operands are stored as `nsl` slices of kpad columns: slice 0 holds the
 // rounded value (hi), slice 1 (if present) the rounded remainder (lo), so
@@ -85,59 +87,116 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
   const int tid = threadIdx.x;
   const int64_t ldop = (int64_t)nsl * kpad;
   if ((int)blockIdx.x >= col_tiles) {
-    const int64_t total = (int64_t)n * kpad;
+    // U: four consecutive columns per thread and step (kpad is a multiple of 64)
+    const int q4 = kpad / 4;
+    const int64_t total = (int64_t)n * q4;
     const int64_t stride = (int64_t)(gridDim.x - col_tiles) * blockDim.x;
     for (int64_t e = (int64_t)(blockIdx.x - col_tiles) * blockDim.x + tid; e < total; e += stride) {
-      const int i = (int)(e / kpad);
-      const int l = (int)(e - (int64_t)i * kpad);
-      const bool keep = l < b && !(i >= o && i < o + b);
-      const float v = keep ? X[(int64_t)i * ldx + o + l] : 0.f;
-      const auto hi = Op::cvt(v);
-      U[(int64_t)i * ldop + l] = hi;
-      if (nsl > 1) U[(int64_t)i * ldop + kpad + l] = Op::cvt(v - static_cast<float>(hi));
+      const int i = (int)(e / q4);
+      const int l0 = 4 * (int)(e - (int64_t)i * q4);
+      const bool row_keep = !(i >= o && i < o + b);
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = (row_keep && l0 + u < b) ? X[(int64_t)i * ldx + o + l0 + u] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const auto hi = Op::cvt(v[u]);
+        U[(int64_t)i * ldop + l0 + u] = hi;
+        if (nsl > 1) U[(int64_t)i * ldop + kpad + l0 + u] = Op::cvt(v[u] - static_cast<float>(hi));
+      }
     }
     return;
   }
-  extern __shared__ float sm[];
-  float* Ps = sm;                       // [kKc][MAXB]
-  float* Xs = Ps + kKc * MAXB;          // [kKc][kCols]
-  float* Vs = Xs + kKc * kCols;         // [kCols][MAXB + 1]
-  constexpr int RPT = MAXB / 8;
-  const int c = tid & 31;
-  const int g = tid >> 5;
+  extern __shared__ __align__(16) float sm[];
+  // two chunks of P^-1 columns (rows padded to MAXB + 4: the fill, k fastest,
+  // hits 32 different banks) and of the strip's rows of X
+  constexpr int PLD = MAXB + 4;
+  float* Ps = sm;                        // [2][kKc][PLD]
+  float* Xs = Ps + 2 * kKc * PLD;        // [2][kKc][kCols]
+  float* Vs = Xs + 2 * kKc * kCols;      // [kCols][MAXB + 1]
+  // thread (rg, cg): rows rg * RPT .. + RPT, columns 4 cg .. + 4 of the strip;
+  // per k step RPT / 4 + 1 vector loads from shared memory feed 4 RPT FMAs
+  // (rows of Ps at or past b are never written: their results are dropped)
+  constexpr int RPT = MAXB / 32;
+  constexpr int PF = MAXB * kKc / 256;   // P^-1 elements per thread per chunk
+  const int cg = tid & 7;
+  const int rg = tid >> 3;
   const int j0 = blockIdx.x * kCols;
-  const int j = j0 + c;
-  float acc[RPT];
+  float acc[RPT][4];
 #pragma unroll
-  for (int q = 0; q < RPT; ++q) acc[q] = 0.f;
-  for (int kc = 0; kc < b; kc += kKc) {
-    for (int e = tid; e < b * kKc; e += 256) {
-      const int r = e / kKc;
-      const int kk = e - r * kKc;
-      Ps[kk * MAXB + r] = (kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+  float rp[PF], rx;
+  auto fetch = [&](int kc) {  // global -> registers
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + q * 256;
+      const int r = e / kKc, kk = e - r * kKc;
+      rp[q] = (r < b && kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
     }
-    {
-      const int kk = tid >> 5;
-      const int jj = j0 + (tid & 31);
-      Xs[kk * kCols + (tid & 31)] = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+    const int kk = tid >> 5;
+    const int jj = j0 + (tid & 31);
+    rx = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+  };
+  auto stash = [&](int buf) {  // registers -> shared chunk buf
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int e = tid + q * 256;
+      const int r = e / kKc, kk = e - r * kKc;
+      Ps[(buf * kKc + kk) * PLD + r] = rp[q];
     }
-    __syncthreads();
+    Xs[(buf * kKc + (tid >> 5)) * kCols + (tid & 31)] = rx;
+  };
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int kc = 0; kc < b; kc += kKc, buf ^= 1) {
+    const bool more = kc + kKc < b;
+    if (more) fetch(kc + kKc);  // in flight while this chunk is used
+    const float* P0 = Ps + buf * kKc * PLD;
+    const float* X0 = Xs + buf * kKc * kCols;
 #pragma unroll
     for (int kk = 0; kk < kKc; ++kk) {
-      const float x = Xs[kk * kCols + c];
+      const float4 xv = *reinterpret_cast<const float4*>(&X0[kk * kCols + 4 * cg]);
+      float pv[RPT];
+      if constexpr (RPT % 4 == 0) {
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) acc[q] = fmaf(Ps[kk * MAXB + g + 8 * q], x, acc[q]);
+        for (int r = 0; r < RPT; r += 4) {
+          const float4 t = *reinterpret_cast<const float4*>(&P0[kk * PLD + rg * RPT + r]);
+          pv[r] = t.x;
+          pv[r + 1] = t.y;
+          pv[r + 2] = t.z;
+          pv[r + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) pv[r] = P0[kk * PLD + rg * RPT + r];
+      }
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        acc[r][0] = fmaf(pv[r], xv.x, acc[r][0]);
+        acc[r][1] = fmaf(pv[r], xv.y, acc[r][1]);
+        acc[r][2] = fmaf(pv[r], xv.z, acc[r][2]);
+        acc[r][3] = fmaf(pv[r], xv.w, acc[r][3]);
+      }
     }
+    if (more) stash(buf ^ 1);  // the other chunk was last read before the previous barrier
     __syncthreads();
   }
-  const bool pivot_col = (j >= o && j < o + b);
 #pragma unroll
-  for (int q = 0; q < RPT; ++q) {
-    const int r = g + 8 * q;
-    if (r < b) {
-      const float v = (j < n) ? (pivot_col ? Pinv[(int64_t)r * b + (j - o)] : acc[q]) : 0.f;
-      if (j < n) X[(int64_t)(o + r) * ldx + j] = v;
-      Vs[c * (MAXB + 1) + r] = v;
+  for (int r = 0; r < RPT; ++r) {
+    const int row = rg * RPT + r;
+    if (row >= b) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 4 * cg + q;
+      const int j = j0 + c;
+      const bool pivot_col = (j >= o && j < o + b);
+      const float v = (j < n) ? (pivot_col ? Pinv[(int64_t)row * b + (j - o)] : acc[r][q]) : 0.f;
+      if (j < n) X[(int64_t)(o + row) * ldx + j] = v;
+      Vs[c * (MAXB + 1) + row] = v;
     }
   }
   __syncthreads();
@@ -185,8 +244,10 @@ cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float
                          int kpad, int nsl, const int32_t* status, cudaStream_t s) {
   using T = typename OpType<kBF16>::T;
   const int col_tiles = (n + kCols - 1) / kCols;
-  const int grid = col_tiles + 64;
-  const size_t smem = sizeof(float) * ((size_t)kKc * MAXB + kKc * kCols + (size_t)kCols * (MAXB + 1));
+  // packing CTAs: about 16 columns of U per thread
+  const int64_t pack_threads = ((int64_t)n * kpad / 16 + 255) / 256;
+  const int grid = col_tiles + (int)std::max<int64_t>(8, std::min<int64_t>(pack_threads, 4096));
+  const size_t smem = sizeof(float) * (2 * (size_t)kKc * (MAXB + 4) + 2 * kKc * kCols + (size_t)kCols * (MAXB + 1));
   auto k = row_panel_mixed_kernel<MAXB, kBF16>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

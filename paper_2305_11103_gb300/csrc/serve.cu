@@ -94,7 +94,9 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
   cudaError_t e = cudaSuccess;
   sl.dbuf = nullptr;
   if (r->host) {
-    e = cudaMallocAsync(reinterpret_cast<void**>(&sl.dbuf), row * n, s);
+    cudaMemPool_t pool = nullptr;
+    e = workspace_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&sl.dbuf), row * n, pool, s);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(sl.dbuf, row, r->A, sizeof(double) * r->lda, row, n, cudaMemcpyHostToDevice, s);
     X = sl.dbuf;

@@ -245,3 +245,11 @@ def test_full_size_8192(bi):
     S = np.linalg.solve(A, E)
     for t, j in enumerate(cols):
         assert np.linalg.norm(X[:, j] - S[:, t]) / np.linalg.norm(S[:, t]) <= 4 * n * 10 * U64
+
+
+def test_release_memory_then_invert_again(bi):
+    A = inputs.diag_dominant_uniform(600, 77, shift=600)
+    X1 = gpu_invert(bi, A, [256, 256, 88])
+    assert bi.lib().blockinv_release_memory() == bi.OK
+    X2 = gpu_invert(bi, A, [256, 256, 88])
+    assert np.array_equal(X1, X2)
