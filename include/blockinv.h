@@ -324,7 +324,8 @@ typedef struct {
   int32_t partition_fallback; /* 0: the requested partition and order; 1: the other  */
                           /* pivot order; 2: merged blocks (singular_fallback)          */
   int32_t blocks_used;    /* pivot blocks of the partition that produced the result    */
-  int32_t reserved[4];
+  int32_t incremental_residuals; /* mixed modes: residuals formed as E - A (X - X_prev) */
+  int32_t reserved[3];
 } blockinv_info;
 
 /* blockinv_invert with options and a report (either pointer may be NULL). */

@@ -83,7 +83,8 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("refine_iters", ctypes.c_int32), ("failing_block", ctypes.c_int64),
                 ("rho", ctypes.c_double), ("rho_initial", ctypes.c_double), ("used_fallback", ctypes.c_int32),
                 ("fp64_pivots", ctypes.c_int32), ("partition_fallback", ctypes.c_int32),
-                ("blocks_used", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("blocks_used", ctypes.c_int32), ("incremental_residuals", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -384,8 +384,8 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
   const size_t row = sizeof(double) * (size_t)n;
   cudaError_t e = ms.a0.alloc(row * n, s);
   if (e == cudaSuccess) e = ms.hist.alloc(sizeof(double) * (opt.max_refine + 1), s);
-  if (e == cudaSuccess) e = ms.ctl.alloc(4 * sizeof(int32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ms.ctl.ptr, 0, 4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = ms.ctl.alloc(kRefineCtlWords * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ms.ctl.ptr, 0, kRefineCtlWords * sizeof(int32_t), s);
   if (e == cudaSuccess) e = ms.piv.alloc(2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.piv.ptr, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.hist.ptr, 0xFF, sizeof(double) * (opt.max_refine + 1), s);
@@ -423,13 +423,14 @@ int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, c
 void read_mixed_info(const MixedState& ms, cudaStream_t s, blockinv_info* info) {
   if (!info || !ms.hist.ptr) return;
   std::vector<double> hist(ms.max_refine + 1, -1.0);
-  int32_t ctl[4] = {0, 0, 0, -1};
+  int32_t ctl[kRefineCtlWords] = {0, 0, 0, -1};
   int32_t piv[2] = {0, 0};
   cudaMemcpyAsync(hist.data(), ms.hist.ptr, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(ctl, ms.ctl.ptr, sizeof(ctl), cudaMemcpyDeviceToHost, s);
   if (ms.piv.ptr) cudaMemcpyAsync(piv, ms.piv.ptr, sizeof(piv), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return;
   info->refine_iters = ctl[1];
+  info->incremental_residuals = ctl[5];
   info->fp64_pivots = piv[1];
   if (ctl[3] >= 0) {
     info->rho_initial = hist[0];
@@ -732,7 +733,7 @@ int blockinv_residual_tc(int64_t n, const double* A, int64_t lda, const double* 
   AsyncBuf ws, hist, ctl, sbuf;
   cudaError_t e = ws.alloc(refine_workspace_bytes((int)n, slices, 0), s);
   if (e == cudaSuccess) e = hist.alloc(sizeof(double), s);
-  if (e == cudaSuccess) e = ctl.alloc(4 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = ctl.alloc(kRefineCtlWords * sizeof(int32_t), s);
   if (e == cudaSuccess) e = sbuf.alloc(2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess)

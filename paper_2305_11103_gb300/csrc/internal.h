@@ -151,6 +151,7 @@ int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda
                            cudaStream_t s);
 
 // Newton-Schulz refinement with the FP64-accurate tensor-core residual (k_refine.cu).
+constexpr int kRefineCtlWords = 8;      // int32 control words of a refinement
 constexpr int kResidualSlices = 9;      // base-32 digits per operand (44 bits)
 constexpr int kMinResidualSlices = 7;
 constexpr int kMaxResidualSlices = 9;    // int64 accumulator bound at n = 16384

@@ -219,7 +219,7 @@ struct EpiSchurF32 {
   int n, o, b;
   const int32_t* status;
   __device__ bool skip() const { return failed(status); }
-  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+  __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
     const bool pivot_col = col >= o && col < o + b;
     float* p = X + (int64_t)row0 * ldx + col;

@@ -47,6 +47,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 
 #include "tc_gemm.cuh"
 
@@ -57,16 +58,33 @@ namespace {
 constexpr int kLog2Digit = 5;  // base-32 digits
 constexpr int kHeadroom = 1;   // fraction bits F = 5 S - 1 keep the leading digit within [-16, 16]
 constexpr int kUpdateChunkK = 2048;  // K elements per accumulator hand-off in the update
+// Incremental residual E_new = E - A (X_new - X): the change of X is cut into
+// base-32 digits like X, but kIncrGroups digit groups suffice (28 products
+// instead of 45) while ||E||_F <= kIncrMaxE, since its column scales are then
+// at most 2^-10 of X's and the dropped groups stay below the fresh residual's
+// error floor.
+constexpr int kIncrGroups = 7;
+constexpr double kIncrMaxE = 1e-3;
 
 struct Ctl {
   int32_t done;        // refinement finished (converged or gave up)
   int32_t updates;     // updates applied
   int32_t code;        // BLOCKINV_OK or BLOCKINV_ERR_NOT_CONVERGED once done
   int32_t last;        // index of the last residual computed
+  int32_t inc;         // the next residual is incremental (E_new = E - A (X_new - X))
+  int32_t incs;        // incremental residuals computed
 };
+static_assert(sizeof(Ctl) <= sizeof(int32_t) * kRefineCtlWords, "refinement control words");
 
-__device__ __forceinline__ bool halted(const Ctl* ctl, const int32_t* status) {
-  return *(volatile const int32_t*)&ctl->done != 0 || *(volatile const int32_t*)status != 0;
+// Which residual a kernel belongs to: every one, the fresh one (all digits of
+// X) or the incremental one (digits of the change of X).
+enum Path { kAny = 0, kFresh = 1, kIncr = 2 };
+
+__device__ __forceinline__ bool halted(const Ctl* ctl, const int32_t* status, int path = kAny) {
+  if (*(volatile const int32_t*)&ctl->done != 0 || *(volatile const int32_t*)status != 0) return true;
+  if (path == kAny) return false;
+  const bool inc = *(volatile const int32_t*)&ctl->inc != 0;
+  return path == kFresh ? inc : !inc;
 }
 
 // Smallest e with |v| < 2^e for normal v (from the exponent field); very
@@ -144,8 +162,8 @@ __global__ void row_scale_kernel(const double* __restrict__ M, int64_t ld, int n
 // Column exponent bounds (atomicMax per column after a CTA reduction) and the
 // sum of squares. cexp must hold a very negative value beforehand.
 __global__ void col_scale_kernel(const double* __restrict__ X, int64_t ld, int n, int32_t* __restrict__ cexp,
-                                 double* __restrict__ sumsq, const Ctl* ctl, const int32_t* status) {
-  if (halted(ctl, status)) return;
+                                 double* __restrict__ sumsq, const Ctl* ctl, const int32_t* status, int path) {
+  if (halted(ctl, status, path)) return;
   __shared__ int se[8][32];
   __shared__ double ss[8];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -169,7 +187,7 @@ __global__ void col_scale_kernel(const double* __restrict__ X, int64_t ld, int n
     int m = se[0][tx];
     for (int y = 1; y < 8; ++y) m = max(m, se[y][tx]);
     if (j < n) atomicMax(&cexp[j], m);
-    if (tx == 0) {
+    if (tx == 0 && sumsq) {
       double t = 0.0;
       for (int y = 0; y < 8; ++y) t += ss[y];
       atomicAdd(sumsq, t);
@@ -212,8 +230,8 @@ __global__ void slice_rows_kernel(const double* __restrict__ M, int64_t ld, int 
 template <int S>
 __global__ void __launch_bounds__(256)
 slice_cols_t_kernel(const double* __restrict__ X, int64_t ld, int n, const int32_t* __restrict__ cexp, int Kp,
-                    uint8_t* __restrict__ out, const Ctl* ctl, const int32_t* status) {
-  if (halted(ctl, status)) return;
+                    uint8_t* __restrict__ out, const Ctl* ctl, const int32_t* status, int path) {
+  if (halted(ctl, status, path)) return;
   __shared__ uint8_t sd[S][32][68];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
@@ -250,8 +268,9 @@ struct EpiAccumI64 {
   int first;
   const Ctl* ctl;
   const int32_t* status;
-  __device__ bool skip() const { return halted(ctl, status); }
-  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+  int path;
+  __device__ bool skip() const { return halted(ctl, status, path); }
+  __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
     long long* p = T + (int64_t)row0 * ldt + col;
     // two halves of 16 rows: all loads of a half before its stores
@@ -267,27 +286,67 @@ struct EpiAccumI64 {
   }
 };
 
+// X += the chunk's product. With an incremental residual to follow, D gets
+// the change of X: the first chunk leaves X_old in D, the last one X_new - D
+// (one FP64 rounding of the change).
 struct EpiAddF64 {
   double* X;
   int64_t ldx;
   int n;
   const Ctl* ctl;
   const int32_t* status;
+  double* D;  // may be null
+  int64_t ldd;
   __device__ bool skip() const { return halted(ctl, status); }
-  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+  __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
+    const bool keep = D && *(volatile const int32_t*)&ctl->inc != 0;
+    const bool first = chunk == 0, last = chunk == nchunks - 1;
     double* p = X + (int64_t)row0 * ldx + col;
+    double* d = keep ? D + (int64_t)row0 * ldd + col : nullptr;
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
-      double cur[16];
+      double cur[16], old[16];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) cur[r] = (row0 + h + r < n) ? p[(int64_t)(h + r) * ldx] : 0.0;
+      for (int r = 0; r < 16; ++r) {
+        const bool in = row0 + h + r < n;
+        cur[r] = in ? p[(int64_t)(h + r) * ldx] : 0.0;
+        old[r] = (in && keep && last && !first) ? d[(int64_t)(h + r) * ldd] : cur[r];
+      }
 #pragma unroll
-      for (int r = 0; r < 16; ++r)
-        if (row0 + h + r < n) p[(int64_t)(h + r) * ldx] = cur[r] + static_cast<double>(v[h + r]);
+      for (int r = 0; r < 16; ++r) {
+        if (row0 + h + r >= n) continue;
+        const double xn = cur[r] + static_cast<double>(v[h + r]);
+        p[(int64_t)(h + r) * ldx] = xn;
+        if (keep && last) d[(int64_t)(h + r) * ldd] = xn - old[r];
+        else if (keep && first) d[(int64_t)(h + r) * ldd] = cur[r];
+      }
     }
   }
 };
+
+// Sum of squares of X (the ||X||^2 of an incremental residual's rho).
+__global__ void sumsq_kernel(const double* __restrict__ X, int64_t ldx, int n, double* sumsq, const Ctl* ctl,
+                             const int32_t* status, int path) {
+  if (halted(ctl, status, path)) return;
+  __shared__ double red[8];
+  double s2 = 0.0;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n;
+    const double v = X[i * ldx + (t - i * n)];
+    s2 = fma(v, v, s2);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(sumsq, t);
+  }
+}
 
 __device__ __forceinline__ float tf32_rn(float x) {
   uint32_t u;
@@ -309,8 +368,11 @@ __global__ void __launch_bounds__(256)
 finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const double* __restrict__ A,
                 int64_t lda, const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ rexp,
                 const int32_t* __restrict__ cexp, int S, double* __restrict__ e2sum, float* __restrict__ Eop,
-                int Kp, double* __restrict__ Eout, int64_t lde, const Ctl* ctl, const int32_t* status) {
-  if (halted(ctl, status)) return;
+                int Kp, double* Eout, int64_t lde, const double* Ebase, int64_t ldb, const Ctl* ctl,
+                const int32_t* status, int path) {
+  // Ebase null: E = I - A X. Otherwise (incremental residual, X = the change
+  // of the iterate): E = Ebase - A X; Ebase and Eout may be the same matrix.
+  if (halted(ctl, status, path)) return;
   __shared__ double tile[32][33];
   __shared__ double red[8];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -325,7 +387,10 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
       const long long t = T[(int64_t)i * ldt + j];
       const double r = (t == 0) ? 0.0 : static_cast<double>(t) * pow2(ex);
       const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
-      if (i == j) {
+      if (Ebase) {
+        const double base = Ebase[(int64_t)i * ldb + j];
+        e = (i == j) ? (base - dx) - r : (base - fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx)) - r;
+      } else if (i == j) {
         e = (1.0 - dx) - r;
       } else {
         e = -fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx) - r;   // (O_A D_X)_ij
@@ -379,13 +444,16 @@ __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n,
 }
 
 // rho for residual `it`; decides whether refinement goes on.
+// The next residual is incremental when incr_ok (its buffers exist) and
+// ||E||_F <= kIncrMaxE.
 __global__ void decide_kernel(const double* sums, int it, double tol, int max_updates, double* hist, Ctl* ctl,
-                              const int32_t* status) {
+                              const int32_t* status, int incr_ok) {
   if (ctl->done || *status != 0) return;
   const double a2 = sums[0], e2 = sums[1 + 2 * it], x2 = sums[2 + 2 * it];
   const double rho = sqrt(e2) / (sqrt(a2) * sqrt(x2));
   hist[it] = rho;
   ctl->last = it;
+  if (ctl->inc) ctl->incs += 1;
   if (rho <= tol) {
     ctl->done = 1;
     ctl->code = BLOCKINV_OK;
@@ -394,6 +462,7 @@ __global__ void decide_kernel(const double* sums, int it, double tol, int max_up
     ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
   } else {
     ctl->updates = it + 1;
+    ctl->inc = (incr_ok && sqrt(e2) <= kIncrMaxE) ? 1 : 0;
   }
 }
 
@@ -407,6 +476,8 @@ __global__ void init_ctl_kernel(Ctl* ctl, int32_t* cexp, int n, int iters) {
     ctl->updates = 0;
     ctl->code = BLOCKINV_ERR_NOT_CONVERGED;
     ctl->last = -1;
+    ctl->inc = 0;
+    ctl->incs = 0;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * iters; t += gridDim.x * blockDim.x) cexp[t] = -2000;
 }
@@ -414,7 +485,7 @@ __global__ void init_ctl_kernel(Ctl* ctl, int32_t* cexp, int n, int iters) {
 template <int S>
 cudaError_t launch_slices(const double* A0, int64_t ld0, const double* X, int64_t ldx, int n, int Kp,
                           const int32_t* rexp, int32_t* cexp, uint8_t* Asl, uint8_t* Xsl, double* x2, bool rows,
-                          const Ctl* ctl, const int32_t* status, cudaStream_t s) {
+                          const Ctl* ctl, const int32_t* status, cudaStream_t s, int path) {
   if (rows) {
     const int64_t quads = (int64_t)n * (Kp / 4);
     const int grid = (int)std::min<int64_t>((quads + 255) / 256, 16 * tc::num_sms());
@@ -422,19 +493,19 @@ cudaError_t launch_slices(const double* A0, int64_t ld0, const double* X, int64_
     return cudaGetLastError();
   }
   dim3 g1((n + 31) / 32, (n + 255) / 256);
-  col_scale_kernel<<<g1, 256, 0, s>>>(X, ldx, n, cexp, x2, ctl, status);
+  col_scale_kernel<<<g1, 256, 0, s>>>(X, ldx, n, cexp, x2, ctl, status, path);
   dim3 g2((n + 31) / 32, Kp / 64);
-  slice_cols_t_kernel<S><<<g2, 256, 0, s>>>(X, ldx, n, cexp, Kp, Xsl, ctl, status);
+  slice_cols_t_kernel<S><<<g2, 256, 0, s>>>(X, ldx, n, cexp, Kp, Xsl, ctl, status, path);
   return cudaGetLastError();
 }
 
 cudaError_t slices_dispatch(int S, const double* A0, int64_t ld0, const double* X, int64_t ldx, int n, int Kp,
                             const int32_t* rexp, int32_t* cexp, uint8_t* Asl, uint8_t* Xsl, double* x2, bool rows,
-                            const Ctl* ctl, const int32_t* status, cudaStream_t s) {
+                            const Ctl* ctl, const int32_t* status, cudaStream_t s, int path = kAny) {
   switch (S) {
-    case 7: return launch_slices<7>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 8: return launch_slices<8>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
-    case 9: return launch_slices<9>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s);
+    case 7: return launch_slices<7>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s, path);
+    case 8: return launch_slices<8>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s, path);
+    case 9: return launch_slices<9>(A0, ld0, X, ldx, n, Kp, rexp, cexp, Asl, Xsl, x2, rows, ctl, status, s, path);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -450,7 +521,8 @@ size_t refine_workspace_bytes(int n, int S, int max_updates) {
   b += 2 * sizeof(float) * (size_t)n * 2 * Kp;  // X and E^T TF32 hi/lo operands
   b += sizeof(int32_t) * (size_t)n * (max_updates + 2);   // exponents
   b += sizeof(double) * (3 + 2 * (max_updates + 1)) + sizeof(double) * (max_updates + 1) + 64;
-  return b + 8 * 256;
+  if (max_updates > 0) b += 2 * sizeof(double) * (size_t)n * ldt;  // E and the change of X (incremental)
+  return b + 10 * 256;
 }
 
 // Enqueue the refinement of X (n x n, FP64, in place) toward A0^-1.
@@ -485,6 +557,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
   int32_t* rexp = static_cast<int32_t*>(carve(sizeof(int32_t) * n));
   int32_t* cexp = static_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)n * (max_updates + 1)));
   double* sums = static_cast<double*>(carve(sizeof(double) * (1 + 2 * (max_updates + 1))));
+  const bool incr_ok = max_updates > 0;
+  double* Ebuf = incr_ok ? static_cast<double*>(carve(sizeof(double) * (size_t)n * ldt)) : nullptr;
+  double* Dbuf = incr_ok ? static_cast<double*>(carve(sizeof(double) * (size_t)n * ldt)) : nullptr;
 
   cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * (1 + 2 * (max_updates + 1)), s);
   // K padding of the operands must be zero (only columns < n are written).
@@ -508,18 +583,12 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     row_scale_kernel<<<(n + 7) / 8, 256, 0, s>>>(A0, ld0, n, rexp, &sums[0], ctl, status);
     e = slices_dispatch(S, A0, ld0, nullptr, 0, n, Kp, rexp, nullptr, Asl, nullptr, nullptr, true, ctl, status, s);
   }
-  for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {
-    int32_t* cx = cexp + (size_t)it * n;
-    {
-      TraceScope t("residual_slice_x", 0, 16.0 * nd * nd + (double)S * nd * Kp, s);
-      e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
-                          status, s);
-    }
-    // Every residual keeps all S digit groups: the first one steers the first
-    // update, and its error (not rho_0 squared) bounds rho after that update.
-    const int groups = S;
-    for (int g = 0; g < groups && e == cudaSuccess; ++g) {
-      for (int p0 = 0; p0 <= g && e == cudaSuccess; p0 += max_pairs) {
+  // the digit-group GEMMs of one residual: groups 0 .. groups - 1, each over
+  // at most max_pairs digit pairs per launch
+  auto group_gemms = [&](int groups, int path) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    for (int g = 0; g < groups && r == cudaSuccess; ++g) {
+      for (int p0 = 0; p0 <= g && r == cudaSuccess; p0 += max_pairs) {
         const int np = std::min(max_pairs, g + 1 - p0);
         tc::KMap km{};
         km.kb_per_pair = Kp / 128;
@@ -529,28 +598,64 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
           km.pa[i] = (int8_t)(p0 + i);
           km.pb[i] = (int8_t)(g - p0 - i);
         }
-        EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0, ctl, status};
+        EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0, ctl, status, path};
         TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-        e = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
+        r = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
       }
     }
-    if (e != cudaSuccess) break;
-    {
-      TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 8.0 * nd * nd : 0.0), s);
-      dim3 g((n + 31) / 32, (n + 31) / 32);
-      finalize_kernel<<<g, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, groups, &sums[1 + 2 * it],
-                                        it < max_updates ? Eop : nullptr, Kp,
-                                        (max_updates == 0) ? Eout : nullptr, lde, ctl, status);
+    return r;
+  };
+  bool next_inc = false;  // host view of ctl->inc (host_steps)
+  for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {
+    int32_t* cx = cexp + (size_t)it * n;
+    dim3 fg((n + 31) / 32, (n + 31) / 32);
+    // Fresh residual E = I - A X from all S digits of X; or, after a residual
+    // with ||E||_F <= kIncrMaxE, E_new = E - A (X - X_prev) from kIncrGroups
+    // groups of the change of X. Without host steps both are enqueued and the
+    // device flag lets one of them run.
+    const bool fresh = !host_steps || !next_inc;
+    const bool incr = incr_ok && it > 0 && (!host_steps || next_inc);
+    if (fresh) {
+      {
+        TraceScope t("residual_slice_x", 0, 16.0 * nd * nd + (double)S * nd * Kp, s);
+        e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
+                            status, s, incr ? kFresh : kAny);
+      }
+      if (e == cudaSuccess) e = group_gemms(S, incr ? kFresh : kAny);
+      if (e != cudaSuccess) break;
+      TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 16.0 * nd * nd : 0.0), s);
+      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
+                                         it < max_updates ? Eop : nullptr, Kp,
+                                         (max_updates == 0) ? Eout : (it < max_updates ? Ebuf : nullptr),
+                                         (max_updates == 0) ? lde : ldt, nullptr, 0, ctl, status,
+                                         incr ? kFresh : kAny);
     }
-    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status);
+    if (incr && e == cudaSuccess) {
+      {
+        TraceScope t("residual_slice_dx", 0, 24.0 * nd * nd + (double)S * nd * Kp, s);
+        e = slices_dispatch(S, nullptr, 0, Dbuf, ldt, n, Kp, rexp, cx, nullptr, Xsl, nullptr, false, ctl, status, s,
+                            fresh ? kIncr : kAny);
+        sumsq_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(X, ldx, n, &sums[2 + 2 * it], ctl, status,
+                                                      fresh ? kIncr : kAny);
+      }
+      if (e == cudaSuccess) e = group_gemms(kIncrGroups, fresh ? kIncr : kAny);
+      if (e != cudaSuccess) break;
+      TraceScope t("residual_finalize", 0, 24.0 * nd * nd, s);
+      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, Dbuf, ldt, rexp, cx, kIncrGroups, &sums[1 + 2 * it],
+                                         it < max_updates ? Eop : nullptr, Kp, Ebuf, ldt, Ebuf, ldt, ctl, status,
+                                         fresh ? kIncr : kAny);
+    }
+    decide_kernel<<<1, 1, 0, s>>>(sums, it, tol, max_updates, hist, ctl, status, incr_ok ? 1 : 0);
     if (it == max_updates) break;
     if (host_steps) {
       // Blocking callers stop enqueueing as soon as the device has decided.
-      int32_t h[2] = {0, 0};
-      e = cudaMemcpyAsync(h, ctl_words, sizeof(h), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      int32_t h[kRefineCtlWords + 1] = {};
+      e = cudaMemcpyAsync(h, ctl_words, sizeof(int32_t) * kRefineCtlWords, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h[kRefineCtlWords], status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess || h[0] != 0 || h[1] != 0) break;
+      if (e != cudaSuccess || h[0] != 0 || h[kRefineCtlWords] != 0) break;
+      next_inc = h[offsetof(Ctl, inc) / sizeof(int32_t)] != 0;
     }
     {
       TraceScope t("ns_split_x", 0, 16.0 * nd * nd, s);
@@ -570,7 +675,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       // own; the hi*lo and lo*hi products (2^-11 smaller) form one more chunk.
       km.chunk_kb = kUpdateChunkK / 32;
       km.chunk_end = km.kb_per_pair;
-      EpiAddF64 epi{X, ldx, n, ctl, status};
+      EpiAddF64 epi{X, ldx, n, ctl, status, Dbuf, ldt};
       const double chunks = std::ceil((double)Kp / kUpdateChunkK) + 1.0;
       TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd * chunks + 16.0 * nd * Kp, s);
       e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true>(tXo, tEo, n, n, km, epi, status, s);

@@ -55,7 +55,7 @@ struct EpiStoreF32 {
   int64_t ldc;
   int M, N;
   __device__ bool skip() const { return false; }
-  __device__ void apply_cols(int row0, int col, const float (&v)[32]) const {
+  __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= N) return;
 #pragma unroll
     for (int r = 0; r < 32; ++r)

@@ -3,8 +3,9 @@
 // shared-memory ring (128-byte swizzle), accumulated by tcgen05.mma into one
 // of two TMEM accumulators (128 lanes x 256 columns each), and handed to an
 // epilogue functor that reads the accumulator with tcgen05.ld. The functor's
-// apply_cols(row0, col, v) receives column `col` of rows row0 .. row0 + 31
-// (v[r] = D[row0 + r][col]; the 32 lanes of a warp hold 32 adjacent columns).
+// apply_cols(row0, col, v, chunk, nchunks) receives column `col` of rows
+// row0 .. row0 + 31 (v[r] = D[row0 + r][col]; the 32 lanes of a warp hold 32
+// adjacent columns) for K-chunk `chunk` of `nchunks` (see chunk_kb).
 //
 //   warp 0, lane 0   TMA producer            (also allocates/frees TMEM)
 //   warp 1, lane 0   MMA issuer
@@ -266,7 +267,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int r = 0; r < 32; ++r) col[r] = stage[r * kStagePitch + lane];
         __syncwarp();
-        epi.apply_cols(row0, n0 + c * 32 + lane, col);
+        epi.apply_cols(row0, n0 + c * 32 + lane, col, w % nch, nch);
       }
       fence_before_sync();
       mbar_arrive(&sh->tempty[a]);

@@ -232,3 +232,19 @@ def test_ill_conditioned_first_block_refines(bi):
     X = d.cpu().numpy()
     r = np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X))
     assert r <= 1e-12, (r, info.as_dict())
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_incremental_residual_matches_fresh(bi, mode):
+    """After the first update the residual is formed as E - A (X_new - X_old)
+    from 7 digit groups of the change; it must agree with a fresh 9-digit
+    residual of the same result and with FP64 numpy."""
+    n = 2048
+    A = inputs.gaussian_shifted(n, 95, sigma=1.5)
+    st, info, X = refine(bi, A, [256] * 8, mode)
+    assert st == bi.OK and info.incremental_residuals >= 1 and info.used_fallback == 0
+    _, rho_fresh = tc_residual(bi, A, X)
+    r = np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X))
+    assert r <= 1e-12
+    assert abs(info.rho - rho_fresh) <= 2e-14 + 0.05 * rho_fresh, (info.rho, rho_fresh, r)
+    assert abs(info.rho - r) <= 2e-14 + 0.05 * r, (info.rho, r)
