@@ -281,7 +281,7 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float*
     km.pa[2] = 1; km.pb[2] = 0;
   }
   EpiSchurF32 epi{X, ldx, n, o, b, status};
-  return tc::launch_gemm<K>(tU, tV, n, n, km, epi, status, s);
+  return tc::launch_gemm<K, EpiSchurF32, true>(tU, tV, n, n, km, epi, status, s);
 }
 
 }  // namespace
@@ -307,7 +307,10 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   const uint32_t BK = 128 / eb;
   const uint64_t w = (uint64_t)nsl * kpad;
   CUtensorMap tU, tV;
-  if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) || !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN))
+  // Vt's box is half a B tile: the two CTAs of a cluster each load one half
+  // and multicast it into both
+  if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) ||
+      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN / 2))
     return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   for (size_t k = 0; k < mp.sizes.size() && e == cudaSuccess; ++k) {
