@@ -193,13 +193,15 @@ int blockinv_batch_plan_run(blockinv_batch_plan* plan, void* stream, int32_t* st
 int blockinv_batch_plan_destroy(blockinv_batch_plan* plan);
 
 /* Batch autotuner. Matrices of order n >= 8 fall into size classes
- * c = floor(log2 n) (3 <= c <= 16). blockinv_batch_tune times, for every class
- * present in n[count], each candidate partition (p near-equal blocks, every
- * block of order 4..128) and Schur-update tile (64 x 64 or 32 x 32) on
- * synthetic diagonally dominant matrices of that class's orders (up to 512
- * of them; device memory allocated and freed inside; best of `reps` graph
- * replays after one warm-up, 1 <= reps <= 100), and keeps the fastest in a
- * process-wide table. Plans and blockinv_invert_batched calls made without
+ * c = floor(log2 n) (3 <= c <= 16). blockinv_batch_tune builds a synthetic
+ * diagonally dominant batch with the orders n[count] (about 4096 of them at
+ * most; device memory allocated and freed inside) and, class by class in
+ * order of total work, times each candidate partition (p near-equal blocks,
+ * every block of order 4..128) and Schur-update tile (64 x 64 or 32 x 32) on
+ * the whole batch with the other classes at their current choice (best of
+ * `reps` graph replays after one warm-up, 1 <= reps <= 100); the fastest,
+ * or the class's current choice if none beats it, goes into a process-wide
+ * table. Plans and blockinv_invert_batched calls made without
  * explicit partitions then use the table (explicit partitions keep their
  * blocks and take the class's tile). Blocking. Not part of the paper's
  * method: it chooses among partitions the method allows.

@@ -12,12 +12,13 @@
 // Pivot blocks of order <= 128 use the grouped one-CTA kernel; larger ones
 // (rare in a batch) use the per-matrix cluster kernel, inside the same graph.
 //
-// Autotuner. Matrices fall into size classes c = floor(log2 n) (n >= 8). For
-// each class present in a batch, the tuner times every candidate (number of
-// near-equal blocks p, Schur tile 64 or 32) on synthetic diagonally dominant
-// matrices of that class's orders, and keeps the fastest in a process-wide
-// table (which can be saved to and loaded from a text file). Plans built
-// without explicit partitions use the table.
+// Autotuner. Matrices fall into size classes c = floor(log2 n) (n >= 8). The
+// tuner builds a synthetic diagonally dominant batch with the caller's orders
+// and, class by class (largest total work first), times every candidate
+// (number of near-equal blocks p, Schur tile 64 or 32) on the whole batch
+// with the other classes at their current choice, keeping the fastest (or the
+// current one) in a process-wide table, which can be saved to and loaded
+// from a text file. Plans built without explicit partitions use the table.
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -119,7 +120,7 @@ void batch_partition(int n, std::vector<int>* out, int* tile) {
 }
 
 int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
-                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile) {
+                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile, const int* tiles) {
   *out = nullptr;
   if (count < 1 || !n || !A || !lda || (block_sizes && !p)) return BLOCKINV_ERR_INVALID;
   BatchPlan tmp;
@@ -139,6 +140,7 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
       batch_partition(n[m], &part, &tile);
     }
     if (force_tile) tile = force_tile;
+    if (tiles) tile = tiles[m];
     int64_t sum = 0;
     for (int b : part) {
       if (b < 1 || b > BLOCKINV_MAX_BLOCK) return BLOCKINV_ERR_INVALID;
@@ -306,21 +308,73 @@ void batch_plan_destroy(BatchPlan* pl) {
 
 namespace {
 
-// Time one candidate (p blocks, Schur tile) on the synthetic matrices of one
-// class: graph replay, best of `reps` after one warm-up; the matrices are
-// refilled before every run (an inverse is not inverted again).
-int time_candidate(const std::vector<int32_t>& ns, double* const* hA, double* const* dA, const int32_t* dn,
-                   int p, int tile, int reps, cudaStream_t s, float* best_ms) {
-  const int count = (int)ns.size();
-  std::vector<int32_t> pp(count, p), sizes;
-  std::vector<int64_t> lda(ns.begin(), ns.end());
-  std::vector<int> part;
-  for (int m = 0; m < count; ++m) {
-    equal_partition(ns[m], p, &part);
-    sizes.insert(sizes.end(), part.begin(), part.end());
+// Synthetic batch for the tuner: matrices of the given orders (diagonally
+// dominant, refilled before every timed run, since a run overwrites them).
+struct TuneBatch {
+  std::vector<int32_t> n;
+  std::vector<double*> hA;
+  std::vector<int64_t> lda;
+  void* buf = nullptr;
+  double* const* dA = nullptr;
+  const int32_t* dn = nullptr;
+  ~TuneBatch() {
+    if (buf) cudaFree(buf);
   }
+  int make(const std::vector<int32_t>& orders) {
+    n = orders;
+    size_t total = 0;
+    std::vector<size_t> off(n.size());
+    for (size_t m = 0; m < n.size(); ++m) {
+      off[m] = total;
+      total += align256(sizeof(double) * (size_t)n[m] * n[m]);
+    }
+    const size_t o_ptr = total, o_n = o_ptr + align256(sizeof(double*) * n.size());
+    if (cudaMalloc(&buf, o_n + sizeof(int32_t) * n.size()) != cudaSuccess) {
+      buf = nullptr;
+      return BLOCKINV_ERR_NOMEM;
+    }
+    char* base = static_cast<char*>(buf);
+    hA.resize(n.size());
+    lda.assign(n.begin(), n.end());
+    for (size_t m = 0; m < n.size(); ++m) hA[m] = reinterpret_cast<double*>(base + off[m]);
+    cudaError_t e = cudaMemcpy(base + o_ptr, hA.data(), sizeof(double*) * n.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_n, n.data(), sizeof(int32_t) * n.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
+    dA = reinterpret_cast<double* const*>(base + o_ptr);
+    dn = reinterpret_cast<const int32_t*>(base + o_n);
+    return BLOCKINV_OK;
+  }
+};
+
+// Partition and tile of every matrix of the batch under a candidate table.
+void table_partitions(const std::vector<int32_t>& ns, const Tuned* table, std::vector<int32_t>* p,
+                      std::vector<int32_t>* sizes, std::vector<int>* tiles) {
+  p->clear();
+  sizes->clear();
+  tiles->clear();
+  std::vector<int> part;
+  for (int32_t nn : ns) {
+    const int c = size_class(nn);
+    const Tuned t = (c >= kMinClass && c <= kMaxClass) ? table[c] : Tuned();
+    if (t.p > 0 && t.p <= nn && (nn + t.p - 1) / t.p <= BLOCKINV_MAX_BLOCK)
+      equal_partition(nn, t.p, &part);
+    else
+      batch_default_partition(nn, &part);
+    p->push_back((int32_t)part.size());
+    sizes->insert(sizes->end(), part.begin(), part.end());
+    tiles->push_back(t.tile);
+  }
+}
+
+// Best of `reps` graph replays (after one warm-up) of the whole batch under
+// a candidate table.
+int time_table(TuneBatch& tb, const Tuned* table, int reps, cudaStream_t s, float* best_ms) {
+  std::vector<int32_t> p, sizes;
+  std::vector<int> tiles;
+  table_partitions(tb.n, table, &p, &sizes, &tiles);
   BatchPlan* pl = nullptr;
-  const int st = batch_plan_create(count, ns.data(), pp.data(), sizes.data(), hA, lda.data(), &pl, tile);
+  const int st = batch_plan_create((int32_t)tb.n.size(), tb.n.data(), p.data(), sizes.data(), tb.hA.data(),
+                                   tb.lda.data(), &pl, 0, tiles.data());
   if (st != BLOCKINV_OK) return st;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -328,7 +382,7 @@ int time_candidate(const std::vector<int32_t>& ns, double* const* hA, double* co
   cudaError_t e = cudaSuccess;
   *best_ms = 1e30f;
   for (int r = -1; r < reps && e == cudaSuccess; ++r) {
-    fill_tune_kernel<<<count, 256, 0, s>>>(dA, dn);
+    fill_tune_kernel<<<(unsigned)tb.n.size(), 256, 0, s>>>(tb.dA, tb.dn);
     e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) e = batch_run(*pl, s, nullptr, true);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
@@ -344,66 +398,63 @@ int time_candidate(const std::vector<int32_t>& ns, double* const* hA, double* co
 
 }  // namespace
 
+// Coordinate descent over the size classes of this batch, largest total
+// work first: each class's candidates are timed on the whole batch (classes
+// share every grouped launch, so a class is only as good as the batch it
+// runs in), with the other classes at their current choice.
 int batch_tune(int32_t count, const int32_t* n, int reps, cudaStream_t s) {
   if (count < 1 || !n || reps < 1 || reps > 100) return BLOCKINV_ERR_INVALID;
-  std::map<int, std::vector<int32_t>> classes;
+  std::vector<int32_t> orders;
+  const int stride = std::max(1, count / 4096);  // at most about 4096 matrices are timed
   for (int m = 0; m < count; ++m) {
     if (n[m] < 1 || n[m] > (1 << 16)) return BLOCKINV_ERR_INVALID;
-    const int c = size_class(n[m]);
-    if (c >= kMinClass && c <= kMaxClass && classes[c].size() < 512) classes[c].push_back(n[m]);
+    if (m % stride == 0) orders.push_back(n[m]);
   }
-  for (auto& kv : classes) {
-    const int c = kv.first;
-    const std::vector<int32_t>& ns = kv.second;
-    const int nmin = *std::min_element(ns.begin(), ns.end());
-    const int nmax = *std::max_element(ns.begin(), ns.end());
-    // synthetic matrices of the class's orders
-    size_t total = 0;
-    std::vector<size_t> off(ns.size());
-    for (size_t m = 0; m < ns.size(); ++m) {
-      off[m] = total;
-      total += align256(sizeof(double) * (size_t)ns[m] * ns[m]);
-    }
-    const size_t o_ptr = total, o_n = o_ptr + align256(sizeof(double*) * ns.size());
-    void* buf = nullptr;
-    if (cudaMalloc(&buf, o_n + sizeof(int32_t) * ns.size()) != cudaSuccess) return BLOCKINV_ERR_NOMEM;
-    char* base = static_cast<char*>(buf);
-    std::vector<double*> hA(ns.size());
-    for (size_t m = 0; m < ns.size(); ++m) hA[m] = reinterpret_cast<double*>(base + off[m]);
-    cudaError_t e = cudaMemcpy(base + o_ptr, hA.data(), sizeof(double*) * ns.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(base + o_n, ns.data(), sizeof(int32_t) * ns.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      cudaFree(buf);
-      return BLOCKINV_ERR_CUDA;
-    }
-    double* const* dA = reinterpret_cast<double* const*>(base + o_ptr);
-    const int32_t* dn = reinterpret_cast<const int32_t*>(base + o_n);
-    // candidates: p near-equal blocks (every block of every order in 4..128,
-    // the grouped pivot kernel's range), Schur tiles 64 and 32
-    Tuned best;
+  std::map<int, double> work;  // class -> sum of n^3
+  std::map<int, std::pair<int, int>> range;
+  for (int32_t nn : orders) {
+    const int c = size_class(nn);
+    if (c < kMinClass || c > kMaxClass) continue;
+    work[c] += (double)nn * nn * nn;
+    auto it = range.find(c);
+    if (it == range.end()) range[c] = {nn, nn};
+    else it->second = {std::min(it->second.first, (int)nn), std::max(it->second.second, (int)nn)};
+  }
+  std::vector<int> classes;
+  for (auto& kv : work) classes.push_back(kv.first);
+  std::sort(classes.begin(), classes.end(), [&](int a, int b) { return work[a] > work[b]; });
+  TuneBatch tb;
+  int st = tb.make(orders);
+  if (st != BLOCKINV_OK) return st;
+  Tuned table[kMaxClass + 1];
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (int c = 0; c <= kMaxClass; ++c) table[c] = g_tune[c];
+  }
+  for (int c : classes) {
+    const int nmin = range[c].first, nmax = range[c].second;
+    Tuned best = table[c];
     float best_ms = 1e30f;
-    int st = BLOCKINV_OK;
+    st = time_table(tb, table, reps, s, &best_ms);  // the current choice
+    if (st != BLOCKINV_OK) return st;
     for (int p : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
-      if (p > nmin || (nmax + p - 1) / p > kGroupedMaxB || nmin / p < 4) continue;
+      if (p > nmin || (nmax + p - 1) / p > kGroupedMaxB || (p > 1 && nmin / p < 4)) continue;
       for (int tile : {64, 32}) {
+        table[c].p = p;
+        table[c].tile = tile;
         float ms = 0.f;
-        st = time_candidate(ns, hA.data(), dA, dn, p, tile, reps, s, &ms);
-        if (st != BLOCKINV_OK) break;
+        st = time_table(tb, table, reps, s, &ms);
+        if (st != BLOCKINV_OK) return st;
         if (ms < best_ms) {
           best_ms = ms;
-          best.p = p;
-          best.tile = tile;
+          best = table[c];
         }
       }
-      if (st != BLOCKINV_OK) break;
     }
-    cudaFree(buf);
-    if (st != BLOCKINV_OK) return st;
-    if (best.p > 0) {
-      std::lock_guard<std::mutex> g(g_tune_mu);
-      g_tune[c] = best;
-    }
+    table[c] = best;
   }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (int c : classes) g_tune[c] = table[c];
   return BLOCKINV_OK;
 }
 

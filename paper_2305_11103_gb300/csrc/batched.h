@@ -39,9 +39,11 @@ struct BatchPlan {
 // 64 x 64 tiles.
 void batch_partition(int n, std::vector<int>* out, int* tile);
 void batch_default_partition(int n, std::vector<int>* out);
-// force_tile: 0 = the tile of each matrix's size class (tuned, else 64).
+// force_tile: 0 = the tile of each matrix's size class (tuned, else 64);
+// tiles (optional): one tile per matrix, overriding both.
 int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
-                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile = 0);
+                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile = 0,
+                      const int* tiles = nullptr);
 // Autotuner: time the candidate partitions and Schur tiles of every size
 // class present in n[] and keep the fastest in the process-wide table.
 int batch_tune(int32_t count, const int32_t* n, int reps, cudaStream_t s);

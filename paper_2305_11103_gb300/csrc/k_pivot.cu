@@ -277,11 +277,12 @@ pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restr
 // Grouped form: one CTA per matrix of a batch, block order <= kGroupedMaxB,
 // every row of the pivot block in the CTA's shared memory.
 __global__ void __launch_bounds__(kPivotThreads)
-pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count) {
+pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count, int bmin) {
   const int m = blockIdx.x;
   if (m >= count) return;
   const GroupStep it = items[m];
   if (it.b > kGroupedMaxB) return;  // handled by the cluster kernel
+  if (it.b <= bmin) return;         // handled by the warp kernel
   int jw = 1, jlog = 0;
   while (jw < it.b && jw < kPivotThreads) {
     jw <<= 1;
@@ -289,6 +290,81 @@ pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count) {
   }
   pivot_gj_body<double, double, false>(it.X + (int64_t)it.o * it.ldx + it.o, it.ldx, it.b, it.b, jlog, it.Pinv,
                                        it.b, it.status, it.k);
+}
+
+// Grouped warp form for pivot blocks of order <= 32: one warp per matrix, a
+// row per lane in registers, Gauss-Jordan with partial pivoting (largest |x|
+// compared on its bit pattern, lowest row on ties), the pivot row broadcast
+// by shuffles: no barriers at all. Rows are not swapped; the result is
+// unscrambled on output (inverse[c][perm[j]] = row of pivot c, entry j).
+constexpr int kWarpPivotMax = 32;
+__global__ void __launch_bounds__(128)
+pivot_warp_grouped_kernel(const GroupStep* __restrict__ items, int count) {
+  const int m = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= count) return;  // warp-uniform from here on
+  const GroupStep it = items[m];
+  if (it.b > kWarpPivotMax || *(volatile const int32_t*)it.status != 0) return;
+  const int b = it.b;
+  const double* P = it.X + (int64_t)it.o * it.ldx + it.o;
+  double x[kWarpPivotMax];
+  bool bad = false;
+#pragma unroll
+  for (int l = 0; l < kWarpPivotMax; ++l) {
+    x[l] = (lane < b && l < b) ? P[(int64_t)lane * it.ldx + l] : 0.0;
+    bad |= !isfinite(x[l]);
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) set_status(it.status, BLOCKINV_ERR_NONFINITE, it.k);
+    return;
+  }
+  bool used = false;
+  int my_col = -1;
+  int perm[kWarpPivotMax];
+#pragma unroll
+  for (int c = 0; c < kWarpPivotMax; ++c) {
+    perm[c] = 0;
+    if (c < b) {
+      const bool cand = lane < b && !used;
+      unsigned long long key = cand ? static_cast<unsigned long long>(__double_as_longlong(fabs(x[c]))) : 0ull;
+      int idx = cand ? lane : kWarpPivotMax;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        if (ok > key || (ok == key && oi < idx)) {
+          key = ok;
+          idx = oi;
+        }
+      }
+      const int pr = idx < kWarpPivotMax ? idx : 0;
+      const double pc = __shfl_sync(0xffffffffu, x[c], pr);
+      if (idx >= kWarpPivotMax || pc == 0.0 || !isfinite(pc)) {
+        if (lane == 0)
+          set_status(it.status, (idx < kWarpPivotMax && pc != 0.0) ? BLOCKINV_ERR_NONFINITE : BLOCKINV_ERR_SINGULAR,
+                     it.k);
+        return;
+      }
+      perm[c] = pr;
+      const double inv = 1.0 / pc;
+      const bool is_pivot = lane == pr;
+      const double alpha = is_pivot ? inv : -x[c] * inv;
+#pragma unroll
+      for (int l = 0; l < kWarpPivotMax; ++l) {
+        const double pl = __shfl_sync(0xffffffffu, x[l], pr);
+        if (l < b) x[l] = (l == c) ? alpha : fma(alpha, pl, is_pivot ? 0.0 : x[l]);
+      }
+      if (is_pivot) {
+        used = true;
+        my_col = c;
+      }
+    }
+  }
+  if (lane < b) {
+#pragma unroll
+    for (int j = 0; j < kWarpPivotMax; ++j)
+      if (j < b) it.Pinv[(int64_t)my_col * b + perm[j]] = x[j];
+  }
 }
 
 // ------------------------------------------------------------------------
@@ -845,10 +921,13 @@ cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cu
   if (count <= 0) return cudaSuccess;
   if (bmax > kGroupedMaxB) return cudaErrorInvalidValue;
   const size_t smem = pivot_smem_bytes(bmax, bmax, sizeof(double));
-  cudaError_t e = cudaFuncSetAttribute(pivot_gj_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  // blocks of order <= 32: one warp each; larger ones: one CTA each
+  pivot_warp_grouped_kernel<<<(count + 3) / 4, 128, 0, s>>>(items, count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || bmax <= kWarpPivotMax) return e;
+  e = cudaFuncSetAttribute(pivot_gj_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  pivot_gj_grouped_kernel<<<count, kPivotThreads, smem, s>>>(items, count);
+  pivot_gj_grouped_kernel<<<count, kPivotThreads, smem, s>>>(items, count, kWarpPivotMax);
   return cudaGetLastError();
 }
 

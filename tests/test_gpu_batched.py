@@ -232,8 +232,8 @@ def test_autotuner_choices_are_valid_and_exact(bi):
         for c in sorted({_size_class(n) for n in ns}):
             st, p, tile = bi.blockinv_batch_tuning(c)
             members = [n for n in ns if _size_class(n) == c]
-            assert st == bi.OK and tile in (32, 64) and 1 <= p <= min(members)
-            assert -(-max(members) // p) <= 128 and min(members) // p >= 4 or p == 1
+            assert st == bi.OK and tile in (32, 64) and 0 <= p <= min(members)   # 0: the default stays
+            assert p == 0 or p == 1 or (-(-max(members) // p) <= 128 and min(members) // p >= 4)
         ts, ptrs, _ = device_batch(mats)
         st = torch.full((300,), 7, dtype=torch.int32, device="cuda")
         plan = bi.BatchPlan(ns, None, ptrs, ns)
@@ -244,6 +244,9 @@ def test_autotuner_choices_are_valid_and_exact(bi):
         parts = []
         for n in ns:
             p = bi.blockinv_batch_tuning(_size_class(n))[1]
+            if p == 0:
+                parts.append(quarter(n))
+                continue
             q, r = divmod(n, p)
             parts.append([q + (1 if i >= p - r else 0) for i in range(p)])
         _check_batch(mats, ts, parts, sample=inputs.rng(67).choice(300, size=40, replace=False))
