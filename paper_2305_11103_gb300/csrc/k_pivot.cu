@@ -25,7 +25,8 @@
 // column whose candidates are all exactly zero gives BLOCKINV_ERR_SINGULAR;
 // the first error is kept in the device status word with the block index.
 // The pivot row is scaled by multiplying with the correctly rounded
-// reciprocal of the pivot (within an ulp of dividing; exact for unit pivots).
+// reciprocal of the pivot (within an ulp of dividing; exact for unit pivots);
+// the FP32 panel kernel of the mixed path uses a Newton-refined estimate.
 #include <climits>
 #include <mutex>
 #include <cooperative_groups.h>
@@ -65,6 +66,15 @@ __device__ __forceinline__ void set_status(int32_t* status, int code, int block)
 // Correctly rounded reciprocal; a column is scaled by multiplying with it (a
 // full IEEE division per element is a long instruction sequence).
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+
+// The FP32 panel kernel's reciprocal (on the critical path of every column;
+// its result is refined later in the mixed path): the hardware estimate and
+// one Newton-Raphson step r <- r (2 - v r), within about an ulp.
+__device__ __forceinline__ float recip_newton(float v) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r * fmaf(-v, r, 2.0f);
+}
 __device__ __forceinline__ double recip(double v) { return __drcp_rn(v); }
 
 template <typename T>
@@ -540,7 +550,7 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
                 pr[4 * q + 2] = v.z;
                 pr[4 * q + 3] = v.w;
               }
-              const float inv = recip(pr[cc]);
+              const float inv = recip_newton(pr[cc]);
               // pivot row: P[p][l] * inv (l != c), inv at l = c; every other
               // row: x[l] - (x[c] inv) P[p][l] (l != c), -x[c] inv at l = c
               if (r0 == p) {
