@@ -312,6 +312,10 @@ typedef struct {
                        /* from a saved copy of A with the other pivot order, then with  */
                        /* the failing block merged into a neighbour (up to order 512),  */
                        /* repeatedly; 0 (default) = return BLOCKINV_ERR_SINGULAR        */
+  int32_t lookahead;   /* 0 (default) = for n >= 2048 and 3 or more blocks, start the next */
+                       /* pivot inverse (FP64: and row panel) on a high-priority stream  */
+                       /* of the library's while the rest of the current Schur update    */
+                       /* runs; -1 = one step at a time. The result bits are the same.   */
 } blockinv_options;
 
 typedef struct {

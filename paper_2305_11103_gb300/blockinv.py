@@ -76,7 +76,7 @@ SIGNATURES = {
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("fallback", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("pivot_f64", ctypes.c_int32), ("pivot_order", ctypes.c_int32),
-                ("singular_fallback", ctypes.c_int32)]
+                ("singular_fallback", ctypes.c_int32), ("lookahead", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -147,11 +147,11 @@ def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_p
 
 
 def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1,
-                       split=0, pivot_f64=0, pivot_order=0, singular_fallback=0):
+                       split=0, pivot_f64=0, pivot_order=0, singular_fallback=0, lookahead=0):
     """Returns (status, Info)."""
     p, arr, _ = _sizes(block_sizes)
     opt = Options(tol=tol, max_refine=max_refine, fallback=fallback, split=split, pivot_f64=pivot_f64,
-                  pivot_order=pivot_order, singular_fallback=singular_fallback)
+                  pivot_order=pivot_order, singular_fallback=singular_fallback, lookahead=lookahead)
     info = Info()
     st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
                                   ctypes.byref(info))

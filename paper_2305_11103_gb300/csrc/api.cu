@@ -211,12 +211,12 @@ struct EventPair {
 // between steps is A alone, so a range picks up where the previous one
 // stopped, and splitting the steps over several calls gives the same bits.
 int enqueue_f64(const Plan& pl, double* A, int64_t lda, int32_t* status, cudaStream_t s, int k0 = 0,
-                int k1 = -1) {
+                int k1 = -1, bool lookahead = true) {
   const int n = pl.n;
   if (k1 < 0) k1 = (int)pl.sizes.size();
   const int p = k1;
   if (k0 >= k1) return BLOCKINV_OK;
-  cudaStream_t t = (n >= 2048 && k1 - k0 >= 3) ? side_stream() : nullptr;
+  cudaStream_t t = (lookahead && n >= 2048 && k1 - k0 >= 3) ? side_stream() : nullptr;
   const bool ahead = t != nullptr;
   AsyncBuf pinv, ubuf;
   cudaError_t e = pinv.alloc(sizeof(double) * (size_t)pl.bmax * pl.bmax, s);
@@ -286,6 +286,7 @@ struct Options {
   int pivot_f64 = 0;  // 0: FP64 re-inversion of ill-conditioned pivot blocks; 1: of all; -1: none
   bool reverse = false;           // pivot blocks last to first (Eq. (d))
   bool singular_fallback = false;  // FP64: retry singular pivots with another order / merged blocks
+  bool lookahead = true;           // one-step look-ahead on a side stream (n >= 2048, 3 or more blocks)
 };
 
 // Pivot blocks whose estimate ||P||_inf ||P^-1||_inf exceeds this are inverted
@@ -307,6 +308,7 @@ Options resolve(const blockinv_options* o) {
     r.pivot_f64 = o->pivot_f64 > 0 ? 1 : (o->pivot_f64 < 0 ? -1 : 0);
     r.reverse = o->pivot_order == 1;
     r.singular_fallback = o->singular_fallback != 0;
+    r.lookahead = o->lookahead >= 0;
   }
   return r;
 }
@@ -342,7 +344,7 @@ int spatial_block(const Plan& pl, int k) {
 // Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
 // of the low-precision inverse).
 int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int nsl, float cond_limit,
-                       int32_t* piv_words, int32_t* status, cudaStream_t s) {
+                       int32_t* piv_words, int32_t* status, cudaStream_t s, bool lookahead) {
   const int n = pl.n;
   const int64_t ld32 = (n + 31) / 32 * 32;
   const int kpad = mixed_kpad(pl.bmax);
@@ -360,7 +362,7 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int ns
   }
   if (e == cudaSuccess)
     e = mixed_elimination(pl, bf16, nsl, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, cond_limit,
-                          piv_words, status, s);
+                          piv_words, status, s, lookahead && n >= 2048);
   if (e == cudaSuccess) {
     TraceScope t("cast_f32_to_f64", 0, 12.0 * n * (double)n, s);
     e = launch_cast_f32_to_f64(X32, ld32, A, lda, n, s);
@@ -393,7 +395,7 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
     e = cudaMemcpy2DAsync(ms.a0.ptr, row, A, sizeof(double) * lda, row, n, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, pivot_cond_limit(opt), static_cast<int32_t*>(ms.piv.ptr),
-                              status, s);
+                              status, s, opt.lookahead);
   if (st != BLOCKINV_OK || opt.max_refine == 0) return st;
   e = ms.ws.alloc(refine_workspace_bytes(n, kResidualSlices, opt.max_refine), s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -407,7 +409,7 @@ int enqueue(const Plan& pl, double* A, int64_t lda, int mode, int32_t* status, c
             const Options& opt, MixedState* ms) {
   switch (mode) {
     case BLOCKINV_F64:
-      return enqueue_f64(pl, A, lda, status, s);
+      return enqueue_f64(pl, A, lda, status, s, 0, -1, opt.lookahead);
     case BLOCKINV_MIXED_TF32:
     case BLOCKINV_MIXED_BF16: {
       MixedState local;
@@ -612,7 +614,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
     e = cudaMemcpy2DAsync(A, sizeof(double) * lda, ms.a0.ptr, row, row, n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
     if (e != cudaSuccess) return record(cuda_status(e), -1);
-    st = enqueue_f64(pl, A, lda, status, s);
+    st = enqueue_f64(pl, A, lda, status, s, 0, -1, opt.lookahead);
     if (st == BLOCKINV_OK) st = finish(status, s);
     fb = g_last_block;
     if (info) info->used_fallback = 1;
@@ -626,7 +628,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
                                        cudaMemcpyDeviceToDevice, s);
     if (e2 == cudaSuccess) e2 = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
     if (e2 != cudaSuccess) return cuda_status(e2);
-    int r = enqueue_f64(q, A, lda, status, s);
+    int r = enqueue_f64(q, A, lda, status, s, 0, -1, opt.lookahead);
     if (r == BLOCKINV_OK) r = finish(status, s);
     return r;
   };

@@ -87,6 +87,11 @@ cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* 
                                      int block_index, float cond_limit, int32_t* gate, int32_t* count,
                                      cudaStream_t s);
 
+// CTAs (hence SMs) the widest launch of one pivot inverse of order b takes:
+// launch_pivot_inverse with elements of elem bytes, and with f64_check also
+// launch_pivot_f64_for_ill.
+int pivot_inverse_ctas(int b, int elem, bool f64_check);
+
 // K2 (FP64): row panel X[o:o+b, j] <- Pinv X[o:o+b, j] for j outside the
 // pivot columns, X[o:o+b, o:o+b] <- Pinv, and U <- X[:, o:o+b] for rows
 // outside the pivot rows (U is n x b, leading dimension b).
@@ -119,8 +124,12 @@ int mixed_kpad(int bmax);
 // pivot_cond_limit: > 0, pivot blocks whose condition estimate exceeds it are
 // inverted again in FP64 arithmetic (launch_pivot_f64_for_ill); < 0, every
 // block; 0, none. piv_words: device int32[2] (gate, count of FP64 pivots).
+// lookahead: with 3 or more blocks, each next pivot inverse runs beside the
+// rest of the current Schur update (same stream, programmatic dependent
+// launch); the result bits are the same.
 cudaError_t mixed_elimination(const Plan& pl, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
-                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s);
+                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s,
+                              bool lookahead);
 
 // Batched small matrices, order 1..8, one thread per matrix (k_small.cu).
 cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* status, cudaStream_t s);

@@ -213,29 +213,38 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
 }
 
 // ---------------------------------------------------- Schur epilogue ------
+// Elements written: every row outside the pivot rows [o, o + b); with
+// part = kInside only those of the square [r0, r1) x [r0, r1) (the next
+// pivot block), with part = kOutside all but those.
+enum SchurPart { kWhole = 0, kInside = 1, kOutside = 2 };
+
 struct EpiSchurF32 {
   float* X;
   int64_t ldx;
   int n, o, b;
   const int32_t* status;
+  int part = kWhole;
+  int r0 = 0, r1 = 0;
   __device__ bool skip() const { return failed(status); }
+  __device__ bool writes(int row, bool col_in) const {
+    if (row >= n || (row >= o && row < o + b)) return false;
+    if (part == kWhole) return true;
+    const bool in = col_in && row >= r0 && row < r1;
+    return part == kInside ? in : !in;
+  }
   __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
     const bool pivot_col = col >= o && col < o + b;
+    const bool col_in = col >= r0 && col < r1;
+    if (part == kInside && !col_in) return;
     float* p = X + (int64_t)row0 * ldx + col;
     // all loads before any store, so the 32 reads are in flight together
     float cur[32];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int row = row0 + r;
-      const bool live = row < n && (row < o || row >= o + b);
-      cur[r] = (live && !pivot_col) ? p[(int64_t)r * ldx] : 0.f;
-    }
+    for (int r = 0; r < 32; ++r) cur[r] = (writes(row0 + r, col_in) && !pivot_col) ? p[(int64_t)r * ldx] : 0.f;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int row = row0 + r;
-      if (row < n && (row < o || row >= o + b)) p[(int64_t)r * ldx] = cur[r] - v[r];
-    }
+    for (int r = 0; r < 32; ++r)
+      if (writes(row0 + r, col_in)) p[(int64_t)r * ldx] = cur[r] - v[r];
   }
 };
 
@@ -266,9 +275,14 @@ cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const f
   return cudaErrorInvalidValue;
 }
 
+// The Schur update of step (o, b): the whole of it (part = kWhole), or the
+// square [o1, o1 + b1)^2 of the next pivot block (kInside: only the tiles
+// that cover it), or everything else (kOutside, on at most max_ctas CTAs,
+// with after_trigger as the programmatic dependent of the kernel before it).
 template <tc::Kind K>
 cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float* X, int64_t ldx, int n, int o,
-                            int b, int kpad, int nsl, int32_t* status, cudaStream_t s) {
+                            int b, int kpad, int nsl, int32_t* status, cudaStream_t s, int part = kWhole,
+                            int o1 = 0, int b1 = 0, int max_ctas = 0, bool after_trigger = false) {
   constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
   const int kb = (b + BK - 1) / BK;
   tc::KMap km = tc::plain_kmap(kb);
@@ -280,8 +294,20 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float*
     km.pa[1] = 0; km.pb[1] = 1;
     km.pa[2] = 1; km.pb[2] = 0;
   }
-  EpiSchurF32 epi{X, ldx, n, o, b, status};
-  return tc::launch_gemm<K, EpiSchurF32, true>(tU, tV, n, n, km, epi, status, s);
+  EpiSchurF32 epi{X, ldx, n, o, b, status, part, o1, o1 + b1};
+  tc::Window win;
+  int M = n, N = n;
+  if (part == kInside) {
+    constexpr int unit_m = 2 * tc::kBM;  // a row unit of the cluster-of-two GEMM
+    win.m_base = o1 / unit_m * unit_m;
+    win.n_base = o1 / tc::kBN * tc::kBN;
+    M = o1 + b1 - win.m_base;
+    N = o1 + b1 - win.n_base;
+  } else if (part == kOutside) {
+    win.max_ctas = max_ctas;
+    win.after_trigger = after_trigger;
+  }
+  return tc::launch_gemm<K, EpiSchurF32, true>(tU, tV, M, N, km, epi, status, s, win);
 }
 
 }  // namespace
@@ -299,8 +325,10 @@ cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64
 int mixed_kpad(int bmax) { return (bmax + 63) / 64 * 64; }
 
 cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
-                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s) {
+                              void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s,
+                              bool lookahead) {
   const int n = mp.n;
+  const int p = (int)mp.sizes.size();
   const int kpad = mixed_kpad(mp.bmax);
   const int eb = bf16 ? 2 : 4;
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -312,33 +340,64 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) ||
       !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN / 2))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  for (size_t k = 0; k < mp.sizes.size() && e == cudaSuccess; ++k) {
+  const bool check = pivot_cond_limit != 0.f && piv_words;
+  auto pivot = [&](int k) -> cudaError_t {
+    const int o = mp.offs[k], b = mp.sizes[k];
+    const double bd = b;
+    TraceScope t("pivot_inverse_f32", 2.0 * bd * bd * bd, 8.0 * bd * bd, s);
+    return launch_pivot_inverse<float>(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, s);
+  };
+  auto pivot_check = [&](int k) -> cudaError_t {
+    if (!check) return cudaSuccess;
+    // FP64 arithmetic for the pivot blocks that the condition estimate flags
+    const int o = mp.offs[k], b = mp.sizes[k];
+    const double bd = b;
+    TraceScope t("pivot_f64_if_ill", 0, 8.0 * bd * bd, s);
+    return launch_pivot_f64_for_ill(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, pivot_cond_limit,
+                                    piv_words, piv_words + 1, s);
+  };
+  auto schur = [&](int k, int part, int k1, int max_ctas, bool after_trigger) -> cudaError_t {
+    const int o = mp.offs[k], b = mp.sizes[k];
+    const int o1 = k1 >= 0 ? mp.offs[k1] : 0, b1 = k1 >= 0 ? mp.sizes[k1] : 0;
+    const double bd = b, nd = n, rest = n - b;
+    const double inside = (double)b1 * b1, elems = part == kWhole ? rest * nd
+                                                   : part == kInside ? inside : rest * nd - inside;
+    TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * elems * (nsl > 1 ? 3 : 1),
+                 4.0 * 2.0 * elems + eb * 2.0 * nd * bd * nsl, s);
+    return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
+                                                  max_ctas, after_trigger)
+                : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
+                                                  max_ctas, after_trigger);
+  };
+  // One-step look-ahead: step k's Schur update is split into the next pivot
+  // block's square and the rest. The next FP32 pivot inverse follows the
+  // square and starts its programmatic dependent, the rest of the update, at
+  // once: the two share the GPU (the update on as many fewer SMs as the pivot
+  // kernel takes) and touch disjoint data (the pivot reads the square and
+  // writes Pinv, the update leaves both alone). The condition check of the
+  // pivot and the next row panel (which overwrites U and Vt) follow both.
+  const bool ahead = lookahead && p >= 3;
+  cudaError_t e = pivot(0);
+  if (e == cudaSuccess) e = pivot_check(0);
+  for (int k = 0; k < p && e == cudaSuccess; ++k) {
     const int o = mp.offs[k], b = mp.sizes[k];
     const double bd = b, nd = n, rest = n - b;
-    {
-      TraceScope t("pivot_inverse_f32", 2.0 * bd * bd * bd, 8.0 * bd * bd, s);
-      e = launch_pivot_inverse<float>(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, (int)k, s);
-    }
-    if (e == cudaSuccess && pivot_cond_limit != 0.f && piv_words) {
-      // FP64 arithmetic for the pivot blocks that the condition estimate flags
-      TraceScope t("pivot_f64_if_ill", 0, 8.0 * bd * bd, s);
-      e = launch_pivot_f64_for_ill(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, (int)k, pivot_cond_limit,
-                                   piv_words, piv_words + 1, s);
-    }
-    if (e != cudaSuccess) break;
     {
       TraceScope t("row_panel_mixed", 2.0 * bd * bd * rest, 4.0 * (2.0 * bd * nd + bd * bd + rest * bd) + eb * 2.0 * nd * kpad, s);
       e = bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s)
                : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
     }
     if (e != cudaSuccess || n == b) continue;
-    {
-      TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * rest * nd * (nsl > 1 ? 3 : 1),
-                     4.0 * 2.0 * rest * nd + eb * 2.0 * nd * bd * nsl, s);
-      e = bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s)
-               : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s);
+    if (!ahead || k + 1 == p) {
+      e = schur(k, kWhole, -1, 0, false);
+      if (e == cudaSuccess && k + 1 < p) e = pivot(k + 1);
+    } else {
+      e = schur(k, kInside, k + 1, 0, false);
+      if (e == cudaSuccess) e = pivot(k + 1);
+      if (e == cudaSuccess)
+        e = schur(k, kOutside, k + 1, tc::num_sms() - pivot_inverse_ctas(mp.sizes[k + 1], 4, false), true);
     }
+    if (e == cudaSuccess && k + 1 < p) e = pivot_check(k + 1);
   }
   return e;
 }

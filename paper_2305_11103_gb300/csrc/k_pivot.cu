@@ -27,6 +27,7 @@
 // The pivot row is scaled by multiplying with the correctly rounded
 // reciprocal of the pivot (within an ulp of dividing; exact for unit pivots);
 // the FP32 panel kernel of the mixed path uses a Newton-refined estimate.
+#include <algorithm>
 #include <climits>
 #include <mutex>
 #include <cooperative_groups.h>
@@ -235,6 +236,9 @@ template <typename T, typename TIO, bool kCluster>
 __global__ void __launch_bounds__(kPivotThreads)
 pivot_gj_kernel(const TIO* __restrict__ P, int64_t ldp, int b, int R, int jlog, TIO* __restrict__ out,
                 int64_t ldo, int32_t* status, int block_index, const int32_t* gate) {
+  // a kernel launched after this one as its programmatic dependent may start
+  // now (it must not touch this block or its inverse)
+  asm volatile("griddepcontrol.launch_dependents;");
   if (gate && *(volatile const int32_t*)gate == 0) return;
   pivot_gj_body<T, TIO, kCluster>(P, ldp, b, R, jlog, out, ldo, status, block_index);
 }
@@ -427,6 +431,9 @@ __global__ void __launch_bounds__(kPivotThreads, 1)
 pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __restrict__ out, int64_t ldo,
                      int32_t* status, int block_index) {
   static_assert(sizeof(T) == 4, "the blocked pivot kernel serves the FP32 mixed path");
+  // a kernel launched after this one as its programmatic dependent may start
+  // now (it must not touch this block or its inverse)
+  asm volatile("griddepcontrol.launch_dependents;");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockedSmem<T> m = blocked_layout<T>(smem_raw, b, ncl);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -925,6 +932,18 @@ cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
+}
+
+int pivot_inverse_ctas(int b, int elem, bool f64_check) {
+  int c = 1, ctas = 0, ncl = 0;
+  size_t smem = 0;
+  PivotPlan plan;
+  if (elem == 4 && b > 64 && plan_blocked(b, elem, &ctas, &ncl, &smem))
+    c = ctas;
+  else if (plan_pivot(b, elem, &plan))
+    c = plan.ctas;
+  if (f64_check && plan_pivot(b, (int)sizeof(double), &plan)) c = std::max(c, plan.ctas);
+  return c;
 }
 
 cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s) {

@@ -106,7 +106,7 @@ __device__ __forceinline__ void item_coords(int t, int units_m, int tiles_n, int
 template <Kind K, class Epi, bool kMC = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int tiles_m,
-            int tiles_n, KMap km, Epi epi, int32_t* status) {
+            int tiles_n, int m_base, int n_base, int dep_wait, KMap km, Epi epi, int32_t* status) {
   constexpr int BK = 128 / KindTraits<K>::elem_bytes;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -130,7 +130,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int nch = nch_a + (kend < km.kblocks ? 1 : 0);
   const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
   const int nitems = my_tiles * nch;
-  if (epi.skip()) return;  // an earlier kernel of this computation failed (uniform over the grid)
+  // An earlier kernel of this computation failed: the status word it wrote is
+  // the same for every CTA. Not so for a programmatic dependent, whose
+  // predecessor may still be writing it (the two CTAs of a pair could then
+  // disagree), so such a grid always runs to the end.
+  if (!dep_wait && epi.skip()) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -163,8 +167,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     for (int t = first; t < ntiles && ok; t += stride) {
       int um, tn;
       item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
-      const int m0 = (kMC ? 2 * um + rank : um) * kBM;
-      const int n0 = tn * kBN;
+      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      const int n0 = n_base + tn * kBN;
       for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
@@ -252,8 +256,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       fence_after_sync();
       int um, tn;
       item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
-      const int m0 = (kMC ? 2 * um + rank : um) * kBM;
-      const int n0 = tn * kBN;
+      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      const int n0 = n_base + tn * kBN;
       const int row0 = m0 + q * 32;
 #pragma unroll 1
       for (int c = half * (kBN / 64); c < (half + 1) * (kBN / 64); ++c) {
@@ -279,15 +283,39 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     fence_after_sync();
     tmem_dealloc(tmem, 2 * kBN);
   }
+  // Launched as the programmatic dependent of the kernel before it: this grid
+  // completes only after that one has, so the stream order after it holds.
+  if (dep_wait && threadIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 int num_sms();
+
+// A window of the output: the tiles of rows m_base .. m_base + M - 1 and
+// columns n_base .. n_base + N - 1 (m_base a multiple of kBM, or of 2 kBM
+// with kMC; n_base a multiple of kBN), on at most max_ctas CTAs (0 = one per
+// SM). The tiles are those of the whole product, so every output element is
+// the same sum whichever window computes it.
+//
+// after_trigger: launch as the programmatic dependent of the previous kernel
+// in the stream, which lets this grid start once every CTA of that kernel has
+// executed griddepcontrol.launch_dependents (so both run at once on disjoint
+// SMs). The caller guarantees that the two touch disjoint data; this grid
+// still completes only after the previous one.
+struct Window {
+  int m_base = 0;
+  int n_base = 0;
+  int max_ctas = 0;
+  bool after_trigger = false;
+};
 
 // kMC: tB must have been made with a box of kBN / 2 rows (each CTA of a
 // pair loads half of the B tile).
 template <Kind K, class Epi, bool kMC = false>
 cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int N, KMap km, const Epi& epi,
-                        int32_t* status, cudaStream_t s) {
+                        int32_t* status, cudaStream_t s, const Window& win = Window{}) {
+  if (win.m_base % (kMC ? 2 * kBM : kBM) != 0 || win.n_base % kBN != 0 || win.max_ctas < 0)
+    return cudaErrorInvalidValue;
+  const int ctas = (win.max_ctas > 0 && win.max_ctas < num_sms()) ? win.max_ctas : num_sms();
   const int tiles_m = (M + kBM - 1) / kBM;
   const int tiles_n = (N + kBN - 1) / kBN;
   const int ntiles = tiles_m * tiles_n;
@@ -297,25 +325,41 @@ cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (!kMC) {
-    const int grid = ntiles < num_sms() ? ntiles : num_sms();
-    kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, km, epi, status);
-    return cudaGetLastError();
+    const int grid = ntiles < ctas ? ntiles : ctas;
+    if (!win.after_trigger) {
+      kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, 0, km, epi, status);
+      return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kGemmThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, 1, km, epi, status);
   }
   const int pairs = ((tiles_m + 1) / 2) * tiles_n;
-  const int clusters = pairs < num_sms() / 2 ? pairs : num_sms() / 2;
+  const int clusters = pairs < ctas / 2 ? pairs : (ctas / 2 > 0 ? ctas / 2 : 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * clusters, 1, 1);
   cfg.blockDim = dim3(kGemmThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, km, epi, status);
+  cfg.numAttrs = win.after_trigger ? 2 : 1;
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, win.after_trigger ? 1 : 0,
+                         km, epi, status);
   return e;
 }
 

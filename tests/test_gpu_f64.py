@@ -207,6 +207,21 @@ def test_look_ahead_matches_plain_sequence_bitwise(bi, sizes):
     assert np.array_equal(X, ref.cpu().numpy())
 
 
+@pytest.mark.parametrize("sizes", [[256] * 9, [300, 200, 500, 512, 512, 176]])
+def test_look_ahead_option_off_same_bits(bi, sizes):
+    """lookahead = -1 runs one step at a time on the caller's stream only."""
+    n = sum(sizes)
+    A = inputs.gaussian_shifted(n, 33, sigma=1.5)
+    outs = []
+    for la in (0, -1):
+        d = torch.from_numpy(A).cuda()
+        st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, "f64", None, lookahead=la)
+        assert st == bi.OK
+        outs.append(d.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert rho(A, outs[0]) <= 1e-12
+
+
 @pytest.mark.parametrize("sizes", [[256] * 8 + [57], [300, 200, 500, 512, 512, 176], [100] * 21])
 def test_look_ahead_ragged_vs_oracle(bi, sizes):
     n = sum(sizes)

@@ -182,6 +182,29 @@ def test_full_size_16384_mixed(bi, mode, sigma, seed):
         assert np.linalg.norm(X[:, j] - S[:, t]) / np.linalg.norm(S[:, t]) <= 4 * n * kappa * U64
 
 
+# The mixed look-ahead splits step k's Schur update into the next pivot block's
+# square (its covering tiles) and the rest, and runs the next FP32 pivot inverse
+# beside the rest. Every element is the same tile sum either way, so the
+# unrefined elimination must match the one-step-at-a-time sequence bit for bit,
+# also where block edges cut through tiles (ragged sizes) and in reverse order.
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("sizes,order", [([256] * 12, 0), ([200, 312, 256, 300, 212, 200, 300, 316, 300], 0),
+                                         ([256] * 12, 1), ([500, 24, 512, 100, 412, 500], 0)])
+def test_mixed_look_ahead_same_bits(bi, mode, sizes, order):
+    n = sum(sizes)
+    assert n >= 2048
+    A = inputs.gaussian_shifted(n, 7 + n, sigma=1.5)
+    outs = []
+    for la in (0, -1):
+        d = torch.from_numpy(A).cuda()
+        st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, mode, None, max_refine=0, pivot_order=order,
+                                         lookahead=la)
+        assert st == bi.OK
+        outs.append(d.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert rho_np(A, outs[0]) < 1e-5
+
+
 def _ill_block(n, kappa, seed):
     """Q diag(logspace(0, -log10 kappa)) Q^T, rounded to FP32 values (so the
     mixed path's FP32 copy is exact)."""
