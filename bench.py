@@ -320,6 +320,17 @@ def run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms):
         trace = bi.blockinv_trace_summary()
         info = infos[-1]
         g = trace.get("residual_group_gemm_e4m3", {"ms": 0, "flops": 0, "launches": 0})
+        if g["ms"]:
+            # The host enqueues all 9 digit groups of an incremental residual
+            # and the device skips those past its group count, so the traced
+            # flops are replaced by the products that ran: 45 digit pairs per
+            # fresh residual, G (G + 1) / 2 per incremental one.
+            G = infos[-1].incremental_groups
+            inc = infos[-1].incremental_residuals
+            fresh = infos[-1].refine_iters + 1 - inc
+            pairs = fresh * 45 + inc * G * (G + 1) // 2
+            g = dict(g, flops=args.steps * pairs * 2.0 * n ** 3, flops_note="digit products that ran")
+            trace["residual_group_gemm_e4m3"] = g
         schur = trace.get(f"schur_update_{mode}_tc", {"ms": 0, "bytes": 0, "launches": 0})
         kt_total = sum(v["ms"] for v in trace.values())
         achieved_g = g["flops"] / (g["ms"] / 1e3) / 1e12 if g["ms"] else None
@@ -330,6 +341,7 @@ def run_mixed_paths(args, bi, torch, dA, dX, n, sizes, stream, fp64_ms):
             "latency_ms": percentiles(per),
             "rho_refinement": info.rho, "rho_initial": info.rho_initial, "rho_fp64_check": rho64,
             "refine_iters": info.refine_iters, "used_fallback": info.used_fallback,
+            "incremental_digit_groups": info.incremental_groups,
             "roofline": {
                 "bound": "tensor", "kernel": "residual_group_gemm_e4m3", "achieved": achieved_g,
                 "peak": peaks["fp8"], "unit": "TFLOP/s",

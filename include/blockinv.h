@@ -331,7 +331,9 @@ typedef struct {
                           /* pivot order; 2: merged blocks (singular_fallback)          */
   int32_t blocks_used;    /* pivot blocks of the partition that produced the result    */
   int32_t incremental_residuals; /* mixed modes: residuals formed as E - A (X - X_prev) */
-  int32_t reserved[3];
+  int32_t incremental_groups; /* base-32 digit groups of the last one (1..9: 9 minus a  */
+                          /* fifth of the exponent gap between X and its change)      */
+  int32_t reserved[2];
 } blockinv_info;
 
 /* blockinv_invert with options and a report (either pointer may be NULL). */

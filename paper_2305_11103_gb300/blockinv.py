@@ -84,7 +84,7 @@ class Info(ctypes.Structure):
                 ("rho", ctypes.c_double), ("rho_initial", ctypes.c_double), ("used_fallback", ctypes.c_int32),
                 ("fp64_pivots", ctypes.c_int32), ("partition_fallback", ctypes.c_int32),
                 ("blocks_used", ctypes.c_int32), ("incremental_residuals", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("incremental_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

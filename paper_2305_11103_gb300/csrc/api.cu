@@ -433,6 +433,7 @@ void read_mixed_info(const MixedState& ms, cudaStream_t s, blockinv_info* info) 
   if (cudaStreamSynchronize(s) != cudaSuccess) return;
   info->refine_iters = ctl[1];
   info->incremental_residuals = ctl[5];
+  info->incremental_groups = ctl[5] > 0 ? ctl[6] : 0;
   info->fp64_pivots = piv[1];
   if (ctl[3] >= 0) {
     info->rho_initial = hist[0];

@@ -47,6 +47,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstddef>
 
 #include "tc_gemm.cuh"
@@ -58,12 +59,14 @@ namespace {
 constexpr int kLog2Digit = 5;  // base-32 digits
 constexpr int kHeadroom = 1;   // fraction bits F = 5 S - 1 keep the leading digit within [-16, 16]
 constexpr int kUpdateChunkK = 2048;  // K elements per accumulator hand-off in the update
-// Incremental residual E_new = E - A (X_new - X): the change of X is cut into
-// base-32 digits like X, but kIncrGroups digit groups suffice (28 products
-// instead of 45) while ||E||_F <= kIncrMaxE, since its column scales are then
-// at most 2^-10 of X's and the dropped groups stay below the fresh residual's
-// error floor.
-constexpr int kIncrGroups = 7;
+// Incremental residual E_new = E - A (X_new - X), used after a residual with
+// ||E||_F <= kIncrMaxE: the change of X is cut into S base-32 digits like X,
+// and only the leading G digit groups are multiplied. With D the smallest
+// difference, over the columns, between the exponent bounds of X and of the
+// change, dropping the groups after G = S - floor(D / 5) costs no more than
+// the fresh residual's own rounding of X (2^(c - 5 S) for a column bound 2^c),
+// so E_new has the fresh residual's error floor; a change 2^-18 of X leaves
+// 6 groups (21 digit products instead of 45).
 constexpr double kIncrMaxE = 1e-3;
 
 struct Ctl {
@@ -73,6 +76,7 @@ struct Ctl {
   int32_t last;        // index of the last residual computed
   int32_t inc;         // the next residual is incremental (E_new = E - A (X_new - X))
   int32_t incs;        // incremental residuals computed
+  int32_t groups;      // digit groups of the last incremental residual
 };
 static_assert(sizeof(Ctl) <= sizeof(int32_t) * kRefineCtlWords, "refinement control words");
 
@@ -269,7 +273,10 @@ struct EpiAccumI64 {
   const Ctl* ctl;
   const int32_t* status;
   int path;
-  __device__ bool skip() const { return halted(ctl, status, path); }
+  int group;  // >= 0: a group of the incremental residual, skipped from ctl->groups on
+  __device__ bool skip() const {
+    return halted(ctl, status, path) || (group >= 0 && group >= *(volatile const int32_t*)&ctl->groups);
+  }
   __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
     long long* p = T + (int64_t)row0 * ldt + col;
@@ -325,26 +332,26 @@ struct EpiAddF64 {
   }
 };
 
-// Sum of squares of X (the ||X||^2 of an incremental residual's rho).
-__global__ void sumsq_kernel(const double* __restrict__ X, int64_t ldx, int n, double* sumsq, const Ctl* ctl,
-                             const int32_t* status, int path) {
+// Digit groups of an incremental residual: G = S - floor(D / 5), D the
+// smallest cx[j] - cd[j] over the columns whose change is not zero (cx: X's
+// exponent bounds, cd: the change's), at least 1 and at most S.
+__global__ void incr_groups_kernel(const int32_t* __restrict__ cx, const int32_t* __restrict__ cd, int n, int S,
+                                   Ctl* ctl, const int32_t* status, int path) {
   if (halted(ctl, status, path)) return;
-  __shared__ double red[8];
-  double s2 = 0.0;
-  const int64_t total = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / n;
-    const double v = X[i * ldx + (t - i * n)];
-    s2 = fma(v, v, s2);
-  }
+  __shared__ int red[32];
+  int dmin = INT_MAX;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (cd[j] > -2000) dmin = min(dmin, cx[j] - cd[j]);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+  for (int off = 16; off > 0; off >>= 1) dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmin;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    atomicAdd(sumsq, t);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) dmin = min(dmin, red[w]);
+    int g = S;
+    if (dmin == INT_MAX) g = 1;                 // no change at all
+    else if (dmin > 0) g = max(1, S - dmin / kLog2Digit);
+    ctl->groups = g;
   }
 }
 
@@ -478,6 +485,7 @@ __global__ void init_ctl_kernel(Ctl* ctl, int32_t* cexp, int n, int iters) {
     ctl->last = -1;
     ctl->inc = 0;
     ctl->incs = 0;
+    ctl->groups = 0;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * iters; t += gridDim.x * blockDim.x) cexp[t] = -2000;
 }
@@ -519,7 +527,7 @@ size_t refine_workspace_bytes(int n, int S, int max_updates) {
   b += 2 * (size_t)n * S * Kp;                  // A and X digit slices
   b += sizeof(long long) * (size_t)n * ldt;     // int64 accumulator
   b += 2 * sizeof(float) * (size_t)n * 2 * Kp;  // X and E^T TF32 hi/lo operands
-  b += sizeof(int32_t) * (size_t)n * (max_updates + 2);   // exponents
+  b += sizeof(int32_t) * (size_t)n * (2 * max_updates + 3);   // exponents
   b += sizeof(double) * (3 + 2 * (max_updates + 1)) + sizeof(double) * (max_updates + 1) + 64;
   if (max_updates > 0) b += 2 * sizeof(double) * (size_t)n * ldt;  // E and the change of X (incremental)
   return b + 10 * 256;
@@ -555,7 +563,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
   float* Xop = static_cast<float*>(carve(sizeof(float) * (size_t)n * 2 * Kp));
   float* Eop = static_cast<float*>(carve(sizeof(float) * (size_t)n * 2 * Kp));
   int32_t* rexp = static_cast<int32_t*>(carve(sizeof(int32_t) * n));
-  int32_t* cexp = static_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)n * (max_updates + 1)));
+  // column exponent bounds: of X (or of its change) per residual, then of X
+  // per incremental residual
+  int32_t* cexp = static_cast<int32_t*>(carve(sizeof(int32_t) * (size_t)n * 2 * (max_updates + 1)));
   double* sums = static_cast<double*>(carve(sizeof(double) * (1 + 2 * (max_updates + 1))));
   const bool incr_ok = max_updates > 0;
   double* Ebuf = incr_ok ? static_cast<double*>(carve(sizeof(double) * (size_t)n * ldt)) : nullptr;
@@ -568,7 +578,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
   if (e == cudaSuccess && max_updates > 0) e = cudaMemsetAsync(Xop, 0, sizeof(float) * (size_t)n * 2 * Kp, s);
   if (e == cudaSuccess && max_updates > 0) e = cudaMemsetAsync(Eop, 0, sizeof(float) * (size_t)n * 2 * Kp, s);
   if (e != cudaSuccess) return e;
-  init_ctl_kernel<<<64, 256, 0, s>>>(ctl, cexp, n, max_updates + 1);
+  init_ctl_kernel<<<64, 256, 0, s>>>(ctl, cexp, n, 2 * (max_updates + 1));
 
   CUtensorMap tAs, tXs, tXo, tEo;
   if (!make_tmap_2d(&tAs, Asl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBM) ||
@@ -585,7 +595,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
   }
   // the digit-group GEMMs of one residual: groups 0 .. groups - 1, each over
   // at most max_pairs digit pairs per launch
-  auto group_gemms = [&](int groups, int path) -> cudaError_t {
+  auto group_gemms = [&](int groups, int path, bool incr_groups) -> cudaError_t {
     cudaError_t r = cudaSuccess;
     for (int g = 0; g < groups && r == cudaSuccess; ++g) {
       for (int p0 = 0; p0 <= g && r == cudaSuccess; p0 += max_pairs) {
@@ -598,7 +608,8 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
           km.pa[i] = (int8_t)(p0 + i);
           km.pb[i] = (int8_t)(g - p0 - i);
         }
-        EpiAccumI64 epi{T, ldt, n, kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0, ctl, status, path};
+        EpiAccumI64 epi{T,    ldt,    n,    kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0,
+                        ctl,  status, path, incr_groups ? g : -1};
         TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
         r = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
       }
@@ -610,9 +621,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     int32_t* cx = cexp + (size_t)it * n;
     dim3 fg((n + 31) / 32, (n + 31) / 32);
     // Fresh residual E = I - A X from all S digits of X; or, after a residual
-    // with ||E||_F <= kIncrMaxE, E_new = E - A (X - X_prev) from kIncrGroups
-    // groups of the change of X. Without host steps both are enqueued and the
-    // device flag lets one of them run.
+    // with ||E||_F <= kIncrMaxE, E_new = E - A (X - X_prev) from the leading
+    // digit groups of the change of X (as many as its scale needs). Without
+    // host steps both are enqueued and the device flag lets one of them run.
     const bool fresh = !host_steps || !next_inc;
     const bool incr = incr_ok && it > 0 && (!host_steps || next_inc);
     if (fresh) {
@@ -621,7 +632,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
         e = slices_dispatch(S, nullptr, 0, X, ldx, n, Kp, rexp, cx, nullptr, Xsl, &sums[2 + 2 * it], false, ctl,
                             status, s, incr ? kFresh : kAny);
       }
-      if (e == cudaSuccess) e = group_gemms(S, incr ? kFresh : kAny);
+      if (e == cudaSuccess) e = group_gemms(S, incr ? kFresh : kAny, false);
       if (e != cudaSuccess) break;
       TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 16.0 * nd * nd : 0.0), s);
       finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
@@ -635,13 +646,17 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
         TraceScope t("residual_slice_dx", 0, 24.0 * nd * nd + (double)S * nd * Kp, s);
         e = slices_dispatch(S, nullptr, 0, Dbuf, ldt, n, Kp, rexp, cx, nullptr, Xsl, nullptr, false, ctl, status, s,
                             fresh ? kIncr : kAny);
-        sumsq_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(X, ldx, n, &sums[2 + 2 * it], ctl, status,
-                                                      fresh ? kIncr : kAny);
+        // X's column exponent bounds and ||X||^2, then the groups needed
+        int32_t* cxx = cexp + (size_t)(max_updates + 1 + it) * n;
+        col_scale_kernel<<<dim3((n + 31) / 32, (n + 255) / 256), 256, 0, s>>>(X, ldx, n, cxx, &sums[2 + 2 * it], ctl,
+                                                                              status, fresh ? kIncr : kAny);
+        incr_groups_kernel<<<1, 1024, 0, s>>>(cxx, cx, n, S, ctl, status, fresh ? kIncr : kAny);
       }
-      if (e == cudaSuccess) e = group_gemms(kIncrGroups, fresh ? kIncr : kAny);
+      // all S groups enqueued; those from ctl->groups on return at once
+      if (e == cudaSuccess) e = group_gemms(S, fresh ? kIncr : kAny, true);
       if (e != cudaSuccess) break;
       TraceScope t("residual_finalize", 0, 24.0 * nd * nd, s);
-      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, Dbuf, ldt, rexp, cx, kIncrGroups, &sums[1 + 2 * it],
+      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, Dbuf, ldt, rexp, cx, S, &sums[1 + 2 * it],
                                          it < max_updates ? Eop : nullptr, Kp, Ebuf, ldt, Ebuf, ldt, ctl, status,
                                          fresh ? kIncr : kAny);
     }

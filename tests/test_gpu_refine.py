@@ -258,14 +258,17 @@ def test_ill_conditioned_first_block_refines(bi):
 
 
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
-def test_incremental_residual_matches_fresh(bi, mode):
+@pytest.mark.parametrize("sigma", [1.5, 1e3])
+def test_incremental_residual_matches_fresh(bi, mode, sigma):
     """After the first update the residual is formed as E - A (X_new - X_old)
-    from 7 digit groups of the change; it must agree with a fresh 9-digit
-    residual of the same result and with FP64 numpy."""
+    from the leading digit groups of the change (fewer than 9 here: the change
+    is far below X); it must agree with a fresh 9-digit residual of the same
+    result and with FP64 numpy."""
     n = 2048
-    A = inputs.gaussian_shifted(n, 95, sigma=1.5)
+    A = inputs.gaussian_shifted(n, 95, sigma=sigma)
     st, info, X = refine(bi, A, [256] * 8, mode)
     assert st == bi.OK and info.incremental_residuals >= 1 and info.used_fallback == 0
+    assert 1 <= info.incremental_groups < 9, info.as_dict()
     _, rho_fresh = tc_residual(bi, A, X)
     r = np.linalg.norm(A @ X - np.eye(n)) / (np.linalg.norm(A) * np.linalg.norm(X))
     assert r <= 1e-12
