@@ -362,8 +362,9 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     const double bd = b, nd = n, rest = n - b;
     const double inside = (double)b1 * b1, elems = part == kWhole ? rest * nd
                                                    : part == kInside ? inside : rest * nd - inside;
-    TraceScope t(bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc", 2.0 * bd * elems * (nsl > 1 ? 3 : 1),
-                 4.0 * 2.0 * elems + eb * 2.0 * nd * bd * nsl, s);
+    const char* name = part == kInside ? (bf16 ? "schur_next_block_bf16_tc" : "schur_next_block_tf32_tc")
+                                       : (bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc");
+    TraceScope t(name, 2.0 * bd * elems * (nsl > 1 ? 3 : 1), 4.0 * 2.0 * elems + eb * 2.0 * nd * bd * nsl, s);
     return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
                                                   max_ctas, after_trigger)
                 : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
