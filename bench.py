@@ -435,7 +435,7 @@ def run_batched(args, bi, torch, stream):
     gbs = tr["bytes"] / tr["launches"] / (kms / 1e3) / 1e9
     tfs = tr["flops"] / tr["launches"] / (kms / 1e3) / 1e12
     out["spd11x11_200k"] = {
-        "workload": "200000 SPD 11x11 FP64 (B B^T + 0.1 I, seed 8), blocks [5, 6], 16 lanes per matrix",
+        "workload": "200000 SPD 11x11 FP64 (B B^T + 0.1 I, seed 8), blocks [5, 6], 4 lanes x 3 rows per matrix",
         "ms_per_batch": ms, "inverses_per_s": count / (ms / 1e3), "kernel_ms": kms,
         "max_rho": float(rho.max()), "failed": int((st != 0).sum().item()),
         "symmetric": bool(np.array_equal(X, X.transpose(0, 2, 1))),

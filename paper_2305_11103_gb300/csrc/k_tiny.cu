@@ -3,16 +3,23 @@
 // systematics matrices split into blocks of 5 and 6), and in general any order
 // up to 32 with the paper's Table 2 partition or the caller's.
 //
-// A segment of NMAX lanes (16 or 32) holds one matrix, one row per lane in
-// registers. Eq. (a) is applied one block at a time, in block order: the
-// pivot block's Gauss-Jordan elimination, column by column with the pivot
-// row searched among the block's rows only (partial pivoting inside the
-// block), where each row operation is applied to whole rows. On the block's
-// rows this forms P^-1 X[k, :] (the row panel); on every other row it forms
-// the Schur complement S = D - C P^-1 B and the column panel -C P^-1. The
-// pivot row is broadcast with warp shuffles of the segment. Rows are not
-// swapped: each lane remembers the column it was pivot for, and the result
-// is unscrambled on the way out.
+// A group of L lanes holds one matrix, R rows per lane in registers (row
+// r = lane + L s, s < R; L R >= n, chosen per order so that few slots idle:
+// 11 x 11 is 4 lanes x 3 rows). Eq. (a) is applied one block at a time, in
+// block order: the pivot block's Gauss-Jordan elimination, column by column
+// with the pivot row searched among the block's rows only (partial pivoting
+// inside the block), where each row operation is applied to whole rows. On the
+// block's rows this forms P^-1 X[k, :] (the row panel); on every other row it
+// forms the Schur complement S = D - C P^-1 B and the column panel -C P^-1.
+// The pivot row is broadcast with warp shuffles inside the group. Rows are not
+// swapped: each row remembers the column it was pivot for, and the result is
+// unscrambled on the way out.
+//
+// Cost model: on this GPU a warp's FP64 instruction occupies the SM's FP64
+// pipe for 16 clocks, so the kernel counts FP64 instructions: per column and
+// lane R L-padded row updates of n fused multiply-adds, and one reciprocal of
+// the pivot (a hardware estimate and two Newton-Raphson steps, 4 FMAs, instead
+// of a division).
 //
 // With BLOCKINV_BATCH_SPD the input is taken as symmetric positive definite:
 // every pivot block and Schur complement is then SPD, so the diagonal pivots
@@ -41,17 +48,34 @@ struct TinyPartition {
   int col_b[kTinyMax];  // its order
 };
 
-template <int NMAX>
+// 1 / v: the hardware estimate (from the leading 32 bits of v, relative error
+// about 2^-20) and two Newton-Raphson steps r <- r + r (1 - v r), each
+// squaring the relative error, so within an ulp or so of the quotient. Outside
+// the normal range of v and 1 / v, the division.
+__device__ __forceinline__ double recip64(double v) {
+  const double a = fabs(v);
+  if (!(a >= 2.2250738585072014e-308 && a <= 4.0e307)) return 1.0 / v;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
+}
+
+template <int L, int R, bool kSPD>
 __global__ void __launch_bounds__(kTinyThreads)
-tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, int spd, int32_t* __restrict__ status) {
-  constexpr int MPC = kTinyThreads / NMAX;  // matrices per CTA
+tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, int32_t* __restrict__ status) {
+  constexpr int NC = L * R;                  // row slots (>= n)
+  constexpr int MPC = kTinyThreads / L;      // matrices per CTA
   extern __shared__ double stage[];          // MPC x n x n
   __shared__ int seg_state[MPC];             // 0 ok, else the error status
   const int n = part.n;
   const int nn = n * n;
   const int64_t m0 = (int64_t)blockIdx.x * MPC;
   const int tid = threadIdx.x;
-  const int seg = tid / NMAX, lane = tid % NMAX;
+  const int seg = tid / L, gl = tid % L;
+  const int wbase = (tid & 31) - gl;         // the group's first lane in the warp
   const int64_t nmat = min((int64_t)MPC, count - m0);
   const bool live = seg < nmat;
   const double* src = A + m0 * nn;
@@ -59,83 +83,124 @@ tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, i
   if (tid < MPC) seg_state[tid] = 0;
   __syncthreads();
 
-  const bool row_ok = live && lane < n;
   double* mine = stage + (size_t)seg * nn;
-  double x[NMAX];
+  double x[R][NC];
   bool nonfinite = false;
 #pragma unroll
-  for (int l = 0; l < NMAX; ++l) {
-    x[l] = (row_ok && l < n) ? mine[lane * n + l] : 0.0;
-    nonfinite |= !isfinite(x[l]);
-  }
-  // a non-finite entry anywhere in this segment's matrix
-  const unsigned bits = __ballot_sync(0xffffffffu, nonfinite);
-  const unsigned segmask = (NMAX == 32) ? 0xffffffffu : (0xffffu << (tid & 16));
-  int err = (bits & segmask) ? BLOCKINV_ERR_NONFINITE : 0;
-  bool used = false;  // this lane's row has been a pivot row
-  int my_col = -1;    // the column it was pivot for
-  int perm[NMAX];     // pivot row of each column (the same in every lane of the segment)
+  for (int s = 0; s < R; ++s) {
+    const int r = gl + L * s;
 #pragma unroll
-  for (int c = 0; c < NMAX; ++c) {
+    for (int l = 0; l < NC; ++l) {
+      x[s][l] = (live && r < n && l < n) ? mine[r * n + l] : 0.0;
+      nonfinite |= !isfinite(x[s][l]);
+    }
+  }
+  // a non-finite entry anywhere in this group's matrix
+  const unsigned bits = __ballot_sync(0xffffffffu, nonfinite);
+  const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << wbase);
+  int err = (bits & gmask) ? BLOCKINV_ERR_NONFINITE : 0;
+  bool used[R];       // the row in slot s has been a pivot row
+  int my_col[R];      // the column it was pivot for
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    used[s] = false;
+    my_col[s] = -1;
+  }
+  int perm[NC];       // pivot row of each column (the same in every lane of the group)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
     perm[c] = c;
     if (c < n) {
-      const int o = part.col_o[c], b = part.col_b[c];
       int pr = c;  // SPD: the diagonal pivot
       bool found = true;
-      if (!spd) {
-        // pivot search among the block's rows not yet used: |x| as its bit
-        // pattern (non-negative doubles order like their bits; NaN above
-        // infinity), compared on the integer pipe, lowest row on ties
-        const bool cand = row_ok && !used && lane >= o && lane < o + b;
-        unsigned long long key = cand ? static_cast<unsigned long long>(__double_as_longlong(fabs(x[c]))) : 0ull;
-        int idx = cand ? lane : NMAX;
+      if constexpr (!kSPD) {
+        // pivot search among the block's rows not yet used: candidates carry
+        // the top bit above |x| as its bit pattern (non-negative doubles order
+        // like their bits; NaN above infinity), lowest row on ties
+        const int o = part.col_o[c], b = part.col_b[c];
+        unsigned long long key = 0ull;
+        int idx = NC;
 #pragma unroll
-        for (int off = NMAX / 2; off > 0; off >>= 1) {
-          const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, key, off, NMAX);
-          const int oi = __shfl_xor_sync(0xffffffffu, idx, off, NMAX);
+        for (int s = 0; s < R; ++s) {
+          const int r = gl + L * s;
+          const bool cand = live && r < n && !used[s] && r >= o && r < o + b;
+          const unsigned long long k =
+              cand ? (static_cast<unsigned long long>(__double_as_longlong(fabs(x[s][c]))) | (1ull << 63)) : 0ull;
+          if (k > key) {
+            key = k;
+            idx = r;
+          }
+        }
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+          const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, key, off, L);
+          const int oi = __shfl_xor_sync(0xffffffffu, idx, off, L);
           if (ok2 > key || (ok2 == key && oi < idx)) {
             key = ok2;
             idx = oi;
           }
         }
-        found = idx < NMAX;
-        pr = found ? idx : 0;
+        found = (key >> 63) != 0;
+        pr = found ? idx : c;
       }
       perm[c] = pr;
-      const double pc = __shfl_sync(0xffffffffu, x[c], pr, NMAX);
+      const int owner = pr % L, slot = pr / L;
+      double pv = x[0][c];
+#pragma unroll
+      for (int s = 1; s < R; ++s)
+        if (slot == s) pv = x[s][c];
+      const double pc = __shfl_sync(0xffffffffu, pv, wbase + owner);
       if (err == 0 && live) {
         if (!found || pc == 0.0) err = BLOCKINV_ERR_SINGULAR;
         else if (!isfinite(pc)) err = BLOCKINV_ERR_NONFINITE;
       }
-      const double inv = (err == 0) ? 1.0 / pc : 0.0;
-      const bool is_pivot = lane == pr;
+      const double inv = (err == 0) ? recip64(pc) : 0.0;
       // every row: x[l] += alpha P[p][l] (l != c), with the pivot row first
       // cleared and alpha = inv there, alpha = -x[c] inv elsewhere; x[c] gets
       // inv on the pivot row and -x[c] inv elsewhere
-      const double alpha = is_pivot ? inv : -x[c] * inv;
+      bool piv[R];
+      double alpha[R];
 #pragma unroll
-      for (int l = 0; l < NMAX; ++l) {
-        const double pl = __shfl_sync(0xffffffffu, x[l], pr, NMAX);  // pivot row, before this column's update
-        if (l < n) x[l] = (l == c) ? alpha : fma(alpha, pl, is_pivot ? 0.0 : x[l]);
+      for (int s = 0; s < R; ++s) {
+        piv[s] = gl == owner && s == slot;
+        alpha[s] = piv[s] ? inv : -x[s][c] * inv;
       }
-      if (is_pivot) {
-        used = true;
-        my_col = c;
+#pragma unroll
+      for (int l = 0; l < NC; ++l) {
+        if (l < n) {
+          double v = x[0][l];
+#pragma unroll
+          for (int s = 1; s < R; ++s)
+            if (slot == s) v = x[s][l];
+          const double pl = __shfl_sync(0xffffffffu, v, wbase + owner);  // pivot row, before this column's update
+#pragma unroll
+          for (int s = 0; s < R; ++s) x[s][l] = (l == c) ? alpha[s] : fma(alpha[s], pl, piv[s] ? 0.0 : x[s][l]);
+        }
       }
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        if (piv[s]) {
+          used[s] = true;
+          my_col[s] = c;
+        }
     }
   }
-  if (err != 0 && live && lane == 0) seg_state[seg] = err;
+  if (err != 0 && live && gl == 0) seg_state[seg] = err;
   __syncthreads();
   const bool ok = live && seg_state[seg] == 0;
   // unscramble: row my_col of the inverse gets x[j] at column perm[j]
-  if (ok && lane < n) {
+  if (ok) {
 #pragma unroll
-    for (int j = 0; j < NMAX; ++j)
-      if (j < n) mine[my_col * n + perm[j]] = x[j];
+    for (int s = 0; s < R; ++s) {
+      if (gl + L * s >= n) continue;
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (j < n) mine[my_col[s] * n + perm[j]] = x[s][j];
+    }
   }
   __syncthreads();
-  if (spd && ok) {  // exact symmetry: the upper triangle wins
-    for (int e = lane; e < nn; e += NMAX) {
+  if (kSPD && ok) {  // exact symmetry: the upper triangle wins
+    for (int e = gl; e < nn; e += L) {
       const int i = e / n, j = e - i * n;
       if (i > j) mine[e] = mine[j * n + i];
     }
@@ -144,17 +209,33 @@ tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, i
   double* dst = A + m0 * nn;
   for (int e = tid; e < nmat * nn; e += kTinyThreads)
     if (seg_state[e / nn] == 0) dst[e] = stage[e];
-  if (status && live && lane == 0) status[m0 + seg] = seg_state[seg];
+  if (status && live && gl == 0) status[m0 + seg] = seg_state[seg];
 }
 
-template <int NMAX>
-cudaError_t launch_tiny(const TinyPartition& part, bool spd, double* A, int64_t count, int32_t* status,
-                        cudaStream_t s) {
-  constexpr int MPC = kTinyThreads / NMAX;
+template <int L, int R, bool kSPD>
+cudaError_t launch_tiny(const TinyPartition& part, double* A, int64_t count, int32_t* status, cudaStream_t s) {
+  constexpr int MPC = kTinyThreads / L;
   const int64_t blocks = (count + MPC - 1) / MPC;
   const size_t smem = sizeof(double) * MPC * part.n * part.n;
-  tiny_batched_kernel<NMAX><<<(unsigned)blocks, kTinyThreads, smem, s>>>(A, count, part, spd ? 1 : 0, status);
+  auto k = tiny_batched_kernel<L, R, kSPD>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<(unsigned)blocks, kTinyThreads, smem, s>>>(A, count, part, status);
   return cudaGetLastError();
+}
+
+// (L, R) per order: L R >= n with few idle slots, at most 48 doubles of rows
+// per lane.
+template <bool kSPD>
+cudaError_t launch_tiny_for(const TinyPartition& part, double* A, int64_t count, int32_t* status, cudaStream_t s) {
+  const int n = part.n;
+  if (n <= 8) return launch_tiny<1, 8, kSPD>(part, A, count, status, s);
+  if (n <= 12) return launch_tiny<4, 3, kSPD>(part, A, count, status, s);
+  if (n <= 16) return launch_tiny<8, 2, kSPD>(part, A, count, status, s);
+  if (n <= 24) return launch_tiny<8, 3, kSPD>(part, A, count, status, s);
+  return launch_tiny<16, 2, kSPD>(part, A, count, status, s);
 }
 
 }  // namespace
@@ -174,7 +255,7 @@ cudaError_t launch_tiny_batched(int n, const std::vector<int>& sizes, bool spd, 
     o += b;
   }
   if (o != n) return cudaErrorInvalidValue;
-  return n <= 16 ? launch_tiny<16>(part, spd, A, count, status, s) : launch_tiny<32>(part, spd, A, count, status, s);
+  return spd ? launch_tiny_for<true>(part, A, count, status, s) : launch_tiny_for<false>(part, A, count, status, s);
 }
 
 }  // namespace blockinv
