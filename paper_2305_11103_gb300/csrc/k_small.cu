@@ -5,12 +5,14 @@
 // Eq. (a) on its matrix in registers, with every index known at compile time;
 // pivot blocks of order <= 4 use closed forms (the "algebraic expressions" of
 // Sec. 5.1): 1/a, the 2 x 2 and 3 x 3 adjugates, and for order 4 Eq. (a)
-// itself on 2 x 2 sub-blocks.
+// itself on 2 x 2 sub-blocks. Reciprocals are the 3-FMA estimate-and-correct
+// of fp64_ops.cuh, and the zero / finiteness tests look at bit patterns.
 //
 // Memory: a CTA of 128 threads stages its 128 consecutive matrices through
 // shared memory, so that the global loads and stores are coalesced. Per
 // matrix the kernel moves 2 * 8 n^2 bytes and does about 2 n^3 flops; on
 // GB300 the FP64 pipe (2 DFMA / clock / SM), not HBM, bounds it.
+#include "fp64_ops.cuh"
 #include "internal.h"
 
 namespace blockinv {
@@ -35,7 +37,8 @@ template <> struct Partition<6> { static constexpr int p = 2; static constexpr i
 template <> struct Partition<7> { static constexpr int p = 2; static constexpr int s[2] = {3, 4}; };
 template <> struct Partition<8> { static constexpr int p = 4; static constexpr int s[4] = {2, 2, 2, 2}; };
 
-__device__ __forceinline__ bool bad(double d) { return d == 0.0 || !isfinite(d); }
+// zero or non-finite, on the integer pipe
+__device__ __forceinline__ bool bad(double d) { return zero_bits(d) || nonfinite_bits(d); }
 
 // Closed-form inverses; return false if singular or non-finite.
 template <int B>
@@ -45,7 +48,7 @@ template <>
 struct Inv<1> {
   __device__ static bool run(const double (&m)[1][1], double (&r)[1][1]) {
     if (bad(m[0][0])) return false;
-    r[0][0] = 1.0 / m[0][0];
+    r[0][0] = recip64(m[0][0]);
     return true;
   }
 };
@@ -55,7 +58,7 @@ struct Inv<2> {
   __device__ static bool run(const double (&m)[2][2], double (&r)[2][2]) {
     const double det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
     if (bad(det)) return false;
-    const double id = 1.0 / det;
+    const double id = recip64(det);
     r[0][0] = m[1][1] * id;
     r[0][1] = -m[0][1] * id;
     r[1][0] = -m[1][0] * id;
@@ -73,7 +76,7 @@ struct Inv<3> {
     const double c02 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
     const double det = m[0][0] * c00 + m[0][1] * c01 + m[0][2] * c02;
     if (bad(det)) return false;
-    const double id = 1.0 / det;
+    const double id = recip64(det);
     r[0][0] = c00 * id;
     r[1][0] = c01 * id;
     r[2][0] = c02 * id;
@@ -213,7 +216,7 @@ small_batched_kernel(double* __restrict__ A, int64_t count, int32_t* __restrict_
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         x[i][j] = stage[t * NN + i * N + j];
-        finite = finite && isfinite(x[i][j]);
+        finite = finite && !nonfinite_bits(x[i][j]);
       }
     int code = BLOCKINV_OK;
     if (!finite) {

@@ -17,9 +17,10 @@
 //
 // Cost model: on this GPU a warp's FP64 instruction occupies the SM's FP64
 // pipe for 16 clocks, so the kernel counts FP64 instructions: per column and
-// lane R L-padded row updates of n fused multiply-adds, and one reciprocal of
-// the pivot (a hardware estimate and two Newton-Raphson steps, 4 FMAs, instead
-// of a division).
+// lane R L-padded row updates of n fused multiply-adds, R products for the
+// multipliers and one reciprocal of the pivot (a hardware estimate and one
+// third-order correction, 3 FMAs, instead of a division). Finiteness and zero
+// tests look at bit patterns on the integer pipe.
 //
 // With BLOCKINV_BATCH_SPD the input is taken as symmetric positive definite:
 // every pivot block and Schur complement is then SPD, so the diagonal pivots
@@ -33,6 +34,7 @@
 #include <climits>
 #include <vector>
 
+#include "fp64_ops.cuh"
 #include "internal.h"
 
 namespace blockinv {
@@ -47,21 +49,6 @@ struct TinyPartition {
   int col_o[kTinyMax];  // offset of the block that holds column c
   int col_b[kTinyMax];  // its order
 };
-
-// 1 / v: the hardware estimate (from the leading 32 bits of v, relative error
-// about 2^-20) and two Newton-Raphson steps r <- r + r (1 - v r), each
-// squaring the relative error, so within an ulp or so of the quotient. Outside
-// the normal range of v and 1 / v, the division.
-__device__ __forceinline__ double recip64(double v) {
-  const double a = fabs(v);
-  if (!(a >= 2.2250738585072014e-308 && a <= 4.0e307)) return 1.0 / v;
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
-  double e = fma(-v, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-v, r, 1.0);
-  return fma(r, e, r);
-}
 
 template <int L, int R, bool kSPD>
 __global__ void __launch_bounds__(kTinyThreads)
@@ -92,7 +79,7 @@ tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, i
 #pragma unroll
     for (int l = 0; l < NC; ++l) {
       x[s][l] = (live && r < n && l < n) ? mine[r * n + l] : 0.0;
-      nonfinite |= !isfinite(x[s][l]);
+      nonfinite |= exp_field(x[s][l]) == 0x7FF;
     }
   }
   // a non-finite entry anywhere in this group's matrix
@@ -150,9 +137,10 @@ tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, i
       for (int s = 1; s < R; ++s)
         if (slot == s) pv = x[s][c];
       const double pc = __shfl_sync(0xffffffffu, pv, wbase + owner);
-      if (err == 0 && live) {
-        if (!found || pc == 0.0) err = BLOCKINV_ERR_SINGULAR;
-        else if (!isfinite(pc)) err = BLOCKINV_ERR_NONFINITE;
+      if (err == 0 && live) {  // compared on the integer pipe
+        const unsigned long long pb = static_cast<unsigned long long>(__double_as_longlong(pc));
+        if (!found || (pb << 1) == 0ull) err = BLOCKINV_ERR_SINGULAR;
+        else if (exp_field(pc) == 0x7FF) err = BLOCKINV_ERR_NONFINITE;
       }
       const double inv = (err == 0) ? recip64(pc) : 0.0;
       // every row: x[l] += alpha P[p][l] (l != c), with the pivot row first
