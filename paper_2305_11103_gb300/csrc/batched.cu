@@ -196,7 +196,8 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
         item_m.push_back(m);
         const int nn = tmp.n[m];
         cols += (nn + 31) / 32;
-        tiles[grp] += ((nn + want - 1) / want) * ((nn + want - 1) / want);
+        // Schur tiles over the nn - b rows outside the pivot block
+        tiles[grp] += ((nn - b + want - 1) / want) * ((nn + want - 1) / want);
         starts.push_back(cols);
         ts[grp].push_back(tiles[grp]);
         st.bmax = std::max(st.bmax, b);

@@ -32,6 +32,7 @@
 #include <mutex>
 #include <cooperative_groups.h>
 
+#include "fp64_ops.cuh"
 #include "internal.h"
 
 namespace cg = cooperative_groups;
@@ -288,22 +289,137 @@ pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restr
   }
 }
 
-// Grouped form: one CTA per matrix of a batch, block order <= kGroupedMaxB,
-// every row of the pivot block in the CTA's shared memory.
+// Grouped form for pivot blocks of order kWarpPivotMax + 1 .. kGroupedMaxB:
+// one CTA per matrix of a batch, the block in shared memory. Per column: the
+// pivot row (largest |x| among the rows not yet used, lowest row on ties,
+// compared as integer keys: |x| as its bit pattern with a top bit marking a
+// candidate), the scaled pivot row and the column's multipliers, then the
+// whole block updated one element per thread and pass, so every lane works
+// whatever b is. A warp's FP64 instruction holds the FP64 pipe for 16 clocks
+// on this GPU: only the threads that scale the pivot row form its reciprocal,
+// and no comparison runs on that pipe.
+__host__ __device__ constexpr size_t grouped_pivot_smem(int b) {
+  return sizeof(double) * ((size_t)b * b + 2 * (size_t)b) + sizeof(unsigned long long) * 8 +
+         sizeof(int) * (8 + 2 * (size_t)b + 1) + 16;
+}
+
 __global__ void __launch_bounds__(kPivotThreads)
 pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count, int bmin) {
   const int m = blockIdx.x;
   if (m >= count) return;
   const GroupStep it = items[m];
-  if (it.b > kGroupedMaxB) return;  // handled by the cluster kernel
-  if (it.b <= bmin) return;         // handled by the warp kernel
-  int jw = 1, jlog = 0;
-  while (jw < it.b && jw < kPivotThreads) {
-    jw <<= 1;
-    ++jlog;
+  if (it.b > kGroupedMaxB || it.b <= bmin) return;  // the cluster kernel / the warp kernel
+  const int b = it.b, bb = b * b;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* rows = reinterpret_cast<double*>(smem_raw);  // b x b
+  double* prow = rows + bb;                            // b: scaled pivot row
+  double* fvec = prow + b;                             // b: multipliers x[r][c]
+  unsigned long long* wkey = reinterpret_cast<unsigned long long*>(fvec + b);  // per warp
+  int* wrow = reinterpret_cast<int*>(wkey + kPivotThreads / 32);               // per warp
+  int* perm = wrow + kPivotThreads / 32;               // b: pivot row of column c
+  int* srow = perm + b;                                // b: column row r was pivot for (-1 = not yet)
+  int* flag = srow + b;                                // non-finite entry seen
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* P = it.X + (int64_t)it.o * it.ldx + it.o;
+  if (tid == 0) flag[0] = 0;
+  for (int r = tid; r < b; r += kPivotThreads) srow[r] = -1;
+  __syncthreads();
+  int bad = 0;
+  for (int e = tid; e < bb; e += kPivotThreads) {
+    const int r = e / b, j = e - r * b;
+    const double v = P[(int64_t)r * it.ldx + j];
+    bad |= nonfinite_bits(v) ? 1 : 0;
+    rows[e] = v;
   }
-  pivot_gj_body<double, double, false>(it.X + (int64_t)it.o * it.ldx + it.o, it.ldx, it.b, it.b, jlog, it.Pinv,
-                                       it.b, it.status, it.k);
+  if (bad) atomicOr(flag, 1);
+  const int prior = *(volatile const int32_t*)it.status;  // an earlier kernel of this inversion failed
+  __syncthreads();
+  if (flag[0] || prior != 0) {
+    if (flag[0] && prior == 0 && tid == 0) set_status(it.status, BLOCKINV_ERR_NONFINITE, it.k);
+    return;
+  }
+  // flat walk e = tid + 256 i over the block, (r, j) stepped without division
+  const int dr = kPivotThreads / b, dj = kPivotThreads - dr * b;
+  const int r_first = tid / b, j_first = tid - r_first * b;
+  int failed = 0;
+  for (int c = 0; c < b; ++c) {
+    unsigned long long key = 0ull;
+    int row = INT_MAX;
+    if (tid < b && srow[tid] < 0) {
+      key = static_cast<unsigned long long>(__double_as_longlong(fabs(rows[tid * b + c]))) | (1ull << 63);
+      row = tid;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, row, off);
+      if (ok > key || (ok == key && oi < row)) {
+        key = ok;
+        row = oi;
+      }
+    }
+    if (lane == 0) {
+      wkey[warp] = key;
+      wrow[warp] = row;
+    }
+    __syncthreads();
+    key = wkey[0];
+    row = wrow[0];
+    for (int w = 1; w < kPivotThreads / 32; ++w) {
+      const unsigned long long ok = wkey[w];
+      const int oi = wrow[w];
+      if (ok > key || (ok == key && oi < row)) {
+        key = ok;
+        row = oi;
+      }
+    }
+    if (key == 0ull || key == (1ull << 63)) {  // no candidate, or all of them zero
+      failed = BLOCKINV_ERR_SINGULAR;
+      break;
+    }
+    if (((key >> 52) & 0x7FF) == 0x7FF) {
+      failed = BLOCKINV_ERR_NONFINITE;
+      break;
+    }
+    const int p = row;
+    if (tid < b) {
+      const double inv = recip(rows[p * b + c]);
+      prow[tid] = (tid == c) ? inv : rows[p * b + tid] * inv;
+      fvec[tid] = rows[tid * b + c];
+    }
+    if (tid == 0) {
+      perm[c] = p;
+      srow[p] = c;
+    }
+    __syncthreads();
+    int r = r_first, j = j_first;
+    for (int e = tid; e < bb; e += kPivotThreads) {
+      const double pj = prow[j];
+      rows[e] = (r == p) ? pj : ((j == c) ? 0.0 : rows[e]) - fvec[r] * pj;
+      j += dj;
+      r += dr;
+      if (j >= b) {
+        j -= b;
+        ++r;
+      }
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) set_status(it.status, failed, it.k);
+    return;
+  }
+  // unscramble: row r holds row srow[r] of the inverse, column j at perm[j]
+  int r = r_first, j = j_first;
+  for (int e = tid; e < bb; e += kPivotThreads) {
+    it.Pinv[(int64_t)srow[r] * b + perm[j]] = rows[e];
+    j += dj;
+    r += dr;
+    if (j >= b) {
+      j -= b;
+      ++r;
+    }
+  }
 }
 
 // Grouped warp form for pivot blocks of order <= 32: one warp per matrix, a
@@ -949,7 +1065,7 @@ int pivot_inverse_ctas(int b, int elem, bool f64_check) {
 cudaError_t launch_pivot_grouped(const GroupStep* items, int count, int bmax, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (bmax > kGroupedMaxB) return cudaErrorInvalidValue;
-  const size_t smem = pivot_smem_bytes(bmax, bmax, sizeof(double));
+  const size_t smem = grouped_pivot_smem(bmax);
   // blocks of order <= 32: one warp each; larger ones: one CTA each
   pivot_warp_grouped_kernel<<<(count + 3) / 4, 128, 0, s>>>(items, count);
   cudaError_t e = cudaGetLastError();

@@ -33,7 +33,10 @@ constexpr int kPanelCols = 32;
 constexpr int kPanelK = 8;
 
 // Row panel for the 32-column strip starting at j0 (all b rows of block k).
-template <int MAXB>
+// kFit (grouped batches, b often well below MAXB): a warp runs only the FMAs
+// of its rows below b (its row count is warp-uniform), and the last k chunk
+// only its b mod 8 values.
+template <int MAXB, bool kFit = false>
 __device__ __forceinline__ void row_panel_strip(double* __restrict__ X, int64_t ldx, int n, int o, int b,
                                                 const double* __restrict__ Pinv, int j0) {
   constexpr int RPT = MAXB / 8;  // rows per thread
@@ -59,11 +62,22 @@ __device__ __forceinline__ void row_panel_strip(double* __restrict__ X, int64_t 
       Xs[kk][tid & 31] = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.0;
     }
     __syncthreads();
+    if (!kFit) {
 #pragma unroll
-    for (int kk = 0; kk < kPanelK; ++kk) {
-      const double x = Xs[kk][c];
+      for (int kk = 0; kk < kPanelK; ++kk) {
+        const double x = Xs[kk][c];
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
+        for (int q = 0; q < RPT; ++q) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
+      }
+    } else {
+      const int nq = b > g ? (b - g + 7) / 8 : 0;  // rows g + 8 q < b of this warp
+      const int kn = min(kPanelK, b - kc);
+      for (int kk = 0; kk < kn; ++kk) {
+        const double x = Xs[kk][c];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+          if (q < nq) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
+      }
     }
     __syncthreads();
   }
@@ -128,7 +142,7 @@ row_panel_grouped_kernel(const GroupStep* __restrict__ items, int count, const i
   const int rows_per = (it.n + strips - 1) / strips;
   const int r0 = min(it.n, s * rows_per), r1 = min(it.n, r0 + rows_per);
   copy_column_panel(it.X, it.ldx, it.o, it.b, it.U, r0, r1, 0, 1);
-  row_panel_strip<MAXB>(it.X, it.ldx, it.n, it.o, it.b, it.Pinv, s * kPanelCols);
+  row_panel_strip<MAXB, true>(it.X, it.ldx, it.n, it.o, it.b, it.Pinv, s * kPanelCols);
 }
 
 // ---------------------------------------------------------------- K3 ------
@@ -147,7 +161,10 @@ __device__ __forceinline__ bool in_range(int v, int lo, int len) { return v >= l
 
 // One TILE x TILE output tile (TILE = 64 or 32) by 256 threads, each holding
 // (TILE / 16) x (TILE / 16) outputs.
-template <int TILE = kTile>
+// kCompact (grouped batches): i0 counts only the n - b rows outside the pivot
+// block (row ic is ic, or ic + b from o on), so no tile computes pivot rows,
+// and the last k chunk runs only its b mod 8 values.
+template <int TILE = kTile, bool kCompact = false>
 __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, int n, int o, int b,
                                            const double* __restrict__ U, int i0, int j0, int o1 = 0, int b1 = 0,
                                            int mask = kAll) {
@@ -170,16 +187,17 @@ __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, 
       const int e = tid + h * 256;
       // U tile: TILE rows x 8 k
       const int ui = e >> 3, uk = e & 7;
-      const int gi = i0 + ui;
-      Us[uk][ui] = (gi < n && kc + uk < b) ? U[(int64_t)gi * b + kc + uk] : 0.0;
+      const int ic = i0 + ui;
+      const bool iok = kCompact ? ic < n - b : ic < n;
+      const int gi = (kCompact && ic >= o) ? ic + b : ic;
+      Us[uk][ui] = (iok && kc + uk < b) ? U[(int64_t)gi * b + kc + uk] : 0.0;
       // V tile: 8 k x TILE columns of row panel k
       const int vk = e / TILE, vj = e % TILE;
       const int gj = j0 + vj;
       Vs[vk][vj] = (gj < n && kc + vk < b) ? X[(int64_t)(o + kc + vk) * ldx + gj] : 0.0;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTileK; ++kk) {
+    auto kstep = [&](int kk) {
       double u[PT], v[PT];
 #pragma unroll
       for (int a = 0; a < PT; ++a) u[a] = Us[kk][ty * PT + a];
@@ -189,13 +207,20 @@ __device__ __forceinline__ void schur_tile(double* __restrict__ X, int64_t ldx, 
       for (int a = 0; a < PT; ++a)
 #pragma unroll
         for (int d = 0; d < PT; ++d) acc[a][d] = fma(u[a], v[d], acc[a][d]);
+    };
+    if (!kCompact || kc + kTileK <= b) {
+#pragma unroll
+      for (int kk = 0; kk < kTileK; ++kk) kstep(kk);
+    } else {
+      for (int kk = 0; kk < b - kc; ++kk) kstep(kk);  // the last, partial chunk
     }
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < PT; ++a) {
-    const int i = i0 + ty * PT + a;
-    if (i >= n || (i >= o && i < o + b)) continue;
+    const int ic = i0 + ty * PT + a;
+    if (kCompact ? ic >= n - b : (ic >= n || (ic >= o && ic < o + b))) continue;
+    const int i = (kCompact && ic >= o) ? ic + b : ic;
     const bool ri = in_range(i, o1, b1);
     double* row = X + (int64_t)i * ldx;
 #pragma unroll
@@ -262,20 +287,20 @@ schur_update_f64_kernel(double* __restrict__ X, int64_t ldx, int n, int o, int b
 }
 
 // Grouped Schur update: tile t of the batch belongs to item m (TILE x TILE
-// tiles, TILE = 64 or 32).
+// tiles, TILE = 64 or 32, over the n - b rows outside the pivot block by the
+// n columns: ceil((n - b) / TILE) x ceil(n / TILE) tiles per item).
 template <int TILE>
 __global__ void __launch_bounds__(256)
 schur_update_grouped_kernel(const GroupStep* __restrict__ items, int count, const int32_t* __restrict__ tile_start) {
   const int t = blockIdx.x;
   const int m = find_item(tile_start, count, t);
   const GroupStep it = items[m];
-  const int tiles_row = (it.n + TILE - 1) / TILE;
+  const int tiles_col = (it.n + TILE - 1) / TILE;
   const int local = t - tile_start[m];
-  const int i0 = (local / tiles_row) * TILE;
-  const int j0 = (local % tiles_row) * TILE;
-  if (i0 >= it.o && i0 + TILE <= it.o + it.b) return;
+  const int i0 = (local / tiles_col) * TILE;  // compact row: pivot rows skipped
+  const int j0 = (local % tiles_col) * TILE;
   if (failed(it.status)) return;
-  schur_tile<TILE>(it.X, it.ldx, it.n, it.o, it.b, it.U, i0, j0);
+  schur_tile<TILE, true>(it.X, it.ldx, it.n, it.o, it.b, it.U, i0, j0);
 }
 
 // --------------------------------------------------------- residual -------
