@@ -264,21 +264,23 @@ slice_cols_t_kernel(const double* __restrict__ X, int64_t ld, int n, const int32
 }
 
 // -------------------------------------------------------- epilogues ------
+// T (int64) gets every digit group of a residual, each exact in the FP32
+// accumulator: chunk c of a tile belongs to group g = chunk_group(starts, c)
+// and is added shifted left by 5 (groups - 1 - g) bits; chunk 0 overwrites.
 struct EpiAccumI64 {
   long long* T;
   int64_t ldt;
   int n;
-  int shift;
-  int first;
+  int groups;
+  uint32_t group_starts;
   const Ctl* ctl;
   const int32_t* status;
   int path;
-  int group;  // >= 0: a group of the incremental residual, skipped from ctl->groups on
-  __device__ bool skip() const {
-    return halted(ctl, status, path) || (group >= 0 && group >= *(volatile const int32_t*)&ctl->groups);
-  }
+  __device__ bool skip() const { return halted(ctl, status, path); }
   __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
     if (col >= n) return;
+    const int shift = kLog2Digit * (groups - 1 - tc::chunk_group(group_starts, chunk));
+    const bool first = chunk == 0;
     long long* p = T + (int64_t)row0 * ldt + col;
     // two halves of 16 rows: all loads of a half before its stores
 #pragma unroll
@@ -547,8 +549,8 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
                            int max_updates, int S, void* ws, double* hist, int32_t* ctl_words, int32_t* status,
                            double* Eout, int64_t lde, cudaStream_t s, bool report, bool host_steps) {
   if (S < kMinResidualSlices || S > kMaxResidualSlices || n < 1 || n > kMixedMaxOrder) return cudaErrorInvalidValue;
-  // digit pairs per GEMM launch: pairs * n * 2^8 <= 2^24
-  const int max_pairs = std::min(tc::kMaxPairs, (1 << 16) / n);
+  // digit pairs per accumulator chunk: pairs * n * 2^8 <= 2^24
+  const int max_pairs = (1 << 16) / n;
   Ctl* ctl = reinterpret_cast<Ctl*>(ctl_words);
   const int Kp = (n + 127) / 128 * 128;
   const int64_t ldt = (n + 31) / 32 * 32;
@@ -593,28 +595,36 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     row_scale_kernel<<<(n + 7) / 8, 256, 0, s>>>(A0, ld0, n, rexp, &sums[0], ctl, status);
     e = slices_dispatch(S, A0, ld0, nullptr, 0, n, Kp, rexp, nullptr, Asl, nullptr, nullptr, true, ctl, status, s);
   }
-  // the digit-group GEMMs of one residual: groups 0 .. groups - 1, each over
-  // at most max_pairs digit pairs per launch
+  // The digit-group GEMMs of one residual in one launch: groups 0 .. groups - 1,
+  // group g the pairs (p, g - p), each group cut into chunks of at most
+  // max_pairs pairs (accumulated from zero in FP32, exact) and handed to the
+  // int64 epilogue with its shift. A tile's chunks follow one another, so its
+  // slice of T stays in L2 between them. With incr_groups the device word
+  // ctl->groups switches off the trailing groups.
   auto group_gemms = [&](int groups, int path, bool incr_groups) -> cudaError_t {
-    cudaError_t r = cudaSuccess;
-    for (int g = 0; g < groups && r == cudaSuccess; ++g) {
-      for (int p0 = 0; p0 <= g && r == cudaSuccess; p0 += max_pairs) {
-        const int np = std::min(max_pairs, g + 1 - p0);
-        tc::KMap km{};
-        km.kb_per_pair = Kp / 128;
-        km.slice_cols = Kp;
-        km.kblocks = np * km.kb_per_pair;
-        for (int i = 0; i < np; ++i) {
-          km.pa[i] = (int8_t)(p0 + i);
-          km.pb[i] = (int8_t)(g - p0 - i);
+    tc::KMap km{};
+    km.kb_per_pair = Kp / 128;
+    km.slice_cols = Kp;
+    int np = 0, nc = 0;
+    km.bounds[0] = 0;
+    for (int g = 0; g < groups; ++g) {
+      for (int p0 = 0; p0 <= g; p0 += max_pairs) {
+        const int cnt = std::min(max_pairs, g + 1 - p0);
+        if (nc >= tc::kMaxChunks || np + cnt > tc::kMaxPairs) return cudaErrorInvalidValue;
+        if (p0 == 0) km.group_starts |= 1u << nc;
+        for (int i = 0; i < cnt; ++i, ++np) {
+          km.pa[np] = (int8_t)(p0 + i);
+          km.pb[np] = (int8_t)(g - p0 - i);
         }
-        EpiAccumI64 epi{T,    ldt,    n,    kLog2Digit * (groups - 1 - g), (g == 0 && p0 == 0) ? 1 : 0,
-                        ctl,  status, path, incr_groups ? g : -1};
-        TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-        r = tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
+        km.bounds[++nc] = (int16_t)(np * km.kb_per_pair);
       }
     }
-    return r;
+    km.nbounds = nc;
+    km.kblocks = np * km.kb_per_pair;
+    km.live_groups = incr_groups ? &ctl->groups : nullptr;
+    EpiAccumI64 epi{T, ldt, n, groups, km.group_starts, ctl, status, path};
+    TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
+    return tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
   };
   bool next_inc = false;  // host view of ctl->inc (host_steps)
   for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {

@@ -44,7 +44,8 @@ constexpr int kEpiWarps = 8;
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr int kStageBytes = kBM * 128 + kBN * 128;
 
-constexpr int kMaxPairs = 16;
+constexpr int kMaxPairs = 48;
+constexpr int kMaxChunks = 16;
 
 struct KMap {
   int kblocks;            // k-blocks per output tile (= pairs * kb_per_pair)
@@ -54,9 +55,23 @@ struct KMap {
                           // epilogues that add into their output (each chunk arrives separately)
   int chunk_end;          // chunks of chunk_kb cover k-blocks [0, chunk_end) (0 = all of K);
                           // the k-blocks after it form one more chunk
+  int nbounds;            // > 0: instead, chunk c covers k-blocks [bounds[c], bounds[c + 1]), c < nbounds
+  uint32_t group_starts;  // with nbounds: bit c set if chunk c starts a new group (bit 0 set)
+  const int32_t* live_groups;  // with nbounds, may be null: only the chunks of groups below
+                               // *live_groups run (read once at entry, written by an earlier kernel)
+  int16_t bounds[kMaxChunks + 1];
   int8_t pa[kMaxPairs];   // A slice of pair i
   int8_t pb[kMaxPairs];   // B slice of pair i
 };
+
+// Group of chunk c under a group-start mask.
+__host__ __device__ __forceinline__ int chunk_group(uint32_t group_starts, int c) {
+#ifdef __CUDA_ARCH__
+  return __popc(group_starts & ((2u << c) - 1u)) - 1;
+#else
+  return __builtin_popcount(group_starts & ((2u << c) - 1u)) - 1;
+#endif
+}
 
 inline KMap plain_kmap(int kblocks) {
   KMap km{};
@@ -127,7 +142,17 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int kbc = (km.chunk_kb > 0 && km.chunk_kb < km.kblocks) ? km.chunk_kb : km.kblocks;
   const int kend = (km.chunk_end > 0 && km.chunk_end < km.kblocks) ? km.chunk_end : km.kblocks;
   const int nch_a = (kend + kbc - 1) / kbc;
-  const int nch = nch_a + (kend < km.kblocks ? 1 : 0);
+  int nch = nch_a + (kend < km.kblocks ? 1 : 0);
+  int kb_run = km.kblocks;  // k-blocks loaded per tile
+  if (km.nbounds > 0) {     // explicit chunks, the trailing groups possibly switched off
+    nch = km.nbounds;
+    if (km.live_groups) {
+      const int g = *(volatile const int32_t*)km.live_groups;
+      nch = 0;
+      while (nch < km.nbounds && chunk_group(km.group_starts, nch) < g) ++nch;
+    }
+    kb_run = km.bounds[nch];
+  }
   const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
   const int nitems = my_tiles * nch;
   // An earlier kernel of this computation failed: the status word it wrote is
@@ -169,7 +194,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
       const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
       const int n0 = n_base + tn * kBN;
-      for (int kb = 0; kb < km.kblocks; ++kb, ++it) {
+      for (int kb = 0; kb < kb_run; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
         if (!mbar_wait(&sh->empty[s], ph ^ 1)) {
@@ -215,8 +240,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       fence_after_sync();
       const uint32_t d = tmem + a * kBN;
-      const int kb0 = c < nch_a ? c * kbc : kend;
-      const int kb1 = c < nch_a ? min(kend, kb0 + kbc) : km.kblocks;
+      const int kb0 = km.nbounds > 0 ? km.bounds[c] : (c < nch_a ? c * kbc : kend);
+      const int kb1 = km.nbounds > 0 ? km.bounds[c + 1] : (c < nch_a ? min(kend, kb0 + kbc) : km.kblocks);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = it % kStages;
         const uint32_t ph = (it / kStages) & 1;
