@@ -369,6 +369,50 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
 }
 
+// t 2^ex in FP64, rounded to nearest (ties to even), built from t's bits on
+// the integer pipe (this GPU's FP64 pipe is the finalize kernel's bound): the
+// magnitude's leading one gives the exponent, the next 52 bits the fraction,
+// the 11 bits below decide the rounding. The same value as the FP64
+// conversion times 2^ex; that product is the fallback where the result
+// would leave the normal range.
+__device__ __forceinline__ double scaled_i64(long long t, int ex) {
+  if (t == 0) return 0.0;
+  const unsigned long long sign = t < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = t < 0 ? 0ull - static_cast<unsigned long long>(t) : static_cast<unsigned long long>(t);
+  const int lz = __clzll(static_cast<long long>(u));
+  u <<= lz;  // leading one at bit 63
+  int e = 63 - lz + ex;
+  unsigned long long m = u >> 11;  // 53 bits with the leading one
+  const unsigned long long rest = u & 0x7FFull;
+  if (rest > 0x400ull || (rest == 0x400ull && (m & 1ull))) {
+    ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  const int be = e + 1023;
+  if (be <= 0 || be >= 2047) return static_cast<double>(t) * pow2(ex);
+  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(be) << 52) |
+                                                     (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// v in FP32 with the fraction truncated, on the integer pipe: magnitudes
+// below the FP32 normal range become zero, above it infinity (NaN stays NaN).
+// Used where 22 bits or fewer are kept (the norm sum, the TF32 hi/lo split).
+__device__ __forceinline__ float f32_trunc(double v) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned sign = static_cast<unsigned>(bits >> 32) & 0x80000000u;
+  const int ef = static_cast<int>((bits >> 52) & 0x7FF);
+  const int e = ef - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) {
+    const bool nan = ef == 0x7FF && (bits & 0xFFFFFFFFFFFFFull) != 0;
+    return __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+  }
+  return __uint_as_float(sign | (static_cast<unsigned>(e) << 23) | static_cast<unsigned>((bits >> 29) & 0x7FFFFFull));
+}
+
 // E = I - a_ii x_ij - [i != j] a_ij x_jj - 2^(e_i + f_j + 2 - 5 (S + 1)) T
 // (S = the digit groups summed in T: 2^(-2F) 32^(2S' - 1 - S) with F = 5S' - 1);
 // ||E||^2; E^T split into TF32 hi/lo (rows j of Eop, columns i and Kp + i);
@@ -394,7 +438,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     if (i < n && j < n) {
       const int ex = rexp[i] + cexp[j] + 2 * kHeadroom - kLog2Digit * (S + 1);
       const long long t = T[(int64_t)i * ldt + j];
-      const double r = (t == 0) ? 0.0 : static_cast<double>(t) * pow2(ex);
+      const double r = scaled_i64(t, ex);
       const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
       if (Ebase) {
         const double base = Ebase[(int64_t)i * ldb + j];
@@ -404,7 +448,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
       } else {
         e = -fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx) - r;   // (O_A D_X)_ij
       }
-      const float ef = static_cast<float>(e);
+      const float ef = f32_trunc(e);
       s2 = fmaf(ef, ef, s2);
       if (Eout) Eout[(int64_t)i * lde + j] = e;
     }
@@ -427,7 +471,7 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     const int i = i0 + tx;
     if (jg < n && i < n) {
       // hi + lo keep 22 bits, within FP32's 24: the split can start from FP32
-      const float v = static_cast<float>(tile[tx][jj]);
+      const float v = f32_trunc(tile[tx][jj]);
       const float hi = tf32_rn(v);
       const float lo = tf32_rn(v - hi);
       Eop[(int64_t)jg * 2 * Kp + i] = hi;
