@@ -392,7 +392,7 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.piv.ptr, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ms.hist.ptr, 0xFF, sizeof(double) * (opt.max_refine + 1), s);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(ms.a0.ptr, row, A, sizeof(double) * lda, row, n, cudaMemcpyDeviceToDevice, s);
+    e = copy_matrix(ms.a0.ptr, n, A, lda, n, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, pivot_cond_limit(opt), static_cast<int32_t*>(ms.piv.ptr),
                               status, s, opt.lookahead);
@@ -523,9 +523,7 @@ void serve_job_release(ServeJob* job) { delete job; }
 int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda, int32_t* status,
                            cudaStream_t s) {
   if (!job || !job->ms.a0.ptr) return BLOCKINV_ERR_NOT_CONVERGED;
-  const size_t row = sizeof(double) * (size_t)pl.n;
-  cudaError_t e = cudaMemcpy2DAsync(A, sizeof(double) * lda, job->ms.a0.ptr, row, row, pl.n,
-                                    cudaMemcpyDeviceToDevice, s);
+  cudaError_t e = copy_matrix(A, lda, job->ms.a0.ptr, pl.n, pl.n, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return cuda_status(e);
   return enqueue_f64(pl, A, lda, status, s);
@@ -596,7 +594,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
   if (e == cudaSuccess && may_retry) {  // the input, for retries after a singular pivot block
     e = keep.alloc(row * (size_t)n, s);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(keep.ptr, row, A, sizeof(double) * lda, row, (size_t)n, cudaMemcpyDeviceToDevice, s);
+      e = copy_matrix(keep.ptr, n, A, lda, n, cudaMemcpyDeviceToDevice, s);
   }
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
@@ -612,7 +610,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
   read_mixed_info(ms, s, info);
   if (st == BLOCKINV_ERR_NOT_CONVERGED && opt.fallback && ms.a0.ptr) {
     // The low-precision elimination or its refinement failed: redo in FP64.
-    e = cudaMemcpy2DAsync(A, sizeof(double) * lda, ms.a0.ptr, row, row, n, cudaMemcpyDeviceToDevice, s);
+    e = copy_matrix(A, lda, ms.a0.ptr, n, n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
     if (e != cudaSuccess) return record(cuda_status(e), -1);
     st = enqueue_f64(pl, A, lda, status, s, 0, -1, opt.lookahead);
@@ -625,8 +623,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
   Plan cur = pl;
   int kind = 0;
   auto rerun = [&](const Plan& q) -> int {
-    cudaError_t e2 = cudaMemcpy2DAsync(A, sizeof(double) * lda, keep.ptr, row, row, (size_t)n,
-                                       cudaMemcpyDeviceToDevice, s);
+    cudaError_t e2 = copy_matrix(A, lda, keep.ptr, n, n, cudaMemcpyDeviceToDevice, s);
     if (e2 == cudaSuccess) e2 = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
     if (e2 != cudaSuccess) return cuda_status(e2);
     int r = enqueue_f64(q, A, lda, status, s, 0, -1, opt.lookahead);
@@ -694,8 +691,7 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
   if (e == cudaSuccess) e = sbuf.alloc(2 * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sbuf.ptr, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(dbuf.ptr, row, A_host, sizeof(double) * (size_t)lda, row, (size_t)n,
-                          cudaMemcpyHostToDevice, s);
+    e = copy_matrix(dbuf.ptr, n, A_host, lda, n, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   int32_t* status = static_cast<int32_t*>(sbuf.ptr);
   st = enqueue(pl, static_cast<double*>(dbuf.ptr), (int64_t)n, mode, status, s, Options(), nullptr);
@@ -703,8 +699,7 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
     cudaStreamSynchronize(s);
     return record(st, -1);
   }
-  e = cudaMemcpy2DAsync(A_host, sizeof(double) * (size_t)lda, dbuf.ptr, row, row, (size_t)n,
-                        cudaMemcpyDeviceToHost, s);
+  e = copy_matrix(A_host, lda, dbuf.ptr, n, n, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   return finish(status, s);
 }

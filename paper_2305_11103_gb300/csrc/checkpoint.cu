@@ -54,8 +54,7 @@ int blockinv_checkpoint_write(const char* path, int64_t n, int32_t p, const int3
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<double> host((size_t)n * n);
   const size_t row = sizeof(double) * (size_t)n;
-  cudaError_t e = cudaMemcpy2DAsync(host.data(), row, A, sizeof(double) * lda, row, (size_t)n,
-                                    cudaMemcpyDeviceToHost, s);
+  cudaError_t e = copy_matrix(host.data(), n, A, lda, n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
   const int32_t np = (int32_t)pl.sizes.size();
@@ -96,8 +95,7 @@ int blockinv_checkpoint_read(const char* path, int64_t n, int32_t p, const int32
   if (std::fread(host.data(), row, (size_t)n, in.f) != (size_t)n) return BLOCKINV_ERR_INVALID;
   if (std::fgetc(in.f) != EOF || fnv1a(host.data(), row * (size_t)n) != h) return BLOCKINV_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpy2DAsync(A, sizeof(double) * lda, host.data(), row, row, (size_t)n,
-                                    cudaMemcpyHostToDevice, s);
+  cudaError_t e = copy_matrix(A, lda, host.data(), n, n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
   *k_done = fk;

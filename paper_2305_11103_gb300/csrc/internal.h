@@ -53,6 +53,18 @@ struct PivotPlan {
 
 bool plan_pivot(int b, int elem_bytes, PivotPlan* plan);
 
+// Copy an n x n FP64 matrix between row-major buffers with leading dimensions
+// dld and sld (in elements): one plain copy when both are n (a pitched copy of
+// contiguous rows ran at about 29 GB/s from pinned host memory, against
+// 190-210 GB/s for the plain one), the pitched form otherwise.
+inline cudaError_t copy_matrix(void* dst, int64_t dld, const void* src, int64_t sld, int64_t n, cudaMemcpyKind kind,
+                               cudaStream_t s) {
+  const size_t row = sizeof(double) * (size_t)n;
+  if (dld == n && sld == n) return cudaMemcpyAsync(dst, src, row * (size_t)n, kind, s);
+  return cudaMemcpy2DAsync(dst, sizeof(double) * (size_t)dld, src, sizeof(double) * (size_t)sld, row, (size_t)n,
+                           kind, s);
+}
+
 // One matrix's elimination step k in a grouped (batched) launch.
 struct GroupStep {
   double* X;       // matrix (device), row-major

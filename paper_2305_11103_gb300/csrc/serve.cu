@@ -98,7 +98,7 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
     e = workspace_pool(&pool);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&sl.dbuf), row * n, pool, s);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(sl.dbuf, row, r->A, sizeof(double) * r->lda, row, n, cudaMemcpyHostToDevice, s);
+      e = copy_matrix(sl.dbuf, n, r->A, r->lda, n, cudaMemcpyHostToDevice, s);
     X = sl.dbuf;
     ld = n;
   }
@@ -109,7 +109,7 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
   sl.ld = ld;
   sl.dev_ms = 0.f;
   if (st == BLOCKINV_OK && r->host)
-    e = cudaMemcpy2DAsync(r->A, sizeof(double) * r->lda, sl.dbuf, row, row, n, cudaMemcpyDeviceToHost, s);
+    e = copy_matrix(r->A, r->lda, sl.dbuf, n, n, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaEventRecord(sl.ev1, s);
   sl.enqueue_status = (st == BLOCKINV_OK && e != cudaSuccess) ? BLOCKINV_ERR_CUDA : st;
@@ -121,12 +121,11 @@ bool fall_back(Slot& sl) {
   Request* r = sl.req;
   cudaStream_t s = sl.s;
   const int n = r->plan.n;
-  const size_t row = sizeof(double) * (size_t)n;
   cudaEventRecord(sl.ev0, s);
   int st = serve_enqueue_fallback(sl.job, r->plan, sl.X, sl.ld, sl.status_dev, s);
   if (st != BLOCKINV_OK) return false;
   if (r->host)
-    cudaMemcpy2DAsync(r->A, sizeof(double) * r->lda, sl.dbuf, row, row, n, cudaMemcpyDeviceToHost, s);
+    copy_matrix(r->A, r->lda, sl.dbuf, n, n, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaEventRecord(sl.ev1, s);
   r->fell_back = true;
