@@ -127,34 +127,34 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-  float rp[PF], rx;
-  auto fetch = [&](int kc) {  // global -> registers
+  // Two chunks in flight: chunk i + 2 is fetched into registers while chunk i
+  // is used, and stashed in shared memory after chunk i + 1 (an L2 round trip
+  // outlasts one chunk's FMAs).
+  struct Regs {
+    float p[PF];
+    float x;
+  };
+  auto fetch = [&](int kc, Regs& g) {  // global -> registers
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
       const int e = tid + q * 256;
       const int r = e / kKc, kk = e - r * kKc;
-      rp[q] = (r < b && kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
+      g.p[q] = (r < b && kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
     }
     const int kk = tid >> 5;
     const int jj = j0 + (tid & 31);
-    rx = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+    g.x = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
   };
-  auto stash = [&](int buf) {  // registers -> shared chunk buf
+  auto stash = [&](int buf, const Regs& g) {  // registers -> shared chunk buf
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
       const int e = tid + q * 256;
       const int r = e / kKc, kk = e - r * kKc;
-      Ps[(buf * kKc + kk) * PLD + r] = rp[q];
+      Ps[(buf * kKc + kk) * PLD + r] = g.p[q];
     }
-    Xs[(buf * kKc + (tid >> 5)) * kCols + (tid & 31)] = rx;
+    Xs[(buf * kKc + (tid >> 5)) * kCols + (tid & 31)] = g.x;
   };
-  fetch(0);
-  stash(0);
-  __syncthreads();
-  int buf = 0;
-  for (int kc = 0; kc < b; kc += kKc, buf ^= 1) {
-    const bool more = kc + kKc < b;
-    if (more) fetch(kc + kKc);  // in flight while this chunk is used
+  auto compute = [&](int buf) {
     const float* P0 = Ps + buf * kKc * PLD;
     const float* X0 = Xs + buf * kKc * kCols;
 #pragma unroll
@@ -182,7 +182,23 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
         acc[r][3] = fmaf(pv[r], xv.w, acc[r][3]);
       }
     }
-    if (more) stash(buf ^ 1);  // the other chunk was last read before the previous barrier
+  };
+  const int nch = (b + kKc - 1) / kKc;
+  Regs ga, gb;
+  fetch(0, ga);
+  if (nch > 1) fetch(kKc, gb);
+  stash(0, ga);
+  __syncthreads();
+  // chunk i uses buffer i & 1; ga / gb alternate as the landing registers
+  for (int i = 0; i < nch; i += 2) {
+    if (i + 2 < nch) fetch((i + 2) * kKc, ga);
+    compute(0);
+    if (i + 1 < nch) stash(1, gb);
+    __syncthreads();
+    if (i + 1 >= nch) break;
+    if (i + 3 < nch) fetch((i + 3) * kKc, gb);
+    compute(1);
+    if (i + 2 < nch) stash(0, ga);
     __syncthreads();
   }
 #pragma unroll
