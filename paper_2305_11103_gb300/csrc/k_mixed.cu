@@ -72,7 +72,7 @@ __global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx,
 // rounded, to Vt[j][0..kpad) (zero beyond b). Extra CTAs pack
 // U[i][l] = X32[i][o + l] for rows outside block k (zero elsewhere).
 constexpr int kCols = 32;
-constexpr int kKc = 8;  // k columns of P^-1 per shared-memory chunk (double-buffered)
+constexpr int kKc = 16;  // k columns of P^-1 per shared-memory chunk (double-buffered)
 
 // Operands are stored as `nsl` slices of kpad columns: slice 0 holds the
 // rounded value (hi), slice 1 (if present) the rounded remainder (lo), so
@@ -130,9 +130,10 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
   // Two chunks in flight: chunk i + 2 is fetched into registers while chunk i
   // is used, and stashed in shared memory after chunk i + 1 (an L2 round trip
   // outlasts one chunk's FMAs).
+  constexpr int XF = kKc * kCols / 256;  // strip elements per thread per chunk
   struct Regs {
     float p[PF];
-    float x;
+    float x[XF];
   };
   auto fetch = [&](int kc, Regs& g) {  // global -> registers
 #pragma unroll
@@ -141,9 +142,12 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
       const int r = e / kKc, kk = e - r * kKc;
       g.p[q] = (r < b && kc + kk < b) ? Pinv[(int64_t)r * b + kc + kk] : 0.f;
     }
-    const int kk = tid >> 5;
-    const int jj = j0 + (tid & 31);
-    g.x = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+#pragma unroll
+    for (int q = 0; q < XF; ++q) {
+      const int kk = (tid >> 5) + 8 * q;
+      const int jj = j0 + (tid & 31);
+      g.x[q] = (kc + kk < b && jj < n) ? X[(int64_t)(o + kc + kk) * ldx + jj] : 0.f;
+    }
   };
   auto stash = [&](int buf, const Regs& g) {  // registers -> shared chunk buf
 #pragma unroll
@@ -152,7 +156,8 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
       const int r = e / kKc, kk = e - r * kKc;
       Ps[(buf * kKc + kk) * PLD + r] = g.p[q];
     }
-    Xs[(buf * kKc + (tid >> 5)) * kCols + (tid & 31)] = g.x;
+#pragma unroll
+    for (int q = 0; q < XF; ++q) Xs[(buf * kKc + (tid >> 5) + 8 * q) * kCols + (tid & 31)] = g.x[q];
   };
   auto compute = [&](int buf) {
     const float* P0 = Ps + buf * kKc * PLD;
