@@ -44,25 +44,24 @@ struct OpType<true> {
 };
 
 // ------------------------------------------------------------- casts ------
+// Row by row (a CTA per row at a time), so no element index is divided.
 __global__ void cast_f64_to_f32_kernel(const double* __restrict__ A, int64_t lda, float* __restrict__ X,
                                        int64_t ldx, int n) {
-  const int64_t total = (int64_t)n * ldx;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / ldx;
-    const int64_t j = e - i * ldx;
-    X[e] = (j < n) ? (float)A[i * lda + j] : 0.f;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* a = A + (int64_t)i * lda;
+    float* x = X + (int64_t)i * ldx;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < ldx; j += blockDim.x) x[j] = (j < n) ? (float)a[j] : 0.f;
   }
 }
 
 __global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx, double* __restrict__ A,
                                        int64_t lda, int n) {
-  const int64_t total = (int64_t)n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n;
-    const int64_t j = e - i * n;
-    A[i * lda + j] = (double)X[i * ldx + j];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const float* x = X + (int64_t)i * ldx;
+    double* a = A + (int64_t)i * lda;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < n; j += blockDim.x) a[j] = (double)x[j];
   }
 }
 

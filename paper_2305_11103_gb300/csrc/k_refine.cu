@@ -118,6 +118,8 @@ __device__ __forceinline__ long long fixed_point(double v, int e, int S) {
   return (bits >> 63) ? -q : q;
 }
 
+// E4M3 byte of an integer |d| <= 16 (exact). The hardware conversion is
+// faster here than assembling the byte on the integer pipe (measured).
 __device__ __forceinline__ uint8_t e4m3(int d) {
   return static_cast<uint8_t>(__nv_cvt_float_to_fp8(static_cast<float>(d), __NV_SATFINITE, __NV_E4M3));
 }
@@ -484,15 +486,17 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
 __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n, float* __restrict__ Xop, int Kp,
                                const Ctl* ctl, const int32_t* status) {
   if (halted(ctl, status)) return;
-  const int64_t total = (int64_t)n * n;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / n);
-    const int k = (int)(t - (int64_t)i * n);
-    const double v = X[(int64_t)i * ldx + k];
-    const float hi = tf32_rn(static_cast<float>(v));
-    const float lo = tf32_rn(static_cast<float>(v - static_cast<double>(hi)));
-    Xop[(int64_t)i * 2 * Kp + k] = hi;
-    Xop[(int64_t)i * 2 * Kp + Kp + k] = lo;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {  // row by row: no index division
+    const double* x = X + (int64_t)i * ldx;
+    float* o = Xop + (int64_t)i * 2 * Kp;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const double v = x[k];
+      const float hi = tf32_rn(static_cast<float>(v));
+      const float lo = tf32_rn(static_cast<float>(v - static_cast<double>(hi)));
+      o[k] = hi;
+      o[Kp + k] = lo;
+    }
   }
 }
 
