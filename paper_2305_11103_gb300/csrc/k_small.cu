@@ -8,20 +8,20 @@
 // itself on 2 x 2 sub-blocks. Reciprocals are the 3-FMA estimate-and-correct
 // of fp64_ops.cuh, and the zero / finiteness tests look at bit patterns.
 //
-// Memory: a CTA of 128 threads stages its 128 consecutive matrices through
-// shared memory, so that the global loads and stores are coalesced. Per
-// matrix the kernel moves 2 * 8 n^2 bytes and does about 2 n^3 flops; on
-// GB300 the FP64 pipe (2 DFMA / clock / SM), not HBM, bounds it.
+// Memory: each warp stages 32 consecutive matrices through shared memory,
+// so that the global loads and stores are coalesced. Per matrix the kernel
+// moves 2 * 8 n^2 bytes and does about 2 n^3 flops; on GB300 the FP64 pipe
+// (2 DFMA / clock / SM), not HBM, bounds it.
 #include "fp64_ops.cuh"
 #include "internal.h"
 
 namespace blockinv {
 
-namespace {
+namespace tc {
+int num_sms();  // streaming multiprocessors of the current device
+}  // namespace tc
 
-// 128 matrices per CTA up to order 6, 64 above (the staging buffer stays under 48 KiB).
-template <int N>
-constexpr int small_threads() { return N <= 6 ? 128 : 64; }
+namespace {
 
 // The paper's partition for orders 1..8 (Table 2): N_k = 2^(int(log2 n) - 1)
 // blocks of order 2..4, the remainder given to the last blocks; n <= 3 is one
@@ -194,53 +194,76 @@ __device__ __forceinline__ int run_steps(double (&x)[N][N]) {
   }
 }
 
+// One CTA per SM, each with a contiguous share of the batch in chunks of 32
+// matrices (one per lane); the CTA's warps take its chunks in turn, each
+// staging its chunk through its own slice of shared memory (matrix pitch odd,
+// so the per-lane accesses hit 32 banks). Even shares per SM keep the FP64
+// pipes of all SMs busy to the end (a grid of 128-matrix CTAs left the second
+// of 1.5 waves half empty).
+// warps per CTA: as many as the registers of one SM allow for the order
 template <int N>
-__global__ void __launch_bounds__(small_threads<N>())
-small_batched_kernel(double* __restrict__ A, int64_t count, int32_t* __restrict__ status) {
+__host__ __device__ constexpr int small_warps() { return N <= 5 ? 24 : (N <= 7 ? 16 : 8); }
+
+template <int N>
+__global__ void __launch_bounds__(32 * small_warps<N>())
+small_batched_kernel(double* __restrict__ A, int64_t count, int32_t* __restrict__ status, int64_t per_cta) {
   constexpr int NN = N * N;
-  constexpr int kSmallThreads = small_threads<N>();
-  __shared__ double stage[kSmallThreads * NN + 1];
-  const int64_t m0 = (int64_t)blockIdx.x * kSmallThreads;
-  const int64_t left = count - m0;
-  const int cnt = left < kSmallThreads ? (int)left : kSmallThreads;
-  if (cnt <= 0) return;
-  double* g = A + m0 * NN;
-  for (int e = threadIdx.x; e < cnt * NN; e += kSmallThreads) stage[e] = g[e];
-  __syncthreads();
-  const int t = threadIdx.x;
-  if (t < cnt) {
-    double x[N][N];
-    bool finite = true;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        x[i][j] = stage[t * NN + i * N + j];
-        finite = finite && !nonfinite_bits(x[i][j]);
-      }
-    int code = BLOCKINV_OK;
-    if (!finite) {
-      code = BLOCKINV_ERR_NONFINITE;
-    } else if (run_steps<N, 0, 0>(x) >= 0) {
-      code = BLOCKINV_ERR_SINGULAR;
-    }
-    if (code == BLOCKINV_OK) {
+  constexpr int PITCH = NN | 1;
+  extern __shared__ double stage_all[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* stage = stage_all + (size_t)warp * 32 * PITCH;
+  const int64_t nchunks = (count + 31) / 32;
+  const int64_t c0 = (int64_t)blockIdx.x * per_cta;
+  const int64_t c1 = min(nchunks, c0 + per_cta);
+  for (int64_t c = c0 + warp; c < c1; c += small_warps<N>()) {
+    const int64_t m0 = c * 32;
+    const int cnt = (int)(count - m0 < 32 ? count - m0 : 32);
+    double* g = A + m0 * NN;
+    for (int e = lane; e < cnt * NN; e += 32) stage[(e / NN) * PITCH + e % NN] = g[e];
+    __syncwarp();
+    if (lane < cnt) {
+      double* mine = stage + lane * PITCH;
+      double x[N][N];
+      bool finite = true;
 #pragma unroll
       for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int j = 0; j < N; ++j) stage[t * NN + i * N + j] = x[i][j];
+        for (int j = 0; j < N; ++j) {
+          x[i][j] = mine[i * N + j];
+          finite = finite && !nonfinite_bits(x[i][j]);
+        }
+      int code = BLOCKINV_OK;
+      if (!finite) {
+        code = BLOCKINV_ERR_NONFINITE;
+      } else if (run_steps<N, 0, 0>(x) >= 0) {
+        code = BLOCKINV_ERR_SINGULAR;
+      }
+      if (code == BLOCKINV_OK) {  // a failed matrix keeps its input
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+          for (int j = 0; j < N; ++j) mine[i * N + j] = x[i][j];
+      }
+      if (status) status[m0 + lane] = code;
     }
-    if (status) status[m0 + t] = code;
+    __syncwarp();
+    for (int e = lane; e < cnt * NN; e += 32) g[e] = stage[(e / NN) * PITCH + e % NN];
+    __syncwarp();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < cnt * NN; e += kSmallThreads) g[e] = stage[e];
 }
 
 template <int N>
 cudaError_t launch_small_n(double* A, int64_t count, int32_t* status, cudaStream_t s) {
-  constexpr int T = small_threads<N>();
-  const int64_t grid = (count + T - 1) / T;
-  small_batched_kernel<N><<<(unsigned)grid, T, 0, s>>>(A, count, status);
+  const int grid = tc::num_sms();
+  const int64_t nchunks = (count + 31) / 32;
+  const int64_t per_cta = (nchunks + grid - 1) / grid;
+  const size_t smem = sizeof(double) * small_warps<N>() * 32 * (size_t)((N * N) | 1);
+  auto k = small_batched_kernel<N>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, 32 * small_warps<N>(), smem, s>>>(A, count, status, per_cta);
   return cudaGetLastError();
 }
 
