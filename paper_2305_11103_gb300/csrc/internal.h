@@ -98,6 +98,14 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
 cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
                                      int block_index, float cond_limit, int32_t* gate, int32_t* count,
                                      cudaStream_t s);
+// Its two halves: the estimate (one CTA; with after_trigger launched as the
+// programmatic dependent of the kernel before it, whose completion it awaits
+// and whose own dependent it lets start at once), and the gated FP64 inverse.
+cudaError_t launch_pivot_cond(const float* P, int64_t ldp, int b, const float* Pinv, int64_t ldo,
+                              const int32_t* status, float cond_limit, int32_t* gate, int32_t* count,
+                              bool after_trigger, cudaStream_t s);
+cudaError_t launch_pivot_f64_gated(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
+                                   int block_index, const int32_t* gate, cudaStream_t s);
 
 // CTAs (hence SMs) the widest launch of one pivot inverse of order b takes:
 // launch_pivot_inverse with elements of elem bytes, and with f64_check also

@@ -367,14 +367,22 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     TraceScope t("pivot_inverse_f32", 2.0 * bd * bd * bd, 8.0 * bd * bd, s);
     return launch_pivot_inverse<float>(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, s);
   };
-  auto pivot_check = [&](int k) -> cudaError_t {
+  // FP64 arithmetic for the pivot blocks that the condition estimate flags:
+  // the estimate, then the gated FP64 inverse
+  auto pivot_cond = [&](int k, bool after_trigger) -> cudaError_t {
     if (!check) return cudaSuccess;
-    // FP64 arithmetic for the pivot blocks that the condition estimate flags
+    const int o = mp.offs[k], b = mp.sizes[k];
+    const double bd = b;
+    TraceScope t("pivot_cond_estimate", 0, 8.0 * bd * bd, s);
+    return launch_pivot_cond(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, pivot_cond_limit, piv_words,
+                             piv_words + 1, after_trigger, s);
+  };
+  auto pivot_gated = [&](int k) -> cudaError_t {
+    if (!check) return cudaSuccess;
     const int o = mp.offs[k], b = mp.sizes[k];
     const double bd = b;
     TraceScope t("pivot_f64_if_ill", 0, 8.0 * bd * bd, s);
-    return launch_pivot_f64_for_ill(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, pivot_cond_limit,
-                                    piv_words, piv_words + 1, s);
+    return launch_pivot_f64_gated(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, piv_words, s);
   };
   auto schur = [&](int k, int part, int k1, int max_ctas, bool after_trigger) -> cudaError_t {
     const int o = mp.offs[k], b = mp.sizes[k];
@@ -392,14 +400,16 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   };
   // One-step look-ahead: step k's Schur update is split into the next pivot
   // block's square and the rest. The next FP32 pivot inverse follows the
-  // square and starts its programmatic dependent, the rest of the update, at
-  // once: the two share the GPU (the update on as many fewer SMs as the pivot
-  // kernel takes) and touch disjoint data (the pivot reads the square and
-  // writes Pinv, the update leaves both alone). The condition check of the
-  // pivot and the next row panel (which overwrites U and Vt) follow both.
+  // square and starts its programmatic dependent, the condition estimate,
+  // which starts its own, the rest of the update, at once: they share the GPU
+  // (the update on as many fewer SMs as the other two take) and touch disjoint
+  // data (the pivot reads the square and writes Pinv, the estimate reads both
+  // and writes the gate, the update leaves all three alone). The gated FP64
+  // inverse and the next row panel (which overwrites U and Vt) follow.
   const bool ahead = lookahead && p >= 3;
   cudaError_t e = pivot(0);
-  if (e == cudaSuccess) e = pivot_check(0);
+  if (e == cudaSuccess) e = pivot_cond(0, false);
+  if (e == cudaSuccess) e = pivot_gated(0);
   for (int k = 0; k < p && e == cudaSuccess; ++k) {
     const int o = mp.offs[k], b = mp.sizes[k];
     const double bd = b, nd = n, rest = n - b;
@@ -412,13 +422,15 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     if (!ahead || k + 1 == p) {
       e = schur(k, kWhole, -1, 0, false);
       if (e == cudaSuccess && k + 1 < p) e = pivot(k + 1);
+      if (e == cudaSuccess && k + 1 < p) e = pivot_cond(k + 1, false);
     } else {
       e = schur(k, kInside, k + 1, 0, false);
       if (e == cudaSuccess) e = pivot(k + 1);
-      if (e == cudaSuccess)
-        e = schur(k, kOutside, k + 1, tc::num_sms() - pivot_inverse_ctas(mp.sizes[k + 1], 4, false), true);
+      if (e == cudaSuccess) e = pivot_cond(k + 1, true);
+      const int reserve = pivot_inverse_ctas(mp.sizes[k + 1], 4, false) + (check ? 1 : 0);
+      if (e == cudaSuccess) e = schur(k, kOutside, k + 1, tc::num_sms() - reserve, true);
     }
-    if (e == cudaSuccess && k + 1 < p) e = pivot_check(k + 1);
+    if (e == cudaSuccess && k + 1 < p) e = pivot_gated(k + 1);
   }
   return e;
 }

@@ -253,6 +253,10 @@ constexpr int kCondThreads = 1024;
 __global__ void __launch_bounds__(kCondThreads)
 pivot_cond_kernel(const float* __restrict__ P, int64_t ldp, const float* __restrict__ Pinv, int64_t ldo, int b,
                   float limit, int32_t* gate, int32_t* count, const int32_t* status) {
+  // Launched as the programmatic dependent of the pivot inverse: let the
+  // kernel after this one start, then wait for the inverse to be complete.
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ float red[2][kCondThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float mp = 0.f, mi = 0.f;
@@ -1041,13 +1045,32 @@ cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_
   return launch_gj<T, T>(P, ldp, b, Pinv, ldo, status, block_index, nullptr, s);
 }
 
+cudaError_t launch_pivot_cond(const float* P, int64_t ldp, int b, const float* Pinv, int64_t ldo,
+                              const int32_t* status, float cond_limit, int32_t* gate, int32_t* count,
+                              bool after_trigger, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1, 1, 1);
+  cfg.blockDim = dim3(kCondThreads, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = after_trigger ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, pivot_cond_kernel, P, ldp, Pinv, ldo, b, cond_limit, gate, count, status);
+}
+
+cudaError_t launch_pivot_f64_gated(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
+                                   int block_index, const int32_t* gate, cudaStream_t s) {
+  return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
+}
+
 cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
                                      int block_index, float cond_limit, int32_t* gate, int32_t* count,
                                      cudaStream_t s) {
-  pivot_cond_kernel<<<1, kCondThreads, 0, s>>>(P, ldp, Pinv, ldo, b, cond_limit, gate, count, status);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pivot_cond(P, ldp, b, Pinv, ldo, status, cond_limit, gate, count, false, s);
   if (e != cudaSuccess) return e;
-  return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
+  return launch_pivot_f64_gated(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
 }
 
 int pivot_inverse_ctas(int b, int elem, bool f64_check) {
