@@ -67,12 +67,12 @@ CPU_SAMPLE_N = 4096
 # it was measured on; reported as null once that source changes.
 NCU_TRAFFIC = {
     # 6144 capture of one elimination step with look-ahead: the next-block part
-    # (48.3 + 0.3 MB) and the rest (280.6 + 210.2 MB), 5888 x 6144 updated
+    # (48.28 + 0.15 MB) and the rest (278.09 + 206.40 MB), 5888 x 6144 updated
     # elements per step; per launch = the step's total over its two launches,
     # scaled by updated elements to 7936 x 8192 per step at 8192.
-    ("schur_update_f64", "f64_8192"): {"bytes_per_launch": 539.3e6 / 2 * (7936 * 8192) / (5888 * 6144),
-                                       "src": "cffdb51500be5b8d"},
-    ("schur_update_f64", "f64_6144"): {"bytes_per_launch": 539.3e6 / 2, "src": "cffdb51500be5b8d"},
+    ("schur_update_f64", "f64_8192"): {"bytes_per_launch": 532.9e6 / 2 * (7936 * 8192) / (5888 * 6144),
+                                       "src": "1910ef6dd2b79f18"},
+    ("schur_update_f64", "f64_6144"): {"bytes_per_launch": 532.9e6 / 2, "src": "1910ef6dd2b79f18"},
 }
 
 

@@ -70,13 +70,28 @@ __device__ __forceinline__ void row_panel_strip(double* __restrict__ X, int64_t 
         for (int q = 0; q < RPT; ++q) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
       }
     } else {
+      // Rows outside, k inside, with a warp-uniform branch around each row's
+      // FMAs: predicated-off FP64 instructions still occupy this GPU's FP64
+      // pipe (measured), so rows at or past b must be branched over.
       const int nq = b > g ? (b - g + 7) / 8 : 0;  // rows g + 8 q < b of this warp
       const int kn = min(kPanelK, b - kc);
-      for (int kk = 0; kk < kn; ++kk) {
-        const double x = Xs[kk][c];
+      if (kn == kPanelK) {
 #pragma unroll
-        for (int q = 0; q < RPT; ++q)
-          if (q < nq) acc[q] = fma(Ps[kk][g + 8 * q], x, acc[q]);
+        for (int q = 0; q < RPT; ++q) {
+          if (q >= nq) break;
+          double a = acc[q];
+#pragma unroll
+          for (int kk = 0; kk < kPanelK; ++kk) a = fma(Ps[kk][g + 8 * q], Xs[kk][c], a);
+          acc[q] = a;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          if (q >= nq) break;
+          double a = acc[q];
+          for (int kk = 0; kk < kn; ++kk) a = fma(Ps[kk][g + 8 * q], Xs[kk][c], a);
+          acc[q] = a;
+        }
       }
     }
     __syncthreads();
