@@ -153,17 +153,18 @@ tiny_batched_kernel(double* __restrict__ A, int64_t count, TinyPartition part, i
         piv[s] = gl == owner && s == slot;
         alpha[s] = piv[s] ? inv : -x[s][c] * inv;
       }
+      // columns past n: a uniform branch out, since predicated-off FP64
+      // instructions still occupy this GPU's FP64 pipe (measured)
 #pragma unroll
       for (int l = 0; l < NC; ++l) {
-        if (l < n) {
-          double v = x[0][l];
+        if (l >= n) break;
+        double v = x[0][l];
 #pragma unroll
-          for (int s = 1; s < R; ++s)
-            if (slot == s) v = x[s][l];
-          const double pl = __shfl_sync(0xffffffffu, v, wbase + owner);  // pivot row, before this column's update
+        for (int s = 1; s < R; ++s)
+          if (slot == s) v = x[s][l];
+        const double pl = __shfl_sync(0xffffffffu, v, wbase + owner);  // pivot row, before this column's update
 #pragma unroll
-          for (int s = 0; s < R; ++s) x[s][l] = (l == c) ? alpha[s] : fma(alpha[s], pl, piv[s] ? 0.0 : x[s][l]);
-        }
+        for (int s = 0; s < R; ++s) x[s][l] = (l == c) ? alpha[s] : fma(alpha[s], pl, piv[s] ? 0.0 : x[s][l]);
       }
 #pragma unroll
       for (int s = 0; s < R; ++s)
