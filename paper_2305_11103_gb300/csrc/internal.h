@@ -91,16 +91,15 @@ template <typename T>
 cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
                                  int32_t* status, int block_index, cudaStream_t s);
 
-// Mixed path, after the FP32 pivot inverse Pinv of the FP32 block P: estimate
-// kappa = ||P||_inf ||Pinv||_inf on the device; if kappa > cond_limit (always
-// when cond_limit < 0), set *gate, count the block in *count and invert P again
-// in FP64 arithmetic (FP32 in and out). gate and count are device int32.
-cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
-                                     int block_index, float cond_limit, int32_t* gate, int32_t* count,
-                                     cudaStream_t s);
-// Its two halves: the estimate (one CTA; with after_trigger launched as the
-// programmatic dependent of the kernel before it, whose completion it awaits
-// and whose own dependent it lets start at once), and the gated FP64 inverse.
+// Mixed path, after the FP32 pivot inverse Pinv of the FP32 block P (gate and
+// count are device int32):
+// - launch_pivot_cond estimates kappa = ||P||_inf ||Pinv||_inf on the device
+//   (one CTA); if kappa > cond_limit (always when cond_limit < 0) it sets
+//   *gate and counts the block in *count. With after_trigger it is launched as
+//   the programmatic dependent of the kernel before it, whose completion it
+//   awaits and whose own dependent it lets start at once.
+// - launch_pivot_f64_gated inverts P again in FP64 arithmetic (FP32 in and
+//   out) when *gate is set, and returns at once otherwise.
 cudaError_t launch_pivot_cond(const float* P, int64_t ldp, int b, const float* Pinv, int64_t ldo,
                               const int32_t* status, float cond_limit, int32_t* gate, int32_t* count,
                               bool after_trigger, cudaStream_t s);
@@ -109,7 +108,7 @@ cudaError_t launch_pivot_f64_gated(const float* P, int64_t ldp, int b, float* Pi
 
 // CTAs (hence SMs) the widest launch of one pivot inverse of order b takes:
 // launch_pivot_inverse with elements of elem bytes, and with f64_check also
-// launch_pivot_f64_for_ill.
+// launch_pivot_f64_gated.
 int pivot_inverse_ctas(int b, int elem, bool f64_check);
 
 // K2 (FP64): row panel X[o:o+b, j] <- Pinv X[o:o+b, j] for j outside the
@@ -142,7 +141,7 @@ int mixed_kpad(int bmax);
 // (TF32) or 2 (BF16) bytes per element; nsl = 2 splits each operand into
 // hi + lo and runs the three products hi*hi + hi*lo + lo*hi.
 // pivot_cond_limit: > 0, pivot blocks whose condition estimate exceeds it are
-// inverted again in FP64 arithmetic (launch_pivot_f64_for_ill); < 0, every
+// inverted again in FP64 arithmetic (launch_pivot_cond, launch_pivot_f64_gated); < 0, every
 // block; 0, none. piv_words: device int32[2] (gate, count of FP64 pivots).
 // lookahead: with 3 or more blocks, each next pivot inverse runs beside the
 // rest of the current Schur update (same stream, programmatic dependent

@@ -1065,13 +1065,6 @@ cudaError_t launch_pivot_f64_gated(const float* P, int64_t ldp, int b, float* Pi
   return launch_gj<double, float>(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
 }
 
-cudaError_t launch_pivot_f64_for_ill(const float* P, int64_t ldp, int b, float* Pinv, int64_t ldo, int32_t* status,
-                                     int block_index, float cond_limit, int32_t* gate, int32_t* count,
-                                     cudaStream_t s) {
-  cudaError_t e = launch_pivot_cond(P, ldp, b, Pinv, ldo, status, cond_limit, gate, count, false, s);
-  if (e != cudaSuccess) return e;
-  return launch_pivot_f64_gated(P, ldp, b, Pinv, ldo, status, block_index, gate, s);
-}
 
 int pivot_inverse_ctas(int b, int elem, bool f64_check) {
   int c = 1, ctas = 0, ncl = 0;
