@@ -201,6 +201,31 @@ def _size_class(n):
     return int(np.floor(np.log2(n)))
 
 
+def test_table_single_block_classes_vs_oracle(bi):
+    """Size classes given one block: their matrices have no Schur tiles at all
+    (the Schur launches count tiles over the rows outside the pivot block)
+    and are inverted by the pivot kernels and the row panel alone."""
+    mats = inputs.uneven_batch(60, 8, 200, 69)
+    ns = [A.shape[0] for A in mats]
+    assert bi.blockinv_batch_tuning_clear() == bi.OK
+    for c in range(3, 8):
+        assert bi.blockinv_batch_tuning_set(c, 1 if c % 2 else 3, 32) == bi.OK
+    try:
+        ts, ptrs, _ = device_batch(mats)
+        st = torch.full((60,), 7, dtype=torch.int32, device="cuda")
+        assert bi.blockinv_invert_batched(ns, None, ptrs, ns, bi.F64, None, st.data_ptr()) == bi.OK
+        torch.cuda.synchronize()
+        assert torch.all(st == 0)
+        parts = []
+        for n in ns:
+            p = 1 if _size_class(n) % 2 else 3
+            q, r = divmod(n, p)
+            parts.append([q + (1 if i >= p - r else 0) for i in range(p)])
+        _check_batch(mats, ts, parts)
+    finally:
+        bi.blockinv_batch_tuning_clear()
+
+
 def test_table_partition_and_32_tiles_vs_oracle(bi):
     """Table entries set by hand: p near-equal blocks and 32 x 32 Schur tiles."""
     mats = inputs.uneven_batch(80, 8, 300, 65)

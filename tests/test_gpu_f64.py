@@ -165,6 +165,20 @@ def test_host_buffer_entry_point(bi):
     check(A, h.numpy(), oracle.block_inverse(A, [200, 200, 200]))
 
 
+def test_host_buffer_padded_rows(bi):
+    """Host rows with a leading dimension above n (the pitched copies), and
+    the padding columns left alone."""
+    n, ld = 520, 531
+    A = inputs.gaussian_shifted(n, 14)
+    big = torch.full((n, ld), 7.25, dtype=torch.float64).pin_memory()
+    big[:, :n] = torch.from_numpy(A)
+    st = bi.blockinv_invert_host(n, [130] * 4, big.data_ptr(), ld, "f64")
+    assert st == bi.OK
+    X = big[:, :n].numpy()
+    check(A, X, oracle.block_inverse(A, [130] * 4))
+    assert torch.all(big[:, n:] == 7.25)
+
+
 def test_async_entry_point_status(bi):
     A = inputs.diag_dominant_uniform(96, 9)
     d = torch.from_numpy(A).cuda()

@@ -188,9 +188,12 @@ def test_full_size_16384_mixed(bi, mode, sigma, seed):
 # unrefined elimination must match the one-step-at-a-time sequence bit for bit,
 # also where block edges cut through tiles (ragged sizes) and in reverse order.
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
-@pytest.mark.parametrize("sizes,order", [([256] * 12, 0), ([200, 312, 256, 300, 212, 200, 300, 316, 300], 0),
-                                         ([256] * 12, 1), ([500, 24, 512, 100, 412, 500], 0)])
-def test_mixed_look_ahead_same_bits(bi, mode, sizes, order):
+@pytest.mark.parametrize("sizes,order,pf", [([256] * 12, 0, 0), ([200, 312, 256, 300, 212, 200, 300, 316, 300], 0, 0),
+                                            ([256] * 12, 1, 0), ([500, 24, 512, 100, 412, 500], 0, 0),
+                                            ([256] * 12, 0, -1), ([256] * 12, 0, 1)])
+def test_mixed_look_ahead_same_bits(bi, mode, sizes, order, pf):
+    # pf: pivot_f64 (0 condition-gated FP64 re-inversion, -1 none: the update
+    # then depends on the pivot kernel directly, 1 every block)
     n = sum(sizes)
     assert n >= 2048
     A = inputs.gaussian_shifted(n, 7 + n, sigma=1.5)
@@ -198,7 +201,7 @@ def test_mixed_look_ahead_same_bits(bi, mode, sizes, order):
     for la in (0, -1):
         d = torch.from_numpy(A).cuda()
         st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, mode, None, max_refine=0, pivot_order=order,
-                                         lookahead=la)
+                                         lookahead=la, pivot_f64=pf)
         assert st == bi.OK
         outs.append(d.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
