@@ -127,15 +127,28 @@ __device__ __forceinline__ uint8_t e4m3(int d) {
 // Balanced base-32 digits of q (|q| <= 2^(5S - 1)), most significant first:
 // d[1..S-1] in [-16, 15], and d[0] in [-16, 16] since the lower digits sum to
 // less than half a unit of the leading one; q = sum_p d[p] 32^(S-1-p).
+// Adding 16 at each of the S - 1 lower digit positions makes those digits
+// plain 5-bit fields (d + 16 in [0, 31], no carries), read with 32-bit shifts;
+// the top digit is what remains above them.
 template <int S>
 __device__ __forceinline__ void digits(long long q, int (&d)[S]) {
+  constexpr long long kBias = 16 * (((1ll << (kLog2Digit * (S - 1))) - 1) / 31);  // 16 * sum_{p < S-1} 32^p
+  const long long qb = q + kBias;
+  const unsigned lo = static_cast<unsigned>(qb);
+  const unsigned hi = static_cast<unsigned>(static_cast<unsigned long long>(qb) >> 32);
 #pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    const int r = static_cast<int>(((q + 16) & 31)) - 16;
-    d[p] = r;
-    q = (q - r) >> kLog2Digit;
+  for (int p = 0; p < S - 1; ++p) {  // field p (from the least significant) is digit S - 1 - p
+    const int sh = kLog2Digit * p;
+    unsigned f;
+    if (sh + kLog2Digit <= 32)
+      f = lo >> sh;
+    else if (sh >= 32)
+      f = hi >> (sh - 32);
+    else
+      f = __funnelshift_r(lo, hi, sh);
+    d[S - 1 - p] = static_cast<int>(f & 31u) - 16;
   }
-  d[0] = static_cast<int>(q);
+  d[0] = static_cast<int>(qb >> (kLog2Digit * (S - 1)));
 }
 
 // ---------------------------------------------------------- scales -------
