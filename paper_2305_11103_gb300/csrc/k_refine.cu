@@ -495,7 +495,31 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
   }
 }
 
-// X split into TF32 hi/lo operands (rows i, columns k and Kp + k).
+// v rounded to 11 significant bits (TF32 precision), half away from zero, as
+// a double, on the integer pipe: add half a unit at bit 41 of the fraction
+// and clear the 42 bits below (a carry into the exponent is the round-up).
+// Zero, subnormal and non-finite v are returned as they are.
+__device__ __forceinline__ double round11(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned ef = static_cast<unsigned>(b >> 52) & 0x7FFu;
+  if (ef == 0 || ef == 0x7FF) return v;
+  return __longlong_as_double(static_cast<long long>((b + (1ull << 41)) & ~((1ull << 42) - 1)));
+}
+
+// A double with at most 24 significant bits as FP32 bits (exact), on the
+// integer pipe; below the FP32 normal range it becomes zero.
+__device__ __forceinline__ float narrow_exact(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const int e = static_cast<int>((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return static_cast<float>(v);
+  return __uint_as_float(sign | (static_cast<unsigned>(e) << 23) | static_cast<unsigned>((b >> 29) & 0x7FFFFFull));
+}
+
+// X split into TF32 hi/lo operands (rows i, columns k and Kp + k): hi = v to
+// 11 significant bits, lo = the remainder (exact in FP64) to 11 bits, so
+// hi + lo carries 22 bits of v; one FP64 subtraction per element.
 __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n, float* __restrict__ Xop, int Kp,
                                const Ctl* ctl, const int32_t* status) {
   if (halted(ctl, status)) return;
@@ -505,10 +529,9 @@ __global__ void split_x_kernel(const double* __restrict__ X, int64_t ldx, int n,
 #pragma unroll 4
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const double v = x[k];
-      const float hi = tf32_rn(static_cast<float>(v));
-      const float lo = tf32_rn(static_cast<float>(v - static_cast<double>(hi)));
-      o[k] = hi;
-      o[Kp + k] = lo;
+      const double hd = round11(v);
+      o[k] = narrow_exact(hd);
+      o[Kp + k] = narrow_exact(round11(v - hd));
     }
   }
 }
