@@ -383,6 +383,11 @@ int blockinv_last_error_detail(int64_t* failing_block);
 /* ABI version: major * 10000 + minor * 100 + patch. */
 int blockinv_version(void);
 
+/* Sizes in bytes of blockinv_options, blockinv_info and blockinv_result as
+ * this library was compiled (any pointer may be NULL), so that a binding can
+ * check its own copies of the structures. Returns BLOCKINV_OK. */
+int blockinv_struct_sizes(int32_t* options_bytes, int32_t* info_bytes, int32_t* result_bytes);
+
 /* Kernel tracing (the library's own profiling hook; not part of the paper's
  * method). blockinv_trace_enable(1) clears and starts recording: every kernel
  * launch of the library is then bracketed by two CUDA events on its stream

@@ -65,6 +65,7 @@ SIGNATURES = {
     "blockinv_status_str": (ctypes.c_char_p, [_int]),
     "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_version": (_int, []),
+    "blockinv_struct_sizes": (_int, [_i32p, _i32p, _i32p]),
     "blockinv_release_memory": (_int, []),
     "blockinv_invert_ex": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp, _vp]),
     "blockinv_diag_gemm": (_int, [_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
@@ -359,6 +360,13 @@ def blockinv_last_error_detail():
 
 def blockinv_version():
     return lib().blockinv_version()
+
+
+def blockinv_struct_sizes():
+    """(sizeof blockinv_options, blockinv_info, blockinv_result) in the library."""
+    o, i, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    lib().blockinv_struct_sizes(ctypes.byref(o), ctypes.byref(i), ctypes.byref(r))
+    return o.value, i.value, r.value
 
 
 def blockinv_trace_enable(on):

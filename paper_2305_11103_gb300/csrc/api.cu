@@ -815,6 +815,13 @@ int blockinv_last_error_detail(int64_t* failing_block) {
 
 int blockinv_version(void) { return 100; }
 
+int blockinv_struct_sizes(int32_t* options_bytes, int32_t* info_bytes, int32_t* result_bytes) {
+  if (options_bytes) *options_bytes = (int32_t)sizeof(blockinv_options);
+  if (info_bytes) *info_bytes = (int32_t)sizeof(blockinv_info);
+  if (result_bytes) *result_bytes = (int32_t)sizeof(blockinv_result);
+  return BLOCKINV_OK;
+}
+
 int blockinv_release_memory(void) {
   cudaMemPool_t pool = nullptr;
   cudaError_t e = workspace_pool(&pool);

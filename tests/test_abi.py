@@ -46,6 +46,15 @@ def test_binding_matches_header():
     assert set(blockinv.SIGNATURES) <= declared_symbols()
 
 
+def test_binding_structs_match_the_library(lib):
+    """The ctypes copies of blockinv_options / blockinv_info / blockinv_result
+    have the sizes the library was compiled with (a field added on one side
+    only would shift every field after it)."""
+    o, i, r = blockinv.blockinv_struct_sizes()
+    assert (o, i, r) == (ctypes.sizeof(blockinv.Options), ctypes.sizeof(blockinv.Info),
+                         ctypes.sizeof(blockinv.Result))
+
+
 def test_status_strings_and_version(lib):
     assert blockinv.blockinv_version() >= 100
     assert blockinv.blockinv_status_str(0) == "ok"
