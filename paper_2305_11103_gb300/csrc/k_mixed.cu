@@ -245,7 +245,18 @@ struct EpiSchurF32 {
   const int32_t* status;
   int part = kWhole;
   int r0 = 0, r1 = 0;
+  // The GEMM moves X's 32 x 32 blocks by TMA and asks value() per element.
+  static constexpr bool kTmaC = true;
   __device__ bool skip() const { return failed(status); }
+  // The new value of X[row][col] from its current value x and the product v
+  // (x itself where this launch writes nothing).
+  __device__ float value(int row, int col, float x, float v) const {
+    if (col >= n) return x;
+    const bool col_in = col >= r0 && col < r1;
+    if (!writes(row, col_in)) return x;
+    const bool pivot_col = col >= o && col < o + b;
+    return (pivot_col ? 0.f : x) - v;
+  }
   __device__ bool writes(int row, bool col_in) const {
     if (row >= n || (row >= o && row < o + b)) return false;
     if (part == kWhole) return true;
@@ -300,8 +311,8 @@ cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const f
 // that cover it), or everything else (kOutside, on at most max_ctas CTAs,
 // with after_trigger as the programmatic dependent of the kernel before it).
 template <tc::Kind K>
-cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float* X, int64_t ldx, int n, int o,
-                            int b, int kpad, int nsl, int32_t* status, cudaStream_t s, int part = kWhole,
+cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const CUtensorMap& tX, float* X, int64_t ldx,
+                            int n, int o, int b, int kpad, int nsl, int32_t* status, cudaStream_t s, int part = kWhole,
                             int o1 = 0, int b1 = 0, int max_ctas = 0, bool after_trigger = false) {
   constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
   const int kb = (b + BK - 1) / BK;
@@ -316,6 +327,7 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, float*
   }
   EpiSchurF32 epi{X, ldx, n, o, b, status, part, o1, o1 + b1};
   tc::Window win;
+  win.c_map = &tX;
   int M = n, N = n;
   if (part == kInside) {
     constexpr int unit_m = 2 * tc::kBM;  // a row unit of the cluster-of-two GEMM
@@ -357,8 +369,12 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   CUtensorMap tU, tV;
   // Vt's box is half a B tile: the two CTAs of a cluster each load one half
   // and multicast it into both
+  // X32 itself in 32 x 32 blocks for the update's epilogue (rows of ld32
+  // floats, a multiple of 128 bytes)
+  CUtensorMap tX;
   if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN / 2))
+      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN / 2) ||
+      !make_tmap_2d(&tX, X32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, n, n, (uint64_t)ld32 * 4, 32, 32))
     return cudaErrorInvalidValue;
   const bool check = pivot_cond_limit != 0.f && piv_words;
   auto pivot = [&](int k) -> cudaError_t {
@@ -393,10 +409,10 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     const char* name = part == kInside ? (bf16 ? "schur_next_block_bf16_tc" : "schur_next_block_tf32_tc")
                                        : (bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc");
     TraceScope t(name, 2.0 * bd * elems * (nsl > 1 ? 3 : 1), 4.0 * 2.0 * elems + eb * 2.0 * nd * bd * nsl, s);
-    return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
-                                                  max_ctas, after_trigger)
-                : launch_schur_tc<tc::Kind::TF32>(tU, tV, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1, b1,
-                                                  max_ctas, after_trigger);
+    return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, tX, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1,
+                                                  b1, max_ctas, after_trigger)
+                : launch_schur_tc<tc::Kind::TF32>(tU, tV, tX, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1,
+                                                  b1, max_ctas, after_trigger);
   };
   // One-step look-ahead: step k's Schur update is split into the next pivot
   // block's square and the rest. The next FP32 pivot inverse follows the

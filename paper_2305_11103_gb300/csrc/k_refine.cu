@@ -283,6 +283,7 @@ slice_cols_t_kernel(const double* __restrict__ X, int64_t ld, int n, const int32
 // accumulator: chunk c of a tile belongs to group g = chunk_group(starts, c)
 // and is added shifted left by 5 (groups - 1 - g) bits; chunk 0 overwrites.
 struct EpiAccumI64 {
+  static constexpr bool kTmaC = false;  // updated through apply_cols
   long long* T;
   int64_t ldt;
   int n;
@@ -314,6 +315,7 @@ struct EpiAccumI64 {
 // the change of X: the first chunk leaves X_old in D, the last one X_new - D
 // (one FP64 rounding of the change).
 struct EpiAddF64 {
+  static constexpr bool kTmaC = false;  // updated through apply_cols
   double* X;
   int64_t ldx;
   int n;

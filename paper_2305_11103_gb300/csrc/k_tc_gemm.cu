@@ -51,6 +51,7 @@ namespace {
 
 // C[row, col] = accumulator (FP32), row-major with leading dimension ldc.
 struct EpiStoreF32 {
+  static constexpr bool kTmaC = false;  // updated through apply_cols
   float* C;
   int64_t ldc;
   int M, N;

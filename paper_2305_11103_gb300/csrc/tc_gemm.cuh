@@ -86,6 +86,7 @@ struct GemmShared {
   uint64_t empty[kStages];
   uint64_t tfull[2];
   uint64_t tempty[2];
+  uint64_t cbar[2 * kEpiWarps];  // kTmaC epilogues: per warp, the TMA loads of its two C-block slots
   uint32_t tmem_base;
 };
 
@@ -97,8 +98,19 @@ constexpr int kStagePitch = 33;
 constexpr size_t kSharedBytes = (sizeof(GemmShared) + 15) / 16 * 16;
 constexpr size_t kEpiStageBytes = sizeof(float) * kEpiWarps * 32 * kStagePitch;
 
-constexpr size_t gemm_smem_bytes() { return (size_t)kStages * kStageBytes + kSharedBytes + kEpiStageBytes + 1024; }
-static_assert(gemm_smem_bytes() <= 227 * 1024, "GEMM shared memory above the per-CTA limit");
+// kTmaC epilogues (the output moved by TMA in 32 x 32 FP32 blocks) keep two
+// 4 KiB C-block slots per epilogue warp, so their GEMMs run 3 operand stages.
+constexpr size_t kTmaCBytes = (size_t)kEpiWarps * 2 * 4096;
+template <bool kTmaC>
+__host__ __device__ constexpr int gemm_stages() { return kTmaC ? 3 : kStages; }
+// Layout after the 1024-aligned base: the operand stages, the epilogue area
+// (1024-aligned), then the barriers.
+template <bool kTmaC = false>
+constexpr size_t gemm_smem_bytes() {
+  return (size_t)gemm_stages<kTmaC>() * kStageBytes + (kTmaC ? kTmaCBytes : kEpiStageBytes) + kSharedBytes + 1024;
+}
+static_assert(gemm_smem_bytes<false>() <= 227 * 1024 && gemm_smem_bytes<true>() <= 227 * 1024,
+              "GEMM shared memory above the per-CTA limit");
 
 __device__ __forceinline__ void flag_timeout(int32_t* status) {
   if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
@@ -120,13 +132,16 @@ __device__ __forceinline__ void item_coords(int t, int units_m, int tiles_n, int
 
 template <Kind K, class Epi, bool kMC = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int tiles_m,
-            int tiles_n, int m_base, int n_base, int dep_wait, KMap km, Epi epi, int32_t* status) {
+gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmC, int tiles_m, int tiles_n, int m_base, int n_base, int dep_wait,
+            KMap km, Epi epi, int32_t* status) {
   constexpr int BK = 128 / KindTraits<K>::elem_bytes;
+  constexpr int kS = gemm_stages<Epi::kTmaC>();  // operand stages of this instance
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  GemmShared* sh = reinterpret_cast<GemmShared*>(smem + kStages * kStageBytes);
+  unsigned char* epi_area = smem + kS * kStageBytes;
+  GemmShared* sh = reinterpret_cast<GemmShared*>(epi_area + (Epi::kTmaC ? kTmaCBytes : kEpiStageBytes));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   // Work items: single tiles, or (kMC) pairs of vertically adjacent tiles per cluster.
@@ -162,7 +177,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (!dep_wait && epi.skip()) return;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kS; ++s) {
       mbar_init(&sh->full[s], 1);
       mbar_init(&sh->empty[s], 1);
     }
@@ -170,8 +185,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mbar_init(&sh->tfull[a], 1);
       mbar_init(&sh->tempty[a], 32 * kEpiWarps);
     }
+    for (int w = 0; w < 2 * kEpiWarps; ++w) mbar_init(&sh->cbar[w], 1);
     if (kMC)
-      for (int s2 = 0; s2 < kStages; ++s2) mbar_init(&sh->empty[s2], 2);  // released by both CTAs
+      for (int s2 = 0; s2 < kS; ++s2) mbar_init(&sh->empty[s2], 2);  // released by both CTAs
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -195,8 +211,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
       const int n0 = n_base + tn * kBN;
       for (int kb = 0; kb < kb_run; ++kb, ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
+        const int s = it % kS;
+        const uint32_t ph = (it / kS) & 1;
         if (!mbar_wait(&sh->empty[s], ph ^ 1)) {
           ok = false;
           break;
@@ -220,11 +236,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     } else if (kMC) {
       // Drain: every stage released by both CTAs, so no late arrival targets a
       // barrier of a CTA that has left (bounded).
-      for (int d = 0; d < kStages; ++d, ++it) mbar_wait(&sh->empty[it % kStages], ((it / kStages) & 1) ^ 1);
+      for (int d = 0; d < kS; ++d, ++it) mbar_wait(&sh->empty[it % kS], ((it / kS) & 1) ^ 1);
     } else if (it > 0) {
       // Let the last copies land before the CTA can leave (bounded).
       const uint32_t last = it - 1;
-      mbar_wait(&sh->full[last % kStages], (last / kStages) & 1);
+      mbar_wait(&sh->full[last % kS], (last / kS) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t id = idesc<K>(kBM, kBN);
@@ -243,8 +259,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const int kb0 = km.nbounds > 0 ? km.bounds[c] : (c < nch_a ? c * kbc : kend);
       const int kb1 = km.nbounds > 0 ? km.bounds[c + 1] : (c < nch_a ? min(kend, kb0 + kbc) : km.kblocks);
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
+        const int s = it % kS;
+        const uint32_t ph = (it / kS) & 1;
         if (!mbar_wait(&sh->full[s], ph)) {
           ok = false;
           break;
@@ -266,7 +282,99 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
     if (!ok) flag_timeout(status);
   } else if (warp >= 2) {
-    float* stage = reinterpret_cast<float*>(smem + kStages * kStageBytes + kSharedBytes) + (warp - 2) * 32 * kStagePitch;
+    if constexpr (Epi::kTmaC) {
+    // The C block of each 32 x 32 accumulator block comes in by TMA into one
+    // of the warp's two slots (the tile's first two while its accumulator is
+    // still being formed, each later one as soon as the block two before it
+    // has gone out), is updated in place (lane = row of the block, as the
+    // accumulator arrives from TMEM; the 128-byte swizzle makes the row's
+    // float4 reads bank-conflict free) and goes back by TMA. Elements the
+    // epilogue must not change are written back as loaded.
+    const int q = warp & 3;  // the TMEM lane quarter this warp may access
+    const int half = (warp - 2) / 4;
+    const int wi = warp - 2;
+    const int cbeg = half * (kBN / 64), cend = cbeg + kBN / 64;
+    uint32_t nload[2] = {0, 0};  // loads per slot: each slot barrier's phase
+    bool ok = true;
+    auto slot_buf = [&](int sl) { return epi_area + (wi * 2 + sl) * 4096; };
+    auto request = [&](int sl, int x, int y) {  // lane 0
+      mbar_arrive_expect_tx(&sh->cbar[wi * 2 + sl], 32 * 32 * 4);
+      tma_load_2d(slot_buf(sl), &tmC, &sh->cbar[wi * 2 + sl], x, y);
+    };
+    uint32_t tl = 0;
+    for (int w = 0; w < nitems && ok; ++w, ++tl) {
+      const int t = first + (w / nch) * stride;
+      const uint32_t a = tl & 1;
+      const uint32_t aph = (tl >> 1) & 1;
+      int um, tn;
+      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
+      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      const int n0 = n_base + tn * kBN;
+      const int row0 = m0 + q * 32;
+      if (lane == 0) {
+        bulk_wait_read_all();  // the previous tile's last stores have left both slots
+        request(0, n0 + cbeg * 32, row0);
+        request(1, n0 + (cbeg + 1) * 32, row0);
+      }
+      int pending = 2;  // requested and not yet waited for, this tile
+      if (!mbar_wait(&sh->tfull[a], aph)) {
+        flag_timeout(status);
+        ok = false;
+      }
+      fence_after_sync();
+#pragma unroll 1
+      for (int c = cbeg; c < cend && ok; ++c) {
+        const int sl = (c - cbeg) & 1;
+        unsigned char* cb = slot_buf(sl);
+        uint32_t v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + c * 32, v);
+        tmem_wait_ld();
+        const bool landed = mbar_wait(&sh->cbar[wi * 2 + sl], nload[sl] & 1);
+        ++nload[sl];
+        --pending;
+        if (!landed) {
+          flag_timeout(status);
+          ok = false;
+          break;
+        }
+        const int col0 = n0 + c * 32;
+        const int row = row0 + lane;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4* p = reinterpret_cast<float4*>(cb + lane * 128 + ((j ^ (lane & 7)) << 4));
+          float4 x = *p;
+          x.x = epi.value(row, col0 + 4 * j + 0, x.x, __uint_as_float(v[4 * j + 0]));
+          x.y = epi.value(row, col0 + 4 * j + 1, x.y, __uint_as_float(v[4 * j + 1]));
+          x.z = epi.value(row, col0 + 4 * j + 2, x.z, __uint_as_float(v[4 * j + 2]));
+          x.w = epi.value(row, col0 + 4 * j + 3, x.w, __uint_as_float(v[4 * j + 3]));
+          *p = x;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          tma_store_2d(&tmC, cb, col0, row0);
+          bulk_commit();
+          if (c + 2 < cend) {
+            bulk_wait_read_all();  // the slot may be refilled
+            request(sl, col0 + 64, row0);
+          }
+        }
+        if (c + 2 < cend) ++pending;
+        __syncwarp();
+      }
+      // after a failure, wait (bounded) for the copies still in flight
+      for (int c = 0; c < pending; ++c) {
+        const int sl = (int)((nload[0] + nload[1]) & 1);
+        mbar_wait(&sh->cbar[wi * 2 + sl], nload[sl] & 1);
+        ++nload[sl];
+      }
+      if (!ok) break;
+      fence_before_sync();
+      mbar_arrive(&sh->tempty[a]);
+    }
+    if (lane == 0) bulk_wait_all();  // every store complete before the CTA can leave
+    } else {
+    float* stage = reinterpret_cast<float*>(epi_area) + (warp - 2) * 32 * kStagePitch;
     const int q = warp & 3;  // the TMEM lane quarter this warp may access
     const int half = (warp - 2) / 4;
     uint32_t tl = 0;
@@ -301,6 +409,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       fence_before_sync();
       mbar_arrive(&sh->tempty[a]);
     }
+    }
   }
   __syncthreads();
   if (kMC) cluster_sync_all();  // the pair leaves together
@@ -331,6 +440,7 @@ struct Window {
   int n_base = 0;
   int max_ctas = 0;
   bool after_trigger = false;
+  const CUtensorMap* c_map = nullptr;  // the output for kTmaC epilogues: 32 x 32 FP32 boxes, 128-byte swizzle
 };
 
 // kMC: tB must have been made with a box of kBN / 2 rows (each CTA of a
@@ -340,19 +450,21 @@ cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int
                         int32_t* status, cudaStream_t s, const Window& win = Window{}) {
   if (win.m_base % (kMC ? 2 * kBM : kBM) != 0 || win.n_base % kBN != 0 || win.max_ctas < 0)
     return cudaErrorInvalidValue;
+  if (Epi::kTmaC && !win.c_map) return cudaErrorInvalidValue;
+  const CUtensorMap tC = win.c_map ? *win.c_map : CUtensorMap{};
   const int ctas = (win.max_ctas > 0 && win.max_ctas < num_sms()) ? win.max_ctas : num_sms();
   const int tiles_m = (M + kBM - 1) / kBM;
   const int tiles_n = (N + kBN - 1) / kBN;
   const int ntiles = tiles_m * tiles_n;
   if (ntiles == 0 || km.kblocks <= 0) return cudaSuccess;
   auto kern = gemm_kernel<K, Epi, kMC>;
-  const size_t smem = gemm_smem_bytes();
+  const size_t smem = gemm_smem_bytes<Epi::kTmaC>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (!kMC) {
     const int grid = ntiles < ctas ? ntiles : ctas;
     if (!win.after_trigger) {
-      kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, 0, km, epi, status);
+      kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 0, km, epi, status);
       return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -365,7 +477,7 @@ cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, 1, km, epi, status);
+    return cudaLaunchKernelEx(&cfg, kern, tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 1, km, epi, status);
   }
   const int pairs = ((tiles_m + 1) / 2) * tiles_n;
   const int clusters = pairs < ctas / 2 ? pairs : (ctas / 2 > 0 ? ctas / 2 : 1);
@@ -383,7 +495,7 @@ cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = win.after_trigger ? 2 : 1;
-  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tiles_m, tiles_n, win.m_base, win.n_base, win.after_trigger ? 1 : 0,
+  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, win.after_trigger ? 1 : 0,
                          km, epi, status);
   return e;
 }
