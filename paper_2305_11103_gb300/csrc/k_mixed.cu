@@ -257,6 +257,18 @@ struct EpiSchurF32 {
     const bool pivot_col = col >= o && col < o + b;
     return (pivot_col ? 0.f : x) - v;
   }
+  // Whether value() changes any element of the 32 x 32 block at (row0, col0):
+  // blocks of pivot rows only, past the matrix, outside the square (kInside)
+  // or wholly inside it (kOutside) are neither loaded nor stored.
+  __device__ bool block_live(int row0, int col0) const {
+    if (row0 >= n || col0 >= n) return false;
+    const int rend = min(row0 + 32, n), cend = min(col0 + 32, n);
+    if (row0 >= o && rend <= o + b) return false;
+    if (part == kWhole) return true;
+    const bool rows_meet = row0 < r1 && rend > r0, cols_meet = col0 < r1 && cend > r0;
+    if (part == kInside) return rows_meet && cols_meet;
+    return !(row0 >= r0 && rend <= r1 && col0 >= r0 && cend <= r1);
+  }
   __device__ bool writes(int row, bool col_in) const {
     if (row >= n || (row >= o && row < o + b)) return false;
     if (part == kWhole) return true;
@@ -330,8 +342,7 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const 
   win.c_map = &tX;
   int M = n, N = n;
   if (part == kInside) {
-    constexpr int unit_m = 2 * tc::kBM;  // a row unit of the cluster-of-two GEMM
-    win.m_base = o1 / unit_m * unit_m;
+    win.m_base = o1 / tc::kBM * tc::kBM;
     win.n_base = o1 / tc::kBN * tc::kBN;
     M = o1 + b1 - win.m_base;
     N = o1 + b1 - win.n_base;
@@ -339,7 +350,7 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const 
     win.max_ctas = max_ctas;
     win.after_trigger = after_trigger;
   }
-  return tc::launch_gemm<K, EpiSchurF32, true>(tU, tV, M, N, km, epi, status, s, win);
+  return tc::launch_gemm<K, EpiSchurF32>(tU, tV, M, N, km, epi, status, s, win);
 }
 
 }  // namespace
@@ -367,13 +378,11 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   const uint32_t BK = 128 / eb;
   const uint64_t w = (uint64_t)nsl * kpad;
   CUtensorMap tU, tV;
-  // Vt's box is half a B tile: the two CTAs of a cluster each load one half
-  // and multicast it into both
   // X32 itself in 32 x 32 blocks for the update's epilogue (rows of ld32
   // floats, a multiple of 128 bytes)
   CUtensorMap tX;
   if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN / 2) ||
+      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN) ||
       !make_tmap_2d(&tX, X32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, n, n, (uint64_t)ld32 * 4, 32, 32))
     return cudaErrorInvalidValue;
   const bool check = pivot_cond_limit != 0.f && piv_words;
@@ -418,10 +427,14 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   // block's square and the rest. The next FP32 pivot inverse follows the
   // square and starts its programmatic dependent, the condition estimate,
   // which starts its own, the rest of the update, at once: they share the GPU
-  // (the update on as many fewer SMs as the other two take) and touch disjoint
-  // data (the pivot reads the square and writes Pinv, the estimate reads both
-  // and writes the gate, the update leaves all three alone). The gated FP64
-  // inverse and the next row panel (which overwrites U and Vt) follow.
+  // (the update on as many fewer SMs as the other two take). The pivot reads
+  // the square and writes Pinv, the estimate reads both and writes the gate.
+  // The rest of the update neither loads nor stores the 32 x 32 blocks of X
+  // that lie wholly inside the square; a block that straddles its edge (a
+  // block order that is not a multiple of 32) is stored back with the
+  // square's bytes as loaded, so the pivot reads the same values either way.
+  // The gated FP64 inverse and the next row panel (which overwrites U and Vt)
+  // follow.
   const bool ahead = lookahead && p >= 3;
   cudaError_t e = pivot(0);
   if (e == cudaSuccess) e = pivot_cond(0, false);

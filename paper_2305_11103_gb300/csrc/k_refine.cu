@@ -32,8 +32,8 @@
 // and the rounding of the fixed-point values leave an error of order
 // 2^(-F) S sqrt(K) relative to the row and column scales.
 //
-// Both products run on the cluster-of-two GEMM that multicasts the shared B
-// tile. The update X += X E uses split TF32 operands (hi + lo for X and E, the
+// Both products run on the persistent tcgen05 GEMM (one CTA per output tile).
+// The update X += X E uses split TF32 operands (hi + lo for X and E, the
 // three products hi*hi + hi*lo + lo*hi) with the FP32 accumulator added to
 // the FP64 X in the epilogue, one K-chunk at a time; E is small, so the
 // correction needs far fewer bits than X itself.
@@ -670,9 +670,9 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
 
   CUtensorMap tAs, tXs, tXo, tEo;
   if (!make_tmap_2d(&tAs, Asl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBM) ||
-      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN / 2) ||
+      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN) ||
       !make_tmap_2d(&tXo, Xop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBM) ||
-      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN / 2))
+      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN))
     return cudaErrorInvalidValue;
 
   const double nd = n;
@@ -710,7 +710,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     km.live_groups = incr_groups ? &ctl->groups : nullptr;
     EpiAccumI64 epi{T, ldt, n, groups, km.group_starts, ctl, status, path};
     TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-    return tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, true>(tAs, tXs, n, n, km, epi, status, s);
+    return tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64>(tAs, tXs, n, n, km, epi, status, s);
   };
   bool next_inc = false;  // host view of ctl->inc (host_steps)
   for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {
@@ -789,7 +789,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       EpiAddF64 epi{X, ldx, n, ctl, status, Dbuf, ldt};
       const double chunks = std::ceil((double)Kp / kUpdateChunkK) + 1.0;
       TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd * chunks + 16.0 * nd * Kp, s);
-      e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true>(tXo, tEo, n, n, km, epi, status, s);
+      e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64>(tXo, tEo, n, n, km, epi, status, s);
     }
   }
   if (e == cudaSuccess && report) {

@@ -24,12 +24,10 @@
 // Every mbarrier wait is bounded; on timeout the status word gets
 // BLOCKINV_ERR_TIMEOUT and the roles wind down.
 //
-// With kMC (TMA multicast) the kernel runs in clusters of two CTAs that own
-// vertically adjacent tiles with the same columns: each CTA loads its own A
-// tile and one half of the shared B tile, multicast into both CTAs, so the
-// L2 reads of B are halved. A stage is reused only after both CTAs' MMAs
-// released it (the MMA warp commits to the empty barriers of both CTAs); the
-// producer drains those releases at the end and the pair leaves together.
+// Each CTA owns whole 128 x 256 output tiles and loads both operand tiles of
+// every k-block itself, by plain TMA tile loads into its own shared memory;
+// consecutive items of a CTA and of its neighbours walk down a group of 16 row tiles
+// before the next column tile, so the B panel they share is read from L2.
 #pragma once
 #include "internal.h"
 #include "tc_common.cuh"
@@ -116,21 +114,33 @@ __device__ __forceinline__ void flag_timeout(int32_t* status) {
   if (status) atomicCAS(&status[0], 0, BLOCKINV_ERR_TIMEOUT);
 }
 
-// Work item t -> (row unit um, column tile tn), row units taken kGroupUnits
+// Work item t -> (row tile um, column tile tn), row tiles taken kGroupRows
 // at a time: consecutive items walk down a group's rows before the next
 // column, so the items in flight together share A and B panels through L2.
-// A row unit is one 128-row tile, or (kMC) a pair of them.
-__device__ __forceinline__ void item_coords(int t, int units_m, int tiles_n, int group, int& um, int& tn) {
-  const int per_group = group * tiles_n;
+constexpr int kGroupRows = 16;
+__device__ __forceinline__ void item_coords(int t, int tiles_m, int tiles_n, int& um, int& tn) {
+  const int per_group = kGroupRows * tiles_n;
   const int g = t / per_group;
-  const int first = g * group;
-  const int gsize = min(units_m - first, group);
+  const int first = g * kGroupRows;
+  const int gsize = min(tiles_m - first, kGroupRows);
   const int r = t - g * per_group;
   um = first + r % gsize;
   tn = r / gsize;
 }
 
-template <Kind K, class Epi, bool kMC = false>
+// The k-th (0-based) set bit of a 4-bit mask.
+__device__ __forceinline__ int nth_set4(uint32_t mask, int k) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (mask & (1u << b)) {
+      if (k == 0) return b;
+      --k;
+    }
+  }
+  return 0;
+}
+
+template <Kind K, class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             const __grid_constant__ CUtensorMap tmC, int tiles_m, int tiles_n, int m_base, int n_base, int dep_wait,
@@ -144,13 +154,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   GemmShared* sh = reinterpret_cast<GemmShared*>(epi_area + (Epi::kTmaC ? kTmaCBytes : kEpiStageBytes));
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  // Work items: single tiles, or (kMC) pairs of vertically adjacent tiles per cluster.
-  const int tiles_mp = kMC ? (tiles_m + 1) / 2 : tiles_m;
-  constexpr int kGroupUnits = kMC ? 8 : 16;  // 16 row tiles per group either way
-  const int ntiles = tiles_mp * tiles_n;
-  const int rank = kMC ? (int)cluster_ctarank() : 0;
-  const int first = kMC ? (int)cluster_id_x() : (int)blockIdx.x;
-  const int stride = kMC ? (int)cluster_count_x() : (int)gridDim.x;
+  const int ntiles = tiles_m * tiles_n;
+  const int first = (int)blockIdx.x;
+  const int stride = (int)gridDim.x;
   // Accumulator hand-offs: each of this CTA's tiles in nch K-chunks (kbc
   // k-blocks each up to kend, then the rest as one), every chunk accumulated
   // from zero and passed to the epilogue.
@@ -171,9 +177,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int my_tiles = first < ntiles ? (ntiles - first + stride - 1) / stride : 0;
   const int nitems = my_tiles * nch;
   // An earlier kernel of this computation failed: the status word it wrote is
-  // the same for every CTA. Not so for a programmatic dependent, whose
-  // predecessor may still be writing it (the two CTAs of a pair could then
-  // disagree), so such a grid always runs to the end.
+  // the same for every CTA. A programmatic dependent runs to the end instead:
+  // its predecessor may still be writing that word, and the dependent's
+  // griddepcontrol.wait at the end is what keeps the stream order.
   if (!dep_wait && epi.skip()) return;
 
   if (threadIdx.x == 0) {
@@ -186,8 +192,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mbar_init(&sh->tempty[a], 32 * kEpiWarps);
     }
     for (int w = 0; w < 2 * kEpiWarps; ++w) mbar_init(&sh->cbar[w], 1);
-    if (kMC)
-      for (int s2 = 0; s2 < kS; ++s2) mbar_init(&sh->empty[s2], 2);  // released by both CTAs
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -196,7 +200,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   }
   fence_before_sync();
   __syncthreads();
-  if (kMC) cluster_sync_all();  // peers may target our barriers only after they exist
   fence_after_sync();
   const uint32_t tmem = sh->tmem_base;
 
@@ -207,8 +210,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     bool ok = true;
     for (int t = first; t < ntiles && ok; t += stride) {
       int um, tn;
-      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
-      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      item_coords(t, tiles_m, tiles_n, um, tn);
+      const int m0 = m_base + um * kBM;
       const int n0 = n_base + tn * kBN;
       for (int kb = 0; kb < kb_run; ++kb, ++it) {
         const int s = it % kS;
@@ -223,20 +226,11 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int pair = kb / km.kb_per_pair;
         const int kk = kb - pair * km.kb_per_pair;
         tma_load_2d(sa, &tmA, &sh->full[s], km.pa[pair] * km.slice_cols + kk * BK, m0);
-        if (kMC) {
-          tma_load_2d_mc(sb + rank * (kBN / 2) * 128, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK,
-                         n0 + rank * (kBN / 2), 0x3);
-        } else {
-          tma_load_2d(sb, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK, n0);
-        }
+        tma_load_2d(sb, &tmB, &sh->full[s], km.pb[pair] * km.slice_cols + kk * BK, n0);
       }
     }
     if (!ok) {
       flag_timeout(status);
-    } else if (kMC) {
-      // Drain: every stage released by both CTAs, so no late arrival targets a
-      // barrier of a CTA that has left (bounded).
-      for (int d = 0; d < kS; ++d, ++it) mbar_wait(&sh->empty[it % kS], ((it / kS) & 1) ^ 1);
     } else if (it > 0) {
       // Let the last copies land before the CTA can leave (bounded).
       const uint32_t last = it - 1;
@@ -272,10 +266,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)  // 4 x 32 bytes of K per 128-byte row
           mma<K>(d, da + 2 * ks, db + 2 * ks, id, ((kb - kb0) | ks) != 0 ? 1u : 0u);
-        if (kMC)
-          mma_commit_mc(&sh->empty[s], 0x3);
-        else
-          mma_commit(&sh->empty[s]);
+        mma_commit(&sh->empty[s]);
       }
       if (!ok) break;
       mma_commit(&sh->tfull[a]);
@@ -288,12 +279,16 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     // still being formed, each later one as soon as the block two before it
     // has gone out), is updated in place (lane = row of the block, as the
     // accumulator arrives from TMEM; the 128-byte swizzle makes the row's
-    // float4 reads bank-conflict free) and goes back by TMA. Elements the
-    // epilogue must not change are written back as loaded.
+    // float4 reads bank-conflict free) and goes back by TMA. Blocks in which
+    // the epilogue changes no element (epi.block_live false) are neither
+    // loaded nor stored; in the others, elements it must not change are
+    // written back as loaded.
+    constexpr int kWarpBlocks = kBN / 64;  // 32-column blocks per warp and tile
+    static_assert(kWarpBlocks <= 4, "live-block mask holds 4 blocks");
     const int q = warp & 3;  // the TMEM lane quarter this warp may access
     const int half = (warp - 2) / 4;
     const int wi = warp - 2;
-    const int cbeg = half * (kBN / 64), cend = cbeg + kBN / 64;
+    const int cbeg = half * kWarpBlocks;
     uint32_t nload[2] = {0, 0};  // loads per slot: each slot barrier's phase
     bool ok = true;
     auto slot_buf = [&](int sl) { return epi_area + (wi * 2 + sl) * 4096; };
@@ -307,37 +302,45 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const uint32_t a = tl & 1;
       const uint32_t aph = (tl >> 1) & 1;
       int um, tn;
-      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
-      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      item_coords(t, tiles_m, tiles_n, um, tn);
+      const int m0 = m_base + um * kBM;
       const int n0 = n_base + tn * kBN;
       const int row0 = m0 + q * 32;
+      uint32_t live = 0;  // this warp's blocks that the epilogue changes
+#pragma unroll
+      for (int c = 0; c < kWarpBlocks; ++c)
+        if (epi.block_live(row0, n0 + (cbeg + c) * 32)) live |= 1u << c;
+      const int nl = __popc(live);
+      auto col_of = [&](int i) { return n0 + (cbeg + nth_set4(live, i)) * 32; };
       if (lane == 0) {
         bulk_wait_read_all();  // the previous tile's last stores have left both slots
-        request(0, n0 + cbeg * 32, row0);
-        request(1, n0 + (cbeg + 1) * 32, row0);
+        if (nl > 0) request(0, col_of(0), row0);
+        if (nl > 1) request(1, col_of(1), row0);
       }
-      int pending = 2;  // requested and not yet waited for, this tile
+      int pending = nl < 2 ? nl : 2;  // requested and not yet waited for, this tile
+      int next = 0;                   // the live block waited for next (slot next & 1)
       if (!mbar_wait(&sh->tfull[a], aph)) {
         flag_timeout(status);
         ok = false;
       }
       fence_after_sync();
 #pragma unroll 1
-      for (int c = cbeg; c < cend && ok; ++c) {
-        const int sl = (c - cbeg) & 1;
+      for (int i = 0; i < nl && ok; ++i) {
+        const int sl = i & 1;
         unsigned char* cb = slot_buf(sl);
+        const int col0 = col_of(i);
         uint32_t v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + c * 32, v);
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + a * kBN + (col0 - n0), v);
         tmem_wait_ld();
-        const bool landed = mbar_wait(&sh->cbar[wi * 2 + sl], nload[sl] & 1);
-        ++nload[sl];
-        --pending;
-        if (!landed) {
+        if (!mbar_wait(&sh->cbar[wi * 2 + sl], nload[sl] & 1)) {
+          // the load is still in flight: the drain below waits for it again
           flag_timeout(status);
           ok = false;
           break;
         }
-        const int col0 = n0 + c * 32;
+        ++nload[sl];
+        --pending;
+        ++next;
         const int row = row0 + lane;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -354,17 +357,17 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (lane == 0) {
           tma_store_2d(&tmC, cb, col0, row0);
           bulk_commit();
-          if (c + 2 < cend) {
+          if (i + 2 < nl) {
             bulk_wait_read_all();  // the slot may be refilled
-            request(sl, col0 + 64, row0);
+            request(sl, col_of(i + 2), row0);
           }
         }
-        if (c + 2 < cend) ++pending;
+        if (i + 2 < nl) ++pending;
         __syncwarp();
       }
       // after a failure, wait (bounded) for the copies still in flight
-      for (int c = 0; c < pending; ++c) {
-        const int sl = (int)((nload[0] + nload[1]) & 1);
+      for (int j = 0; j < pending; ++j) {
+        const int sl = (next + j) & 1;
         mbar_wait(&sh->cbar[wi * 2 + sl], nload[sl] & 1);
         ++nload[sl];
       }
@@ -388,8 +391,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       fence_after_sync();
       int um, tn;
-      item_coords(t, tiles_mp, tiles_n, kGroupUnits, um, tn);
-      const int m0 = m_base + (kMC ? 2 * um + rank : um) * kBM;
+      item_coords(t, tiles_m, tiles_n, um, tn);
+      const int m0 = m_base + um * kBM;
       const int n0 = n_base + tn * kBN;
       const int row0 = m0 + q * 32;
 #pragma unroll 1
@@ -412,7 +415,6 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     }
   }
   __syncthreads();
-  if (kMC) cluster_sync_all();  // the pair leaves together
   if (warp == 0) {
     fence_after_sync();
     tmem_dealloc(tmem, 2 * kBN);
@@ -425,10 +427,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 int num_sms();
 
 // A window of the output: the tiles of rows m_base .. m_base + M - 1 and
-// columns n_base .. n_base + N - 1 (m_base a multiple of kBM, or of 2 kBM
-// with kMC; n_base a multiple of kBN), on at most max_ctas CTAs (0 = one per
-// SM). The tiles are those of the whole product, so every output element is
-// the same sum whichever window computes it.
+// columns n_base .. n_base + N - 1 (m_base a multiple of kBM, n_base a
+// multiple of kBN), on at most max_ctas CTAs (0 = one per SM). The tiles are
+// those of the whole product, so every output element is the same sum
+// whichever window computes it.
 //
 // after_trigger: launch as the programmatic dependent of the previous kernel
 // in the stream, which lets this grid start once every CTA of that kernel has
@@ -443,61 +445,41 @@ struct Window {
   const CUtensorMap* c_map = nullptr;  // the output for kTmaC epilogues: 32 x 32 FP32 boxes, 128-byte swizzle
 };
 
-// kMC: tB must have been made with a box of kBN / 2 rows (each CTA of a
-// pair loads half of the B tile).
-template <Kind K, class Epi, bool kMC = false>
+// tA: box {128 bytes of K, kBM rows}; tB: box {128 bytes of K, kBN rows}.
+template <Kind K, class Epi>
 cudaError_t launch_gemm(const CUtensorMap& tA, const CUtensorMap& tB, int M, int N, KMap km, const Epi& epi,
                         int32_t* status, cudaStream_t s, const Window& win = Window{}) {
-  if (win.m_base % (kMC ? 2 * kBM : kBM) != 0 || win.n_base % kBN != 0 || win.max_ctas < 0)
-    return cudaErrorInvalidValue;
+  if (win.m_base % kBM != 0 || win.n_base % kBN != 0 || win.max_ctas < 0) return cudaErrorInvalidValue;
   if (Epi::kTmaC && !win.c_map) return cudaErrorInvalidValue;
+  // A kTmaC epilogue loads and stores each C block once per tile: K-chunked
+  // hand-offs would reload a block whose store may not be visible yet.
+  if (Epi::kTmaC && (km.chunk_kb > 0 || km.chunk_end > 0 || km.nbounds > 0)) return cudaErrorInvalidValue;
   const CUtensorMap tC = win.c_map ? *win.c_map : CUtensorMap{};
   const int ctas = (win.max_ctas > 0 && win.max_ctas < num_sms()) ? win.max_ctas : num_sms();
   const int tiles_m = (M + kBM - 1) / kBM;
   const int tiles_n = (N + kBN - 1) / kBN;
   const int ntiles = tiles_m * tiles_n;
   if (ntiles == 0 || km.kblocks <= 0) return cudaSuccess;
-  auto kern = gemm_kernel<K, Epi, kMC>;
+  auto kern = gemm_kernel<K, Epi>;
   const size_t smem = gemm_smem_bytes<Epi::kTmaC>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (!kMC) {
-    const int grid = ntiles < ctas ? ntiles : ctas;
-    if (!win.after_trigger) {
-      kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 0, km, epi, status);
-      return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(kGemmThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 1, km, epi, status);
+  const int grid = ntiles < ctas ? ntiles : ctas;
+  if (!win.after_trigger) {
+    kern<<<grid, kGemmThreads, smem, s>>>(tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 0, km, epi, status);
+    return cudaGetLastError();
   }
-  const int pairs = ((tiles_m + 1) / 2) * tiles_n;
-  const int clusters = pairs < ctas / 2 ? pairs : (ctas / 2 > 0 ? ctas / 2 : 1);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * clusters, 1, 1);
+  cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kGemmThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = win.after_trigger ? 2 : 1;
-  e = cudaLaunchKernelEx(&cfg, kern, tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, win.after_trigger ? 1 : 0,
-                         km, epi, status);
-  return e;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, tA, tB, tC, tiles_m, tiles_n, win.m_base, win.n_base, 1, km, epi, status);
 }
 
 }  // namespace tc
