@@ -26,8 +26,12 @@
  *    (A^T)^-1 = (A^-1)^T and the partition is symmetric.
  *  - Device pointers are CUDA device memory of the current device (for
  *    example allocated by PyTorch). The caller owns every buffer it passes;
- *    the library never frees them. Workspace is allocated by the library in
- *    stream order (cudaMallocAsync) and released before the call returns.
+ *    the library never frees them. Workspace comes from a memory pool of the
+ *    library's own per device (cudaMallocFromPoolAsync on the caller's
+ *    stream, freed in stream order before the call returns). The pool keeps
+ *    the memory it has handed out, so repeated solves do not map it again;
+ *    blockinv_release_memory() returns the unused part to the driver. The
+ *    caller's default memory pool is not touched.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
  *  - Argument errors are reported synchronously and leave the matrix
  *    untouched. Numerical errors (a singular or non-finite pivot block) are
@@ -348,6 +352,22 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
  * check the tensor-core path in isolation. */
 int blockinv_diag_gemm(int kind, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,
                        const void* B, int64_t ldb, float* C, int64_t ldc, void* stream);
+
+/* Diagnostic: out[i] = 1 / v[i] by the reciprocal the batched FP64 kernels
+ * use (the hardware estimate and one third-order correction of the series
+ * 1 / v = r / (1 - e), 3 FMAs; within one ulp of the IEEE quotient where v
+ * and 1 / v are normal, the IEEE division elsewhere). count elements, device
+ * pointers, stream-ordered (not blocking). Not part of the paper's method. */
+int blockinv_diag_recip64(const double* v, double* out, int64_t count, void* stream);
+
+/* Diagnostic: one bounded wait on an mbarrier that nothing arrives at, with
+ * the wait function every tensor-core kernel of the library uses, limited to
+ * limit_ns nanoseconds (0 .. 2e9; the kernels themselves use 2e9). When the
+ * limit runs out the kernel records BLOCKINV_ERR_TIMEOUT in a status word
+ * the way those kernels do, and this call returns that status (blocking).
+ * No copy or tensor-core operation is pending when the wait gives up.
+ * Not part of the paper's method: it exercises the timeout path. */
+int blockinv_diag_wait_timeout(int64_t limit_ns, void* stream);
 
 /* rho = ||A X - I||_F / (||A||_F ||X||_F), computed on the GPU with FP64
  * products and sums (device pointers, row-major). The normwise residual used

@@ -69,6 +69,8 @@ SIGNATURES = {
     "blockinv_release_memory": (_int, []),
     "blockinv_invert_ex": (_int, [_i64, _i32, _i32p, _vp, _i64, _int, _vp, _vp, _vp]),
     "blockinv_diag_gemm": (_int, [_int, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp]),
+    "blockinv_diag_recip64": (_int, [_vp, _vp, _i64, _vp]),
+    "blockinv_diag_wait_timeout": (_int, [_i64, _vp]),
     "blockinv_trace_enable": (_int, [_int]),
     "blockinv_trace_summary": (ctypes.c_int64, [ctypes.c_char_p, ctypes.c_int64]),
 }
@@ -161,6 +163,14 @@ def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.
 
 def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None):
     return lib().blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, _stream_ptr(stream))
+
+
+def blockinv_diag_recip64(v_ptr, out_ptr, count, stream=None):
+    return lib().blockinv_diag_recip64(v_ptr, out_ptr, count, _stream_ptr(stream))
+
+
+def blockinv_diag_wait_timeout(limit_ns, stream=None):
+    return lib().blockinv_diag_wait_timeout(limit_ns, _stream_ptr(stream))
 
 
 def blockinv_invert_batched_small(count, n, A_ptr, status_ptr=None, stream=None):

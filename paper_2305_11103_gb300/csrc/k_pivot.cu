@@ -502,6 +502,273 @@ pivot_warp_grouped_kernel(const GroupStep* __restrict__ items, int count) {
 }
 
 // ------------------------------------------------------------------------
+// Look-ahead variant for FP64 blocks of order <= 256 (the FP64 path's pivot
+// blocks). On this GPU the FP64 pipe retires 2 DFMA per clock and SM, so a
+// 256-block (b^3 = 16.8 M DFMA) needs the rows spread over a cluster of up
+// to 16 CTAs; what limits the column loop is then the latency of finding and
+// exchanging each pivot row. Thread j of every CTA holds column j of the
+// CTA's rows (at most kLaRows) in registers, and column c + 1 is eliminated
+// ahead of the rest of column c's update:
+//
+//   1. thread c + 1 applies step c to its column (all local rows), picks the
+//      local candidate for column c + 1 (largest magnitude among rows not
+//      yet used as pivots, lowest row on ties) and leaves the column's values
+//      (the multipliers of step c + 1) in shared memory;
+//   2. every thread applies step c to the candidate row's element in its
+//      column and stores it into the slot of this CTA in every CTA of the
+//      cluster (distributed shared memory); thread c + 1 adds the key
+//      (|value| bits, row) and the reciprocal of the candidate pivot;
+//   3. barrier.cluster.arrive, then step c on every other local row, then
+//      barrier.cluster.wait: the exchange overlaps the bulk of the update;
+//   4. every CTA reduces the keys in its own slots to the same pivot row and
+//      finds the row itself, already scaled by nothing, in that CTA's slot.
+//
+// Slots alternate by column parity, so a slot is rewritten only after every
+// CTA has passed the barrier that follows its last use. The arithmetic of
+// each element is that of pivot_gj_body (the row scaled by the correctly
+// rounded reciprocal, then x - f * scaled), so both kernels give the same
+// bits for the same pivot sequence.
+constexpr int kLaRows = 16;    // local rows per CTA (register arrays)
+constexpr int kLaMaxB = kPivotThreads;  // one column per thread
+
+struct LaKey {
+  unsigned long long vbits;  // |candidate| as FP64 bits (0 with no candidate)
+  int row;                   // global row (INT_MAX with no candidate)
+  int pad;
+  double inv;                // correctly rounded 1 / candidate
+};
+
+struct LaSmem {
+  double* slot;   // [2][C][b]: candidate rows by column parity and CTA
+  LaKey* key;     // [2][C]
+  double* fcol;   // [2][kLaRows]: the next column's values (multipliers)
+  int* perm;      // [b]: pivot row of each column
+  int* misc;      // [0] local candidate row (-1 none), [1] flags of this CTA
+};
+
+__device__ __forceinline__ LaSmem la_layout(unsigned char* raw, int b, int C) {
+  LaSmem m;
+  m.slot = reinterpret_cast<double*>(raw);
+  m.key = reinterpret_cast<LaKey*>(m.slot + 2 * (size_t)C * b);
+  m.fcol = reinterpret_cast<double*>(m.key + 2 * C);
+  m.perm = reinterpret_cast<int*>(m.fcol + 2 * kLaRows);
+  m.misc = m.perm + b;
+  return m;
+}
+
+size_t la_smem_bytes(int b, int C) {
+  return sizeof(double) * 2 * (size_t)C * b + sizeof(LaKey) * 2 * C + sizeof(double) * 2 * kLaRows +
+         sizeof(int) * ((size_t)b + 4) + 16;
+}
+
+__device__ __forceinline__ bool key_better(const LaKey& a, const LaKey& b) {
+  return a.vbits > b.vbits || (a.vbits == b.vbits && a.row < b.row);
+}
+
+// Split cluster barrier (every thread of every CTA; the warp reconverges first).
+__device__ __forceinline__ void cluster_arrive() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kPivotThreads, 1)
+pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __restrict__ out, int64_t ldo,
+                    int32_t* status, int block_index) {
+  // a kernel launched after this one as its programmatic dependent may start
+  // now (it must not touch this block or its inverse)
+  asm volatile("griddepcontrol.launch_dependents;");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  LaSmem m = la_layout(smem_raw, b, C);
+  const int tid = threadIdx.x;
+  const int R = (b + C - 1) / C;  // rows per CTA (<= kLaRows)
+  const int r0 = rank * R;
+  const int nloc = max(0, min(b, r0 + R) - r0);
+  const bool col = tid < b;       // this thread holds column tid
+
+  double x[kLaRows];
+  int bad = 0;
+#pragma unroll
+  for (int r = 0; r < kLaRows; ++r) {
+    x[r] = 0.0;
+    if (col && r < nloc) {
+      x[r] = P[(int64_t)(r0 + r) * ldp + tid];
+      if (!isfinite(x[r])) bad = 1;
+    }
+  }
+  if (tid == 0) m.misc[1] = (*(volatile const int32_t*)&status[0] != 0) ? 2 : 0;
+  __syncthreads();
+  if (bad) atomicOr(&m.misc[1], 1);
+  // every CTA of the cluster is running (peers' shared memory may be
+  // written from here on) and every CTA's flags are set
+  cl.sync();
+  int flags = 0;
+  for (int q = 0; q < C; ++q) flags |= *cl.map_shared_rank(&m.misc[1], q);
+  if (flags) {
+    // the same decision in every CTA: non-finite input, or an earlier kernel failed
+    if ((flags & 1) && !(flags & 2) && rank == 0 && tid == 0)
+      set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
+    cl.sync();
+    return;
+  }
+
+  uint32_t used = 0;  // local rows already used as pivots (same in every thread)
+  // Candidate of column cn from this CTA, with its rows' column cn (x of
+  // thread cn) already up to date: thread cn publishes the multipliers and
+  // the key, every thread pushes its element of the candidate row.
+  auto pick = [&](int cn) {
+    if (tid == cn) {
+      int best = -1;
+      double bv = -1.0;
+#pragma unroll
+      for (int r = 0; r < kLaRows; ++r) {
+        if (r < nloc) {
+          m.fcol[(cn & 1) * kLaRows + r] = x[r];
+          const double a = fabs(x[r]);
+          if (!((used >> r) & 1u) && a > bv) {
+            bv = a;
+            best = r;
+          }
+        }
+      }
+      m.misc[0] = best;
+    }
+  };
+  auto push = [&](int cn, int rs) {
+    // element of the candidate row rs in this thread's column, to every CTA
+    const int par = cn & 1;
+    if (col && rs >= 0) {
+      double v = 0.0;
+#pragma unroll
+      for (int r = 0; r < kLaRows; ++r)
+        if (r == rs) v = x[r];
+      for (int q = 0; q < C; ++q) cl.map_shared_rank(m.slot, q)[((size_t)par * C + rank) * b + tid] = v;
+    }
+    if (tid == cn) {
+      LaKey k;
+      k.vbits = 0ull;
+      k.row = INT_MAX;
+      k.pad = 0;
+      k.inv = 0.0;
+      if (rs >= 0) {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < kLaRows; ++r)
+          if (r == rs) v = x[r];
+        k.vbits = static_cast<unsigned long long>(__double_as_longlong(fabs(v)));
+        k.row = r0 + rs;
+        k.inv = recip(v);
+      }
+      for (int q = 0; q < C; ++q) cl.map_shared_rank(m.key, q)[par * C + rank] = k;
+    }
+  };
+  // the pivot of column cn from the keys in this CTA's slots
+  auto choose = [&](int cn, int& who, LaKey& best) {
+    const int par = cn & 1;
+    best = m.key[par * C];
+    who = 0;
+    for (int q = 1; q < C; ++q) {
+      const LaKey k = m.key[par * C + q];
+      if (key_better(k, best)) {
+        best = k;
+        who = q;
+      }
+    }
+  };
+
+  // column 0: candidates from the input itself
+  pick(0);
+  __syncthreads();
+  push(0, m.misc[0]);
+  cl.sync();
+  int failed = 0;
+  for (int c = 0; c < b; ++c) {
+    int who;
+    LaKey kb;
+    choose(c, who, kb);
+    const double pv = __longlong_as_double(static_cast<long long>(kb.vbits));
+    if (kb.row == INT_MAX || !(pv > 0.0)) {
+      failed = BLOCKINV_ERR_SINGULAR;
+      break;
+    }
+    if (!isfinite(pv) || !isfinite(kb.inv)) {
+      failed = BLOCKINV_ERR_NONFINITE;
+      break;
+    }
+    const int p = kb.row;
+    const int pl = p - r0;  // local index of the pivot row (if this CTA holds it)
+    const bool mine = pl >= 0 && pl < nloc;
+    if (tid == 0) m.perm[c] = p;
+    if (mine) used |= 1u << pl;
+    const double* prow = m.slot + ((size_t)(c & 1) * C + who) * b;
+    const double inv = kb.inv;
+    const double* fc = m.fcol + (c & 1) * kLaRows;
+    double f[kLaRows];
+#pragma unroll
+    for (int r = 0; r < kLaRows; ++r) f[r] = (r < nloc) ? fc[r] : 0.0;
+    // step c on element (r, j) of this thread's column j
+    auto step = [&](int r, double xv, double sj) -> double {
+      if (mine && r == pl) return sj;  // the pivot row, scaled
+      return (tid == c) ? -f[r] * inv : fma(-f[r], sj, xv);
+    };
+    const int cn = c + 1;
+    const bool ahead = cn < b;
+    if (ahead && tid == cn) {
+      const double sj = prow[cn] * inv;
+#pragma unroll
+      for (int r = 0; r < kLaRows; ++r)
+        if (r < nloc) x[r] = step(r, x[r], sj);
+      pick(cn);
+    }
+    __syncthreads();
+    const int rs = ahead ? m.misc[0] : -1;
+    const double sj = col ? ((tid == c) ? inv : prow[tid] * inv) : 0.0;
+    if (ahead) {
+      if (col && tid != cn && rs >= 0) {
+#pragma unroll
+        for (int r = 0; r < kLaRows; ++r)
+          if (r == rs) x[r] = step(r, x[r], sj);
+      }
+      push(cn, rs);
+      cluster_arrive();
+    }
+    if (col && tid != cn) {
+#pragma unroll
+      for (int r = 0; r < kLaRows; ++r)
+        if (r < nloc && r != rs) x[r] = step(r, x[r], sj);
+    }
+    if (ahead) cluster_wait();
+  }
+  // no CTA writes another CTA's shared memory after this barrier
+  cl.sync();
+  if (failed) {
+    if (rank == 0 && tid == 0) set_status(status, failed, block_index);
+    return;
+  }
+  // unscramble: inverse[c][p_j] = a[p_c][j] for the step c at which row p_c was pivot
+  __syncthreads();
+  if (col) {
+    const int pj = m.perm[tid];
+    for (int c = 0; c < b; ++c) {
+      const int pl = m.perm[c] - r0;
+      if (pl >= 0 && pl < nloc) {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < kLaRows; ++r)
+          if (r == pl) v = x[r];
+        out[(int64_t)c * ldo + pj] = v;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
 // Panel-blocked variant for FP32 blocks of order 65..512. The columns are cut
 // into panels of 32, dealt round-robin to the CTAs of a cluster (each CTA
 // keeps its columns for all rows, column-major). For panel k, its owner runs
@@ -1032,9 +1299,56 @@ cudaError_t launch_gj(const TIO* P, int64_t ldp, int b, TIO* Pinv, int64_t ldo, 
                             block_index, gate);
 }
 
+// Cluster size of the look-ahead FP64 kernel: at most kLaRows rows per CTA,
+// about 8 rows per CTA for small blocks (shorter column steps), at most 16.
+int la_ctas(int b) {
+  int c = (b + 7) / 8;
+  if (c > 16) c = 16;
+  while ((b + c - 1) / c > kLaRows) ++c;
+  return c;
+}
+
+cudaError_t launch_pivot_la(const double* P, int64_t ldp, int b, double* Pinv, int64_t ldo, int32_t* status,
+                            int block_index, cudaStream_t s) {
+  const int C = la_ctas(b);
+  if (C > 16 || b > kLaMaxB) return cudaErrorInvalidValue;
+  const size_t smem = la_smem_bytes(b, C);
+  cudaError_t e = set_smem_once<pivot_la_f64_kernel>(smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {  // clusters above the portable 8 CTAs, allowed once per device
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      e = cudaFuncSetAttribute(pivot_la_f64_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(kPivotThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pivot_la_f64_kernel, P, ldp, b, Pinv, ldo, status, block_index);
+}
+
 template <typename T>
 cudaError_t launch_pivot_inverse(const T* P, int64_t ldp, int b, T* Pinv, int64_t ldo,
                                  int32_t* status, int block_index, cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (b <= kLaMaxB) return launch_pivot_la(P, ldp, b, Pinv, ldo, status, block_index, s);
+  }
   if constexpr (sizeof(T) == 4) {
     if (b > 64) {
       bool done = false;
@@ -1070,7 +1384,9 @@ int pivot_inverse_ctas(int b, int elem, bool f64_check) {
   int c = 1, ctas = 0, ncl = 0;
   size_t smem = 0;
   PivotPlan plan;
-  if (elem == 4 && b > 64 && plan_blocked(b, elem, &ctas, &ncl, &smem))
+  if (elem == 8 && b <= kLaMaxB)
+    c = la_ctas(b);
+  else if (elem == 4 && b > 64 && plan_blocked(b, elem, &ctas, &ncl, &smem))
     c = ctas;
   else if (plan_pivot(b, elem, &plan))
     c = plan.ctas;

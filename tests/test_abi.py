@@ -164,3 +164,12 @@ def test_fixed_batched_argument_errors(lib):
     assert f(10, 11, [5, 6], 0x1000, flags=2) == blockinv.ERR_INVALID
     assert f(10, 11, [5, 6], None) == blockinv.ERR_INVALID
     assert f(0, 11, [5, 6], None) == blockinv.OK
+
+
+def test_diagnostic_argument_errors(lib):
+    """The diagnostic entry points reject bad arguments before any CUDA call."""
+    assert blockinv.blockinv_diag_wait_timeout(-1, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_diag_wait_timeout(2_000_000_001, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_diag_recip64(None, None, -1, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_diag_recip64(None, None, 4, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_diag_recip64(None, None, 0, None) == blockinv.OK

@@ -2,16 +2,18 @@
 
 Tolerances. The gate for every result is the normwise residual
 rho = ||A X - I||_F / (||A||_F ||X||_F) <= 1e-12. The error against the oracle,
-eps = ||X - X_oracle||_F / ||X_oracle||_F, is bounded by the forward-error
-estimate c * n * kappa_F(A) * u (u = 2^-53) with c = 4: both sides are
-backward-stable eliminations of the same matrix in different association
-orders. Exact-arithmetic inputs (the unimodular pin) must match bit for bit.
+normwise eps = ||X - X_oracle||_F / ||X_oracle||_F and elementwise
+max |X - X_oracle| / max |X_oracle|, is bounded by 16 sqrt(n) kappa_2(A) u
+(u = 2^-53; see tests/tolerance.py): both sides are eliminations with partial
+pivoting of the same matrix in different association orders.
+Exact-arithmetic inputs (the unimodular pin) must match bit for bit.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2305_11103_gb300 import inputs
+from tolerance import eps_max, eps_norm, fwd_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,20 +49,12 @@ def rho(A, X):
     return np.linalg.norm(A @ X - np.eye(A.shape[0])) / (np.linalg.norm(A) * np.linalg.norm(X))
 
 
-def eps(X, Xo):
-    return np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
-
-
-def eps_bound(A, Xo):
-    n = A.shape[0]
-    kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
-    return 4 * n * kappa * U64
-
-
 def check(A, X, Xo):
-    r, e = rho(A, X), eps(X, Xo)
+    r, e, em = rho(A, X), eps_norm(X, Xo), eps_max(X, Xo)
+    bound = fwd_bound(A, Xo)
     assert r <= RHO_GATE, f"rho {r:.3e}"
-    assert e <= eps_bound(A, Xo), f"eps {e:.3e} > {eps_bound(A, Xo):.3e}"
+    assert e <= bound, f"eps {e:.3e} > {bound:.3e}"
+    assert em <= bound, f"elementwise eps {em:.3e} > {bound:.3e}"
     return r, e
 
 
@@ -248,9 +242,9 @@ def test_look_ahead_ragged_vs_oracle(bi, sizes):
 @pytest.mark.slow
 def test_full_size_8192(bi):
     """n = 8192, 32 x 32 grid of 256-blocks, N(0,1)/sqrt(n) + 1.5 I, seed 2 (the
-    benchmark workload, same launch sequence). The oracle cannot invert it in
-    test time, so: rho on the GPU (FP64) <= 1e-12; sampled rows of A X - I and
-    X A - I in FP64 on the CPU; sampled columns against LAPACK solves."""
+    8192 benchmark workload, same launch sequence): rho on the GPU (FP64), and
+    normwise and elementwise error against the oracle's inverse of the same
+    matrix (about 20 s on 16 host cores)."""
     n = 8192
     A = inputs.gaussian_shifted(n, 2, sigma=1.5)
     dA = torch.from_numpy(A).cuda()
@@ -258,22 +252,8 @@ def test_full_size_8192(bi):
     bi.invert_(dX, [256] * 32)
     assert bi.residual(dA, dX) <= RHO_GATE
     X = dX.cpu().numpy()
-    g = inputs.rng(1234)
-    rows = g.choice(n, size=12, replace=False)
-    nA, nX = np.linalg.norm(A), np.linalg.norm(X)
-    for i in rows:
-        e = A[i] @ X
-        e[i] -= 1.0
-        assert np.linalg.norm(e) * np.sqrt(n) / (nA * nX) <= RHO_GATE
-        f = X[i] @ A
-        f[i] -= 1.0
-        assert np.linalg.norm(f) * np.sqrt(n) / (nA * nX) <= RHO_GATE
-    cols = g.choice(n, size=3, replace=False)
-    E = np.zeros((n, 3))
-    E[cols, range(3)] = 1.0
-    S = np.linalg.solve(A, E)
-    for t, j in enumerate(cols):
-        assert np.linalg.norm(X[:, j] - S[:, t]) / np.linalg.norm(S[:, t]) <= 4 * n * 10 * U64
+    Xo = oracle.block_inverse(A, [256] * 32)
+    check(A, X, Xo)
 
 
 def test_release_memory_then_invert_again(bi):

@@ -52,10 +52,17 @@ def test_noalloc_matches_invert_twice(bi):
 def test_noalloc_limits_and_errors(bi):
     A = inputs.diag_dominant_uniform(64, 73)
     d = torch.from_numpy(A).cuda()
-    # block order above the scratch limit, and a partition that does not sum to n
+    # a single block is fine; an order above the scratch limit (n > 2048) is not
     assert bi.blockinv_invert_noalloc(64, [64], d.data_ptr(), 64, None)[0] == bi.OK
     big = torch.zeros((2049, 2049), dtype=torch.float64, device="cuda")
     assert bi.blockinv_invert_noalloc(2049, [256] * 8 + [1], big.data_ptr(), 2049, None)[0] == bi.ERR_INVALID
+    # a block order above the scratch limit (257 > 256) with n <= 2048 is
+    # rejected and leaves A untouched
+    B = inputs.diag_dominant_uniform(512, 74)
+    g = torch.from_numpy(B).cuda()
+    assert bi.blockinv_invert_noalloc(512, [257, 255], g.data_ptr(), 512, None)[0] == bi.ERR_INVALID
+    assert torch.equal(g.cpu(), torch.from_numpy(B))
+    # a partition that does not sum to n
     e = torch.from_numpy(A).cuda()
     assert bi.blockinv_invert_noalloc(64, [32, 31], e.data_ptr(), 64, None)[0] == bi.ERR_INVALID
     assert torch.equal(e.cpu(), torch.from_numpy(A))
