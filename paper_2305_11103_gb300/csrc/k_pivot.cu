@@ -503,61 +503,67 @@ pivot_warp_grouped_kernel(const GroupStep* __restrict__ items, int count) {
 
 // ------------------------------------------------------------------------
 // Look-ahead variant for FP64 blocks of order <= 256 (the FP64 path's pivot
-// blocks). On this GPU the FP64 pipe retires 2 DFMA per clock and SM, so a
-// 256-block (b^3 = 16.8 M DFMA) needs the rows spread over a cluster of up
-// to 16 CTAs; what limits the column loop is then the latency of finding and
-// exchanging each pivot row. Thread j of every CTA holds column j of the
-// CTA's rows (at most kLaRows) in registers, and column c + 1 is eliminated
-// ahead of the rest of column c's update:
+// blocks). On this GPU the FP64 pipe retires 2 DFMA per clock and SM, and
+// an FP64 warp instruction takes its full pipe slot whatever its active
+// lanes (measured: one thread's 16 FMAs on a column cost about a
+// microsecond). The 256-block (b^3 = 16.8 M DFMA) therefore spreads its rows
+// over a cluster of up to 16 CTAs (at most kLaRows rows each, in shared
+// memory), and the per-column critical path is built from few FP64
+// instructions, every one of them with all its lanes busy:
 //
-//   1. thread c + 1 applies step c to its column (all local rows), picks the
-//      local candidate for column c + 1 (largest magnitude among rows not
-//      yet used as pivots, lowest row on ties) and leaves the column's values
-//      (the multipliers of step c + 1) in shared memory;
-//   2. every thread applies step c to the candidate row's element in its
-//      column and stores it into the slot of this CTA in every CTA of the
-//      cluster (distributed shared memory); thread c + 1 adds the key
-//      (|value| bits, row) and the reciprocal of the candidate pivot;
-//   3. barrier.cluster.arrive, then step c on every other local row, then
-//      barrier.cluster.wait: the exchange overlaps the bulk of the update;
-//   4. every CTA reduces the keys in its own slots to the same pivot row and
-//      finds the row itself, already scaled by nothing, in that CTA's slot.
+//   1. warp 0 applies step c to column c + 1 (lane = local row, one FMA),
+//      takes each lane's reciprocal, and picks the local candidate of column
+//      c + 1 (largest magnitude among rows not yet used as pivots, lowest
+//      row on ties) on the integer pipe from the value's bit pattern;
+//   2. every thread applies step c to the candidate row's element of its
+//      column (one FMA) and stores it into this CTA's slot in every CTA of
+//      the cluster (distributed shared memory); thread 0 adds the key
+//      (|value| bits, row) and the candidate's reciprocal;
+//   3. barrier.cluster.arrive, step c on every other local row (the bulk of
+//      the FP64 work, b x rows FMAs), then barrier.cluster.wait: the
+//      exchange of the next pivot row overlaps the bulk of the update;
+//   4. every CTA reduces the keys in its own slots (integer compares) to the
+//      same pivot row and finds that row, unscaled, in the winner's slot.
 //
-// Slots alternate by column parity, so a slot is rewritten only after every
-// CTA has passed the barrier that follows its last use. The arithmetic of
-// each element is that of pivot_gj_body (the row scaled by the correctly
-// rounded reciprocal, then x - f * scaled), so both kernels give the same
-// bits for the same pivot sequence.
-constexpr int kLaRows = 16;    // local rows per CTA (register arrays)
+// Slots alternate by column parity: a slot is rewritten only after every CTA
+// has passed the barrier that follows its last use. Each element gets
+// x - f * (P[p][j] r) with r the pivot's reciprocal (3 FMAs from the hardware
+// estimate, within an ulp; exact for powers of two), the same arithmetic as
+// the row-split kernel except for that reciprocal.
+constexpr int kLaRows = 16;             // local rows per CTA
 constexpr int kLaMaxB = kPivotThreads;  // one column per thread
 
 struct LaKey {
   unsigned long long vbits;  // |candidate| as FP64 bits (0 with no candidate)
   int row;                   // global row (INT_MAX with no candidate)
   int pad;
-  double inv;                // correctly rounded 1 / candidate
+  double inv;                // reciprocal of the candidate
 };
 
 struct LaSmem {
+  double* rows;   // [kLaRows][b]: this CTA's rows
   double* slot;   // [2][C][b]: candidate rows by column parity and CTA
   LaKey* key;     // [2][C]
-  double* fcol;   // [2][kLaRows]: the next column's values (multipliers)
+  LaKey* cand;    // [1]: this CTA's candidate of the next column
+  double* fbuf;   // [kLaRows]: multipliers of the current step (column c before it)
   int* perm;      // [b]: pivot row of each column
-  int* misc;      // [0] local candidate row (-1 none), [1] flags of this CTA
+  int* misc;      // [0] candidate local row (-1 none), [1] flags of this CTA
 };
 
 __device__ __forceinline__ LaSmem la_layout(unsigned char* raw, int b, int C) {
   LaSmem m;
-  m.slot = reinterpret_cast<double*>(raw);
+  m.rows = reinterpret_cast<double*>(raw);
+  m.slot = m.rows + (size_t)kLaRows * b;
   m.key = reinterpret_cast<LaKey*>(m.slot + 2 * (size_t)C * b);
-  m.fcol = reinterpret_cast<double*>(m.key + 2 * C);
-  m.perm = reinterpret_cast<int*>(m.fcol + 2 * kLaRows);
+  m.cand = m.key + 2 * C;
+  m.fbuf = reinterpret_cast<double*>(m.cand + 1);
+  m.perm = reinterpret_cast<int*>(m.fbuf + kLaRows);
   m.misc = m.perm + b;
   return m;
 }
 
 size_t la_smem_bytes(int b, int C) {
-  return sizeof(double) * 2 * (size_t)C * b + sizeof(LaKey) * 2 * C + sizeof(double) * 2 * kLaRows +
+  return sizeof(double) * ((size_t)kLaRows * b + 2 * (size_t)C * b + kLaRows) + sizeof(LaKey) * (2 * C + 1) +
          sizeof(int) * ((size_t)b + 4) + 16;
 }
 
@@ -575,6 +581,47 @@ __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The reciprocal without the range check of recip64 (the caller checks the
+// winner's exponent): estimate r, e = 1 - v r, r (1 + e + e^2).
+__device__ __forceinline__ double recip_core(double v) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+  const double e = fma(-v, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// Local candidate of column cn from warp 0 (lane = local row): key and
+// reciprocal into m.cand, local row into m.misc[0]. x = the lane's updated
+// value, valid = the lane holds a row not yet used as a pivot.
+__device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, bool valid, int r0) {
+  const unsigned long long ab =
+      valid ? (static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
+  const unsigned hi = static_cast<unsigned>(ab >> 32), lo = static_cast<unsigned>(ab);
+  const double rr = recip_core(x);
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const unsigned win = __reduce_min_sync(0xffffffffu, (valid && hi == mhi && lo == mlo) ? (unsigned)lane : 64u);
+  if (lane == 0 && win == 64u) {
+    LaKey k;
+    k.vbits = 0ull;
+    k.row = INT_MAX;
+    k.pad = 0;
+    k.inv = 0.0;
+    *m.cand = k;
+    m.misc[0] = -1;
+  }
+  if ((unsigned)lane == win) {
+    LaKey k;
+    k.vbits = ab;
+    k.row = r0 + lane;
+    k.pad = 0;
+    const int ef = exp_field(x);
+    k.inv = (ef >= 1 && ef <= 2044) ? rr : 1.0 / x;  // outside the normal range: the division
+    *m.cand = k;
+    m.misc[0] = lane;
+  }
+}
+
 __global__ void __launch_bounds__(kPivotThreads, 1)
 pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __restrict__ out, int64_t ldo,
                     int32_t* status, int block_index) {
@@ -586,22 +633,19 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   LaSmem m = la_layout(smem_raw, b, C);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int R = (b + C - 1) / C;  // rows per CTA (<= kLaRows)
   const int r0 = rank * R;
   const int nloc = max(0, min(b, r0 + R) - r0);
-  const bool col = tid < b;       // this thread holds column tid
+  const bool col = tid < b;       // this thread updates column tid
 
-  double x[kLaRows];
   int bad = 0;
-#pragma unroll
-  for (int r = 0; r < kLaRows; ++r) {
-    x[r] = 0.0;
-    if (col && r < nloc) {
-      x[r] = P[(int64_t)(r0 + r) * ldp + tid];
-      if (!isfinite(x[r])) bad = 1;
+  if (col)
+    for (int r = 0; r < nloc; ++r) {
+      const double v = P[(int64_t)(r0 + r) * ldp + tid];
+      if (nonfinite_bits(v)) bad = 1;
+      m.rows[(size_t)r * b + tid] = v;
     }
-  }
   if (tid == 0) m.misc[1] = (*(volatile const int32_t*)&status[0] != 0) ? 2 : 0;
   __syncthreads();
   if (bad) atomicOr(&m.misc[1], 1);
@@ -618,132 +662,95 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
     return;
   }
 
-  uint32_t used = 0;  // local rows already used as pivots (same in every thread)
-  // Candidate of column cn from this CTA, with its rows' column cn (x of
-  // thread cn) already up to date: thread cn publishes the multipliers and
-  // the key, every thread pushes its element of the candidate row.
-  auto pick = [&](int cn) {
-    if (tid == cn) {
-      int best = -1;
-      double bv = -1.0;
-#pragma unroll
-      for (int r = 0; r < kLaRows; ++r) {
-        if (r < nloc) {
-          m.fcol[(cn & 1) * kLaRows + r] = x[r];
-          const double a = fabs(x[r]);
-          if (!((used >> r) & 1u) && a > bv) {
-            bv = a;
-            best = r;
-          }
-        }
-      }
-      m.misc[0] = best;
-    }
-  };
+  uint32_t used = 0;  // local rows already used as pivots (the same in every thread)
+  // this CTA's candidate of column cn (already up to date in m.rows) to every CTA
   auto push = [&](int cn, int rs) {
-    // element of the candidate row rs in this thread's column, to every CTA
     const int par = cn & 1;
     if (col && rs >= 0) {
-      double v = 0.0;
-#pragma unroll
-      for (int r = 0; r < kLaRows; ++r)
-        if (r == rs) v = x[r];
+      const double v = m.rows[(size_t)rs * b + tid];
       for (int q = 0; q < C; ++q) cl.map_shared_rank(m.slot, q)[((size_t)par * C + rank) * b + tid] = v;
     }
-    if (tid == cn) {
-      LaKey k;
-      k.vbits = 0ull;
-      k.row = INT_MAX;
-      k.pad = 0;
-      k.inv = 0.0;
-      if (rs >= 0) {
-        double v = 0.0;
-#pragma unroll
-        for (int r = 0; r < kLaRows; ++r)
-          if (r == rs) v = x[r];
-        k.vbits = static_cast<unsigned long long>(__double_as_longlong(fabs(v)));
-        k.row = r0 + rs;
-        k.inv = recip(v);
-      }
-      for (int q = 0; q < C; ++q) cl.map_shared_rank(m.key, q)[par * C + rank] = k;
-    }
-  };
-  // the pivot of column cn from the keys in this CTA's slots
-  auto choose = [&](int cn, int& who, LaKey& best) {
-    const int par = cn & 1;
-    best = m.key[par * C];
-    who = 0;
-    for (int q = 1; q < C; ++q) {
-      const LaKey k = m.key[par * C + q];
-      if (key_better(k, best)) {
-        best = k;
-        who = q;
-      }
-    }
+    if (tid < C) cl.map_shared_rank(m.key, tid)[par * C + rank] = *m.cand;
   };
 
   // column 0: candidates from the input itself
-  pick(0);
+  if (warp == 0) {
+    const double x = lane < nloc ? m.rows[(size_t)lane * b] : 0.0;
+    la_pick(m, lane, x, lane < nloc, r0);
+  }
   __syncthreads();
   push(0, m.misc[0]);
   cl.sync();
   int failed = 0;
   for (int c = 0; c < b; ++c) {
-    int who;
-    LaKey kb;
-    choose(c, who, kb);
-    const double pv = __longlong_as_double(static_cast<long long>(kb.vbits));
-    if (kb.row == INT_MAX || !(pv > 0.0)) {
+    // the pivot of column c: the best key in this CTA's slots (integer compares)
+    const int par = c & 1;
+    int who = 0;
+    LaKey kb = m.key[par * C];
+    for (int q = 1; q < C; ++q) {
+      const LaKey k = m.key[par * C + q];
+      if (key_better(k, kb)) {
+        kb = k;
+        who = q;
+      }
+    }
+    const unsigned long long vb = kb.vbits;
+    if (kb.row == INT_MAX || vb == 0ull) {
       failed = BLOCKINV_ERR_SINGULAR;
       break;
     }
-    if (!isfinite(pv) || !isfinite(kb.inv)) {
+    if ((vb >> 52) >= 0x7FFull || nonfinite_bits(kb.inv)) {
       failed = BLOCKINV_ERR_NONFINITE;
       break;
     }
     const int p = kb.row;
-    const int pl = p - r0;  // local index of the pivot row (if this CTA holds it)
+    const int pl = p - r0;  // local index of the pivot row, if this CTA holds it
     const bool mine = pl >= 0 && pl < nloc;
     if (tid == 0) m.perm[c] = p;
     if (mine) used |= 1u << pl;
-    const double* prow = m.slot + ((size_t)(c & 1) * C + who) * b;
+    const double* prow = m.slot + ((size_t)par * C + who) * b;
     const double inv = kb.inv;
-    const double* fc = m.fcol + (c & 1) * kLaRows;
-    double f[kLaRows];
-#pragma unroll
-    for (int r = 0; r < kLaRows; ++r) f[r] = (r < nloc) ? fc[r] : 0.0;
-    // step c on element (r, j) of this thread's column j
-    auto step = [&](int r, double xv, double sj) -> double {
-      if (mine && r == pl) return sj;  // the pivot row, scaled
-      return (tid == c) ? -f[r] * inv : fma(-f[r], sj, xv);
-    };
+    // multipliers: column c of the local rows before step c
+    const double fl = (warp == 0 && lane < nloc) ? m.rows[(size_t)lane * b + c] : 0.0;
+    if (warp == 0 && lane < nloc) m.fbuf[lane] = fl;
     const int cn = c + 1;
     const bool ahead = cn < b;
-    if (ahead && tid == cn) {
-      const double sj = prow[cn] * inv;
-#pragma unroll
-      for (int r = 0; r < kLaRows; ++r)
-        if (r < nloc) x[r] = step(r, x[r], sj);
-      pick(cn);
+    if (ahead && warp == 0) {
+      // step c on column cn (lane = row), then this CTA's candidate of column cn
+      double x = 0.0;
+      bool valid = false;
+      if (lane < nloc) {
+        double* e = m.rows + (size_t)lane * b + cn;
+        const double sj = prow[cn] * inv;
+        x = (mine && lane == pl) ? sj : fma(-fl, sj, *e);
+        *e = x;
+        valid = !((used >> lane) & 1u);
+      }
+      la_pick(m, lane, x, valid, r0);
     }
-    __syncthreads();
+    __syncthreads();  // column cn, the candidate and the multipliers are in shared memory
     const int rs = ahead ? m.misc[0] : -1;
+    // step c on element (r, tid): the pivot row is scaled, column c takes
+    // -f inv, every other element x - f (P[p][tid] inv)
     const double sj = col ? ((tid == c) ? inv : prow[tid] * inv) : 0.0;
     if (ahead) {
       if (col && tid != cn && rs >= 0) {
-#pragma unroll
-        for (int r = 0; r < kLaRows; ++r)
-          if (r == rs) x[r] = step(r, x[r], sj);
+        double* e = m.rows + (size_t)rs * b + tid;
+        *e = fma(-m.fbuf[rs], sj, tid == c ? 0.0 : *e);  // rs is never the pivot row
       }
+      __syncthreads();  // the candidate row is complete
       push(cn, rs);
       cluster_arrive();
     }
     if (col && tid != cn) {
-#pragma unroll
-      for (int r = 0; r < kLaRows; ++r)
-        if (r < nloc && r != rs) x[r] = step(r, x[r], sj);
+      for (int r = 0; r < nloc; ++r) {
+        if (r == rs) continue;
+        double* e = m.rows + (size_t)r * b + tid;
+        *e = (mine && r == pl) ? sj : fma(-m.fbuf[r], sj, tid == c ? 0.0 : *e);
+      }
     }
     if (ahead) cluster_wait();
+    __syncthreads();  // the bulk of step c is in shared memory before column c + 2 is read
   }
   // no CTA writes another CTA's shared memory after this barrier
   cl.sync();
@@ -752,18 +759,11 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
     return;
   }
   // unscramble: inverse[c][p_j] = a[p_c][j] for the step c at which row p_c was pivot
-  __syncthreads();
   if (col) {
     const int pj = m.perm[tid];
     for (int c = 0; c < b; ++c) {
-      const int pl = m.perm[c] - r0;
-      if (pl >= 0 && pl < nloc) {
-        double v = 0.0;
-#pragma unroll
-        for (int r = 0; r < kLaRows; ++r)
-          if (r == pl) v = x[r];
-        out[(int64_t)c * ldo + pj] = v;
-      }
+      const int l = m.perm[c] - r0;
+      if (l >= 0 && l < nloc) out[(int64_t)c * ldo + pj] = m.rows[(size_t)l * b + tid];
     }
   }
 }
