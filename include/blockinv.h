@@ -239,7 +239,7 @@ typedef struct blockinv_ctx blockinv_ctx;
 
 typedef struct {
   int32_t status;        /* final status of the request                     */
-  int32_t mode;
+  int32_t mode;          /* the mode that produced the result (see below)   */
   int64_t n;
   int32_t refine_iters;  /* mixed modes: Newton-Schulz updates              */
   int32_t used_fallback; /* 1: refinement failed, the FP64 path was rerun   */
@@ -252,9 +252,17 @@ typedef struct {
 /* Create a context on `device` (1 <= max_slots <= 64). */
 int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, blockinv_ctx** ctx);
 /* Queue one inversion (arguments as blockinv_invert; A device memory unless
- * flags has BLOCKINV_SUBMIT_HOST). A must stay valid until the request is
- * finished. Returns BLOCKINV_ERR_BUDGET if the request alone exceeds the
- * budget. *ticket identifies the request. */
+ * flags has BLOCKINV_SUBMIT_HOST). A must hold the input when this is called
+ * (the context's streams do not wait for the caller's: finish any copy into
+ * A first) and stay valid until the request is finished. Returns
+ * BLOCKINV_ERR_BUDGET if the request alone exceeds the budget. *ticket
+ * identifies the request.
+ * Requests of order <= 512 are coalesced: at each admission pass every
+ * queued one that fits in the budget (up to 512) is inverted in one batch
+ * job by the grouped FP64 batched engine (partitions and Schur tiles from the
+ * batch autotuner's table unless block_sizes is given), whatever the mode:
+ * at these orders FP64 is faster than the mixed pipeline and exact to FP64
+ * rounding. blockinv_result.mode then reads BLOCKINV_F64. */
 int blockinv_submit(blockinv_ctx* ctx, int64_t n, int32_t p, const int32_t* block_sizes, double* A, int64_t lda,
                     int mode, int flags, uint64_t* ticket);
 /* A mixed-mode request whose refinement does not converge (for example an
@@ -269,6 +277,11 @@ int blockinv_wait(blockinv_ctx* ctx, uint64_t ticket, blockinv_result* out);
 int blockinv_cancel(blockinv_ctx* ctx, uint64_t ticket);
 /* Queued and running request counts and the device bytes admitted. */
 int blockinv_ctx_stats(blockinv_ctx* ctx, int64_t* queued, int64_t* running, size_t* bytes_in_use);
+/* Completion queue: up to max_tickets tickets of requests that finished (or
+ * were cancelled) since they were last reported here, oldest first, into
+ * tickets[]; *count receives how many. Their records are still taken with
+ * blockinv_poll. */
+int blockinv_poll_done(blockinv_ctx* ctx, uint64_t* tickets, int32_t max_tickets, int32_t* count);
 /* Finish running requests, cancel queued ones, release everything. */
 int blockinv_ctx_destroy(blockinv_ctx* ctx);
 
@@ -298,6 +311,25 @@ int blockinv_checkpoint_write(const char* path, int64_t n, int32_t p, const int3
 int blockinv_checkpoint_read(const char* path, int64_t n, int32_t p, const int32_t* block_sizes, double* A,
                              int64_t lda, int32_t* k_done, void* stream);
 
+/* Block-size autotuner of the single-matrix path (and of the serving
+ * context's requests above order 512). For every size class
+ * c = floor(log2 n) among the orders n[count] above 16, it takes the
+ * class's median order m, a synthetic diagonally dominant matrix of that
+ * order (device memory allocated and freed inside), and times blocks of
+ * order 64, 128, 192, 256, 320, 384 and 512 (those <= m; the last block the
+ * remainder) over `reps` inversions in `mode` after one warm-up (1 <= reps
+ * <= 100); the fastest goes into a process-wide table per mode and class.
+ * Calls with p == 0 for n > 16 then use blocks of the tuned order (256 where
+ * the class is untuned). Blocking. Not part of the paper's method: it
+ * chooses among the partitions Eq. (blocking) allows.
+ * blockinv_tuning reads an entry (0 = not tuned), blockinv_tuning_set writes
+ * one (0 clears it), blockinv_tuning_clear forgets all; these three touch no
+ * GPU state. Size classes run from 0 to 20. */
+int blockinv_tune(int32_t count, const int32_t* n, int32_t mode, int32_t reps, void* stream);
+int blockinv_tuning(int32_t mode, int32_t size_class, int32_t* block);
+int blockinv_tuning_set(int32_t mode, int32_t size_class, int32_t block);
+int blockinv_tuning_clear(void);
+
 /* Options and per-call report for blockinv_invert_ex. */
 typedef struct {
   double tol;          /* refinement target for rho (mixed modes); <= 0 means 1e-12     */
@@ -320,6 +352,16 @@ typedef struct {
                        /* pivot inverse (FP64: and row panel) on a high-priority stream  */
                        /* of the library's while the rest of the current Schur update    */
                        /* runs; -1 = one step at a time. The result bits are the same.   */
+  int32_t fuse;        /* mixed modes: 1 = unless lookahead is -1, apply the Schur       */
+                       /* updates of two consecutive elimination steps in one sweep over  */
+                       /* X (a rank b_k + b_{k+1} tensor-core update, after step k has    */
+                       /* updated block row and column k + 1 alone), so that X is loaded  */
+                       /* once for two steps' updates, as the paper's combined up/down    */
+                       /* calculation (Sec. 5.6) avoids reloading blocks; the products   */
+                       /* are summed in another order, so the bits differ. 0 (default) = */
+                       /* one step per sweep (on this GPU the update is bound by the      */
+                       /* tensor-core operand feed, not by moving X, and the second      */
+                       /* step's pivot inverse can no longer overlap an update).         */
 } blockinv_options;
 
 typedef struct {

@@ -45,6 +45,10 @@ SIGNATURES = {
     "blockinv_checkpoint_write": (_int, [ctypes.c_char_p, _i64, _i32, _i32p, _vp, _i64, _i32, _vp]),
     "blockinv_checkpoint_read": (_int, [ctypes.c_char_p, _i64, _i32, _i32p, _vp, _i64, _i32p, _vp]),
     "blockinv_batch_tune": (_int, [_i32, _i32p, _i32, _vp]),
+    "blockinv_tune": (_int, [_i32, _i32p, _i32, _i32, _vp]),
+    "blockinv_tuning": (_int, [_i32, _i32, _i32p]),
+    "blockinv_tuning_set": (_int, [_i32, _i32, _i32]),
+    "blockinv_tuning_clear": (_int, []),
     "blockinv_batch_tuning": (_int, [_i32, _i32p, _i32p]),
     "blockinv_batch_tuning_set": (_int, [_i32, _i32, _i32]),
     "blockinv_batch_tuning_clear": (_int, []),
@@ -58,6 +62,7 @@ SIGNATURES = {
     "blockinv_ctx_stats": (_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "blockinv_ctx_destroy": (_int, [_vp]),
+    "blockinv_poll_done": (_int, [_vp, ctypes.POINTER(ctypes.c_uint64), _i32, ctypes.POINTER(ctypes.c_int32)]),
     "blockinv_invert_noalloc": (_int, [_i64, _i32, _i32p, _vp, _i64, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "blockinv_residual": (_int, [_i64, _vp, _i64, _vp, _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "blockinv_residual_tc": (_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, ctypes.POINTER(ctypes.c_double),
@@ -79,7 +84,7 @@ SIGNATURES = {
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_refine", ctypes.c_int32), ("fallback", ctypes.c_int32),
                 ("split", ctypes.c_int32), ("pivot_f64", ctypes.c_int32), ("pivot_order", ctypes.c_int32),
-                ("singular_fallback", ctypes.c_int32), ("lookahead", ctypes.c_int32)]
+                ("singular_fallback", ctypes.c_int32), ("lookahead", ctypes.c_int32), ("fuse", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -150,11 +155,11 @@ def blockinv_invert_async(n, block_sizes, A_ptr, lda, mode, stream, status_dev_p
 
 
 def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.0, max_refine=-1, fallback=1,
-                       split=0, pivot_f64=0, pivot_order=0, singular_fallback=0, lookahead=0):
+                       split=0, pivot_f64=0, pivot_order=0, singular_fallback=0, lookahead=0, fuse=0):
     """Returns (status, Info)."""
     p, arr, _ = _sizes(block_sizes)
     opt = Options(tol=tol, max_refine=max_refine, fallback=fallback, split=split, pivot_f64=pivot_f64,
-                  pivot_order=pivot_order, singular_fallback=singular_fallback, lookahead=lookahead)
+                  pivot_order=pivot_order, singular_fallback=singular_fallback, lookahead=lookahead, fuse=fuse)
     info = Info()
     st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
                                   ctypes.byref(info))
@@ -227,6 +232,26 @@ def blockinv_checkpoint_read(path, n, block_sizes, A_ptr, lda, stream=None):
 def blockinv_batch_tune(ns, reps=3, stream=None):
     n_arr = (ctypes.c_int32 * len(ns))(*ns)
     return lib().blockinv_batch_tune(len(ns), n_arr, reps, _stream_ptr(stream))
+
+
+def blockinv_tune(ns, mode=F64, reps=3, stream=None):
+    arr = (ctypes.c_int32 * len(ns))(*[int(v) for v in ns])
+    return lib().blockinv_tune(len(ns), arr, _mode(mode), reps, _stream_ptr(stream))
+
+
+def blockinv_tuning(mode, size_class):
+    """(status, block) of one (mode, size class) entry (block 0: not tuned)."""
+    b = ctypes.c_int32(0)
+    st = lib().blockinv_tuning(_mode(mode), size_class, ctypes.byref(b))
+    return st, b.value
+
+
+def blockinv_tuning_set(mode, size_class, block):
+    return lib().blockinv_tuning_set(_mode(mode), size_class, block)
+
+
+def blockinv_tuning_clear():
+    return lib().blockinv_tuning_clear()
 
 
 def blockinv_batch_tuning(size_class):
@@ -305,6 +330,15 @@ class Context:
         r = Result()
         st = lib().blockinv_poll(self.handle, ticket, ctypes.byref(r))
         return st, r
+
+    def poll_done(self, max_tickets=4096):
+        """Tickets of requests finished since the last call (results still taken with poll)."""
+        buf = (ctypes.c_uint64 * max_tickets)()
+        k = ctypes.c_int32(0)
+        st = lib().blockinv_poll_done(self.handle, buf, max_tickets, ctypes.byref(k))
+        if st != OK:
+            raise BlockinvError(st, -1, "blockinv_poll_done")
+        return list(buf[:k.value])
 
     def wait(self, ticket):
         r = Result()

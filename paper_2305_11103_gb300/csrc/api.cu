@@ -45,19 +45,40 @@ bool g_trace_on = false;
 std::vector<TraceRec> g_trace;
 
 
+// Block order of the single-matrix path per mode and size class
+// c = floor(log2 n) chosen by the autotuner (0 = not tuned: kDefaultBlock).
+constexpr int kTuneClasses = 21;
+std::mutex g_block_mu;
+int g_block[3][kTuneClasses] = {};
+
+int order_class(int n) {
+  int c = 0;
+  while (c + 1 < kTuneClasses && (2 << c) <= n) ++c;
+  return c;  // 2^c <= n < 2^(c+1) below the last class
+}
+
+int chosen_block(int n, int mode) {
+  if (mode < 0 || mode > 2) return kDefaultBlock;
+  std::lock_guard<std::mutex> g(g_block_mu);
+  const int b = g_block[mode][order_class(n)];
+  return b > 0 ? b : kDefaultBlock;
+}
+
 // Default partition when the caller passes p == 0. Small orders follow the
 // paper's rule (Table 2: N_k = 2^(int(log2 n) - 1) blocks of order 2..4, the
-// remainder handed to the last blocks); larger ones use blocks of order 256
-// with the last block taking the remainder.
-void default_partition(int n, std::vector<int>* out) {
+// remainder handed to the last blocks); larger ones use blocks of the order
+// the autotuner chose for the mode and size class (256 if untuned), the last
+// block taking the remainder.
+void default_partition(int n, std::vector<int>* out, int mode = BLOCKINV_F64) {
   if (n <= 16) {
     paper_partition(n, out);
     return;
   }
   out->clear();
-  const int p = (n + kDefaultBlock - 1) / kDefaultBlock;
-  out->assign(p, kDefaultBlock);
-  out->back() = n - kDefaultBlock * (p - 1);
+  const int b = std::min(n, chosen_block(n, mode));
+  const int p = (n + b - 1) / b;
+  out->assign(p, b);
+  out->back() = n - b * (p - 1);
 }
 
 }  // namespace
@@ -92,11 +113,12 @@ bool valid_mode(int mode, int64_t n) {
   return (mode == BLOCKINV_MIXED_TF32 || mode == BLOCKINV_MIXED_BF16) && n <= kMixedMaxOrder;
 }
 
-int make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* plan) {
+int make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, Plan* plan,
+              int mode = BLOCKINV_F64) {
   if (n < 1 || n > (int64_t)1 << 20 || lda < n || p < 0 || p > n) return BLOCKINV_ERR_INVALID;
   plan->n = (int)n;
   if (p == 0) {
-    default_partition((int)n, &plan->sizes);
+    default_partition((int)n, &plan->sizes, mode);
   } else {
     if (!block_sizes) return BLOCKINV_ERR_INVALID;
     plan->sizes.assign(block_sizes, block_sizes + p);
@@ -287,6 +309,7 @@ struct Options {
   bool reverse = false;           // pivot blocks last to first (Eq. (d))
   bool singular_fallback = false;  // FP64: retry singular pivots with another order / merged blocks
   bool lookahead = true;           // one-step look-ahead on a side stream (n >= 2048, 3 or more blocks)
+  bool fuse = false;               // mixed: two elimination steps per Schur sweep (option fuse = 1)
 };
 
 // Pivot blocks whose estimate ||P||_inf ||P^-1||_inf exceeds this are inverted
@@ -309,6 +332,7 @@ Options resolve(const blockinv_options* o) {
     r.reverse = o->pivot_order == 1;
     r.singular_fallback = o->singular_fallback != 0;
     r.lookahead = o->lookahead >= 0;
+    r.fuse = r.lookahead && o->fuse > 0;
   }
   return r;
 }
@@ -344,7 +368,7 @@ int spatial_block(const Plan& pl, int k) {
 // Enqueue the mixed-precision elimination of A (overwritten by the FP64 copy
 // of the low-precision inverse).
 int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int nsl, float cond_limit,
-                       int32_t* piv_words, int32_t* status, cudaStream_t s, bool lookahead) {
+                       int32_t* piv_words, int32_t* status, cudaStream_t s, bool lookahead, bool fuse) {
   const int n = pl.n;
   const int64_t ld32 = (n + 31) / 32 * 32;
   const int kpad = mixed_kpad(pl.bmax);
@@ -352,8 +376,9 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int ns
   AsyncBuf x32, pinv, u, vt;
   cudaError_t e = x32.alloc(sizeof(float) * (size_t)n * ld32, s);
   if (e == cudaSuccess) e = pinv.alloc(sizeof(float) * (size_t)pl.bmax * pl.bmax, s);
-  if (e == cudaSuccess) e = u.alloc(eb * (size_t)n * kpad * nsl, s);
-  if (e == cudaSuccess) e = vt.alloc(eb * (size_t)n * kpad * nsl, s);
+  // two slice sets per operand row (the panels of two steps when they are fused)
+  if (e == cudaSuccess) e = u.alloc(eb * (size_t)n * kpad * nsl * 2, s);
+  if (e == cudaSuccess) e = vt.alloc(eb * (size_t)n * kpad * nsl * 2, s);
   if (e != cudaSuccess) return cuda_status(e);
   float* X32 = static_cast<float*>(x32.ptr);
   {
@@ -362,7 +387,7 @@ int enqueue_mixed_elim(const Plan& pl, double* A, int64_t lda, bool bf16, int ns
   }
   if (e == cudaSuccess)
     e = mixed_elimination(pl, bf16, nsl, X32, ld32, static_cast<float*>(pinv.ptr), u.ptr, vt.ptr, cond_limit,
-                          piv_words, status, s, lookahead && n >= 2048);
+                          piv_words, status, s, lookahead && n >= 2048, fuse);
   if (e == cudaSuccess) {
     TraceScope t("cast_f32_to_f64", 0, 12.0 * n * (double)n, s);
     e = launch_cast_f32_to_f64(X32, ld32, A, lda, n, s);
@@ -395,7 +420,7 @@ int enqueue_mixed(const Plan& pl, double* A, int64_t lda, bool bf16, int32_t* st
     e = copy_matrix(ms.a0.ptr, n, A, lda, n, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   int st = enqueue_mixed_elim(pl, A, lda, bf16, opt.split, pivot_cond_limit(opt), static_cast<int32_t*>(ms.piv.ptr),
-                              status, s, opt.lookahead);
+                              status, s, opt.lookahead, opt.fuse);
   if (st != BLOCKINV_OK || opt.max_refine == 0) return st;
   e = ms.ws.alloc(refine_workspace_bytes(n, kResidualSlices, opt.max_refine), s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -478,7 +503,7 @@ struct ServeJob {
 
 int serve_make_plan(int64_t n, int32_t p, const int32_t* block_sizes, int64_t lda, int mode, Plan* pl) {
   if (!valid_mode(mode, n)) return BLOCKINV_ERR_INVALID;
-  return make_plan(n, p, block_sizes, lda, pl);
+  return make_plan(n, p, block_sizes, lda, pl, mode);
 }
 
 size_t serve_footprint(const Plan& pl, int mode) {
@@ -486,7 +511,7 @@ size_t serve_footprint(const Plan& pl, int mode) {
   size_t f = 8 * (b * b + n * b) + 256;
   if (mode != BLOCKINV_F64) {
     const size_t kp = mixed_kpad(pl.bmax);
-    f = 8 * n * n + 4 * n * ((n + 31) / 32 * 32) + 4 * b * b + 2 * 2 * 4 * n * kp +
+    f = 8 * n * n + 4 * n * ((n + 31) / 32 * 32) + 4 * b * b + 2 * 2 * 2 * 4 * n * kp +
         refine_workspace_bytes(pl.n, kResidualSlices, 5) + 4096;
   }
   return f;
@@ -559,7 +584,7 @@ extern "C" {
 int blockinv_invert_async(int64_t n, int32_t p, const int32_t* block_sizes, double* A,
                           int64_t lda, int mode, void* stream, int32_t* status_dev) {
   Plan pl;
-  int st = make_plan(n, p, block_sizes, lda, &pl);
+  int st = make_plan(n, p, block_sizes, lda, &pl, mode);
   if (st != BLOCKINV_OK) return record(st, -1);
   if (!A || !status_dev || !valid_mode(mode, n)) return record(BLOCKINV_ERR_INVALID, -1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -577,7 +602,7 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
     info->rho_initial = -1;
   }
   Plan pl;
-  int st = make_plan(n, p, block_sizes, lda, &pl);
+  int st = make_plan(n, p, block_sizes, lda, &pl, mode);
   if (st == BLOCKINV_OK && (!A || !valid_mode(mode, n))) st = BLOCKINV_ERR_INVALID;
   if (st != BLOCKINV_OK) {
     if (info) info->status = st;
@@ -681,7 +706,7 @@ int blockinv_invert(int64_t n, int32_t p, const int32_t* block_sizes, double* A,
 int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, double* A_host,
                          int64_t lda, int mode, void* stream) {
   Plan pl;
-  int st = make_plan(n, p, block_sizes, lda, &pl);
+  int st = make_plan(n, p, block_sizes, lda, &pl, mode);
   if (st != BLOCKINV_OK) return record(st, -1);
   if (!A_host || !valid_mode(mode, n)) return record(BLOCKINV_ERR_INVALID, -1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -702,6 +727,103 @@ int blockinv_invert_host(int64_t n, int32_t p, const int32_t* block_sizes, doubl
   e = copy_matrix(A_host, lda, dbuf.ptr, n, n, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return record(cuda_status(e), -1);
   return finish(status, s);
+}
+
+// ------------------------------------ block-size autotuner (one matrix) --
+// For every size class c = floor(log2 n) among the given orders above 16:
+// the class's median order m, a synthetic diagonally dominant matrix of that
+// order (filled on the device), and each candidate block order b <= m
+// (blocks of b, the last one the remainder) timed over `reps` inversions in
+// `mode` after one warm-up; the fastest goes into the table that the default
+// partition (p == 0) reads.
+int blockinv_tune(int32_t count, const int32_t* n, int32_t mode, int32_t reps, void* stream) {
+  if (count < 1 || !n || reps < 1 || reps > 100 || mode < 0 || mode > 2) return record(BLOCKINV_ERR_INVALID, -1);
+  std::map<int, std::vector<int>> classes;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 1 || n[i] > (1 << 20) || !valid_mode(mode, n[i])) return record(BLOCKINV_ERR_INVALID, -1);
+    if (n[i] > 16) classes[order_class(n[i])].push_back(n[i]);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  static const int kCand[] = {64, 128, 192, 256, 320, 384, 512};
+  EventPair ev;
+  cudaError_t e = cudaEventCreate(&ev.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+  if (e != cudaSuccess) return record(cuda_status(e), -1);
+  for (auto& kv : classes) {
+    std::vector<int>& v = kv.second;
+    std::sort(v.begin(), v.end());
+    const int m = v[v.size() / 2];
+    AsyncBuf src, work, sbuf;
+    e = src.alloc(sizeof(double) * (size_t)m * m, s);
+    if (e == cudaSuccess) e = work.alloc(sizeof(double) * (size_t)m * m, s);
+    if (e == cudaSuccess) e = sbuf.alloc(2 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_fill_diag_dominant(static_cast<double*>(src.ptr), m, 0x5eedull + m, s);
+    if (e != cudaSuccess) return record(cuda_status(e), -1);
+    int32_t* status = static_cast<int32_t*>(sbuf.ptr);
+    int best = 0;
+    float best_ms = 0.f;
+    for (int b : kCand) {
+      if (b > m) break;
+      std::vector<int> part((m + b - 1) / b, b);
+      part.back() = m - b * ((int)part.size() - 1);
+      Plan pl;
+      if (make_plan(m, (int32_t)part.size(), part.data(), m, &pl) != BLOCKINV_OK) continue;
+      float tot = 0.f;
+      bool ok = true;
+      for (int r = 0; r <= reps && ok; ++r) {
+        e = cudaMemcpyAsync(work.ptr, src.ptr, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.a, s);
+        int st = e == cudaSuccess ? enqueue(pl, static_cast<double*>(work.ptr), m, mode, status, s, Options(), nullptr)
+                                  : BLOCKINV_ERR_CUDA;
+        if (st == BLOCKINV_OK) e = cudaEventRecord(ev.b, s);
+        int32_t h[2] = {BLOCKINV_ERR_CUDA, 0};
+        if (st == BLOCKINV_OK && e == cudaSuccess)
+          e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float ms = 0.f;
+        if (st != BLOCKINV_OK || e != cudaSuccess || h[0] != BLOCKINV_OK ||
+            cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess) {
+          ok = false;
+          break;
+        }
+        if (r > 0) tot += ms;
+      }
+      if (e != cudaSuccess) return record(cuda_status(e), -1);
+      if (ok && (best == 0 || tot < best_ms)) {
+        best = b;
+        best_ms = tot;
+      }
+    }
+    if (best > 0) {
+      std::lock_guard<std::mutex> g(g_block_mu);
+      g_block[mode][kv.first] = best;
+    }
+  }
+  return record(BLOCKINV_OK, -1);
+}
+
+int blockinv_tuning(int32_t mode, int32_t size_class, int32_t* block) {
+  if (mode < 0 || mode > 2 || size_class < 0 || size_class >= kTuneClasses || !block) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_block_mu);
+  *block = g_block[mode][size_class];
+  return BLOCKINV_OK;
+}
+
+int blockinv_tuning_set(int32_t mode, int32_t size_class, int32_t block) {
+  if (mode < 0 || mode > 2 || size_class < 0 || size_class >= kTuneClasses || block < 0 ||
+      block > BLOCKINV_MAX_BLOCK)
+    return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_block_mu);
+  g_block[mode][size_class] = block;
+  return BLOCKINV_OK;
+}
+
+int blockinv_tuning_clear(void) {
+  std::lock_guard<std::mutex> g(g_block_mu);
+  for (auto& row : g_block)
+    for (int& b : row) b = 0;
+  return BLOCKINV_OK;
 }
 
 int blockinv_residual(int64_t n, const double* A, int64_t lda, const double* X, int64_t ldx,

@@ -21,6 +21,7 @@
 // from a text file. Plans built without explicit partitions use the table.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -119,8 +120,37 @@ void batch_partition(int n, std::vector<int>* out, int* tile) {
     batch_default_partition(n, out);
 }
 
+namespace {
+
+// One synthetic diagonally dominant matrix of order n for timing (row-major,
+// leading dimension n): a[i][j] in [-1, 1) from a 64-bit mix of (seed, index),
+// plus n on the diagonal.
+__global__ void fill_dd_kernel(double* __restrict__ a, int n, unsigned long long seed) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long z = (seed << 40) ^ static_cast<unsigned long long>(e);
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    const int i = static_cast<int>(e / n), j = static_cast<int>(e - (int64_t)i * n);
+    a[e] = u + (i == j ? static_cast<double>(n) : 0.0);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fill_diag_dominant(double* A, int n, unsigned long long seed, cudaStream_t s) {
+  const int64_t total = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  fill_dd_kernel<<<blocks, 256, 0, s>>>(A, n, seed);
+  return cudaGetLastError();
+}
+
 int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
-                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile, const int* tiles) {
+                      double* const* A, const int64_t* lda, BatchPlan** out, int force_tile, const int* tiles,
+                      cudaStream_t pool_stream, void* staging, size_t* staging_bytes) {
   *out = nullptr;
   if (count < 1 || !n || !A || !lda || (block_sizes && !p)) return BLOCKINV_ERR_INVALID;
   BatchPlan tmp;
@@ -221,9 +251,24 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
   const size_t o_status = o_starts + align256(sizeof(int32_t) * starts.size());
   const size_t o_ws = o_status + align256(sizeof(int32_t) * 2 * count);
   const size_t total = o_ws + ws_total;
+  const size_t tb = sizeof(GroupStep) * items.size(), sb = sizeof(int32_t) * starts.size();
+  if (pool_stream) {  // the caller's pinned staging must hold both tables
+    const size_t need = tb + sb;
+    const size_t cap = staging_bytes ? *staging_bytes : 0;
+    if (staging_bytes) *staging_bytes = need;
+    if (!staging || cap < need) return BLOCKINV_ERR_NOMEM;
+  }
   if (cudaGetDevice(&tmp.device) != cudaSuccess) return BLOCKINV_ERR_CUDA;
   void* dev = nullptr;
-  if (cudaMalloc(&dev, total) != cudaSuccess) return BLOCKINV_ERR_NOMEM;
+  if (pool_stream) {
+    // stream-ordered, from the library's pool (no device-wide synchronisation)
+    cudaMemPool_t pool = nullptr;
+    if (workspace_pool(&pool) != cudaSuccess) return BLOCKINV_ERR_CUDA;
+    if (cudaMallocFromPoolAsync(&dev, total, pool, pool_stream) != cudaSuccess) return BLOCKINV_ERR_NOMEM;
+    tmp.pool_stream = pool_stream;
+  } else if (cudaMalloc(&dev, total) != cudaSuccess) {
+    return BLOCKINV_ERR_NOMEM;
+  }
   char* base = static_cast<char*>(dev);
   tmp.dev = dev;
   tmp.items = reinterpret_cast<GroupStep*>(base + o_items);
@@ -237,13 +282,27 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
     g.status = tmp.status + 2 * m;
     if (g.b > kGroupedMaxB) tmp.steps[g.k].big.push_back(g);
   }
-  cudaError_t e = cudaMemcpy(base + o_items, items.data(), sizeof(GroupStep) * items.size(),
-                             cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + o_starts, starts.data(), sizeof(int32_t) * starts.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(dev);
-    return BLOCKINV_ERR_CUDA;
+  cudaError_t e;
+  if (pool_stream) {
+    // the tables go through the caller's pinned staging, which must stay
+    // untouched until the work on pool_stream has passed these copies
+    memcpy(staging, items.data(), tb);
+    memcpy(static_cast<char*>(staging) + tb, starts.data(), sb);
+    e = cudaMemcpyAsync(base + o_items, staging, tb, cudaMemcpyHostToDevice, pool_stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + o_starts, static_cast<char*>(staging) + tb, sb, cudaMemcpyHostToDevice, pool_stream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(dev, pool_stream);
+      return BLOCKINV_ERR_CUDA;
+    }
+  } else {
+    e = cudaMemcpy(base + o_items, items.data(), sizeof(GroupStep) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(base + o_starts, starts.data(), sizeof(int32_t) * starts.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(dev);
+      return BLOCKINV_ERR_CUDA;
+    }
   }
   *out = new BatchPlan(std::move(tmp));
   return BLOCKINV_OK;
@@ -303,7 +362,12 @@ cudaError_t batch_run(BatchPlan& pl, cudaStream_t s, int32_t* status_out, bool u
 void batch_plan_destroy(BatchPlan* pl) {
   if (!pl) return;
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
-  if (pl->dev) cudaFree(pl->dev);
+  if (pl->dev) {
+    if (pl->pool_stream)
+      cudaFreeAsync(pl->dev, pl->pool_stream);  // after the plan's work on that stream
+    else
+      cudaFree(pl->dev);
+  }
   delete pl;
 }
 

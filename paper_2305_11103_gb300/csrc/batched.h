@@ -32,6 +32,7 @@ struct BatchPlan {
   int32_t* status = nullptr;  // 2 words per matrix
   double flops = 0, bytes = 0;
   cudaGraphExec_t exec = nullptr;
+  cudaStream_t pool_stream = nullptr;  // pooled plans: the stream of their allocation and release
 };
 
 // Partition and Schur tile of a matrix of order n in a batch: the tuned
@@ -41,9 +42,17 @@ void batch_partition(int n, std::vector<int>* out, int* tile);
 void batch_default_partition(int n, std::vector<int>* out);
 // force_tile: 0 = the tile of each matrix's size class (tuned, else 64);
 // tiles (optional): one tile per matrix, overriding both.
+// pool_stream: non-null = the device tables and workspace come from the
+// library's memory pool in that stream's order (no device-wide
+// synchronisation, for the serving loop) and go back to it, in the same
+// order, when the plan is destroyed; the tables are copied from `staging`
+// (pinned, *staging_bytes long; on return the bytes needed, and
+// BLOCKINV_ERR_NOMEM if that is more), which the caller leaves untouched
+// until the stream has passed the copies.
 int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const int32_t* block_sizes,
                       double* const* A, const int64_t* lda, BatchPlan** out, int force_tile = 0,
-                      const int* tiles = nullptr);
+                      const int* tiles = nullptr, cudaStream_t pool_stream = nullptr, void* staging = nullptr,
+                      size_t* staging_bytes = nullptr);
 // Autotuner: time the candidate partitions and Schur tiles of every size
 // class present in n[] and keep the fastest in the process-wide table.
 int batch_tune(int32_t count, const int32_t* n, int reps, cudaStream_t s);

@@ -137,18 +137,26 @@ cudaError_t launch_cast_f64_to_f32(const double* A, int64_t lda, float* X, int64
 cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64_t lda, int n, cudaStream_t s);
 int mixed_kpad(int bmax);
 // Runs every elimination step on X32 (n x n, leading dimension ld32). Pinv is
-// bmax^2 floats; U and Vt are n x (nsl * mixed_kpad(bmax)) operands of 4
-// (TF32) or 2 (BF16) bytes per element; nsl = 2 splits each operand into
-// hi + lo and runs the three products hi*hi + hi*lo + lo*hi.
+// bmax^2 floats; U and Vt are n x (2 * nsl * mixed_kpad(bmax)) operands of 4
+// (TF32) or 2 (BF16) bytes per element (two steps' slice sets); nsl = 2
+// splits each operand into hi + lo and runs the three products
+// hi*hi + hi*lo + lo*hi.
 // pivot_cond_limit: > 0, pivot blocks whose condition estimate exceeds it are
 // inverted again in FP64 arithmetic (launch_pivot_cond, launch_pivot_f64_gated); < 0, every
 // block; 0, none. piv_words: device int32[2] (gate, count of FP64 pivots).
 // lookahead: with 3 or more blocks, each next pivot inverse runs beside the
 // rest of the current Schur update (same stream, programmatic dependent
-// launch); the result bits are the same.
+// launch); the result bits are the same. fuse (with lookahead, 2 or more
+// blocks): the Schur updates of two consecutive steps run as one sweep over
+// X32 (rank b_k + b_{k+1}), after step k has updated block row and column
+// k + 1 only; the sums are associated differently from one step at a time.
 cudaError_t mixed_elimination(const Plan& pl, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s,
-                              bool lookahead);
+                              bool lookahead, bool fuse);
+
+// A synthetic diagonally dominant matrix of order n (U[-1,1) from a hash of
+// (seed, index) plus n on the diagonal) for the autotuners (batched.cu).
+cudaError_t launch_fill_diag_dominant(double* A, int n, unsigned long long seed, cudaStream_t s);
 
 // Batched small matrices, order 1..8, one thread per matrix (k_small.cu).
 cudaError_t launch_small_batched(int n, double* A, int64_t count, int32_t* status, cudaStream_t s);

@@ -76,15 +76,16 @@ constexpr int kKc = 16;  // k columns of P^-1 per shared-memory chunk (double-bu
 // Operands are stored as `nsl` slices of kpad columns: slice 0 holds the
 // rounded value (hi), slice 1 (if present) the rounded remainder (lo), so
 // that hi*hi + hi*lo + lo*hi carries about twice the operand precision.
+// Rows are ldop elements apart (two steps' slice sets side by side when the
+// Schur updates of two steps run as one sweep).
 template <int MAXB, bool kBF16>
 __global__ void __launch_bounds__(256)
 row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, const float* __restrict__ Pinv,
                        typename OpType<kBF16>::T* __restrict__ U, typename OpType<kBF16>::T* __restrict__ Vt,
-                       int kpad, int nsl, const int32_t* status, int col_tiles) {
+                       int kpad, int nsl, int64_t ldop, const int32_t* status, int col_tiles) {
   using Op = OpType<kBF16>;
   if (failed(status)) return;
   const int tid = threadIdx.x;
-  const int64_t ldop = (int64_t)nsl * kpad;
   if ((int)blockIdx.x >= col_tiles) {
     // U: four consecutive columns per thread and step (kpad is a multiple of 64)
     const int q4 = kpad / 4;
@@ -233,67 +234,100 @@ row_panel_mixed_kernel(float* __restrict__ X, int64_t ldx, int n, int o, int b, 
 }
 
 // ---------------------------------------------------- Schur epilogue ------
-// Elements written: every row outside the pivot rows [o, o + b); with
-// part = kInside only those of the square [r0, r1) x [r0, r1) (the next
-// pivot block), with part = kOutside all but those.
-enum SchurPart { kWhole = 0, kInside = 1, kOutside = 2 };
+// The Schur update of one elimination step, or of two in one sweep:
+//
+//   X[i, j] <- (drop(i, j) ? 0 : X[i, j]) - sum_l U[i, l] Vt[j, l]
+//
+// for the rows i outside [s0, s1) (the newest pivot block, written by its
+// row panel instead). drop(i, j): j in [d0, d1), or j in [g0, g1) with i
+// outside [e0, e1). One step k: s = d = block k, g empty (block column k
+// becomes -U P^-1, since Vt holds P^-1 there). Two steps k, k + 1 (U and Vt
+// holding both steps' panels): s = d = block k + 1, g = e = block k (the rows
+// of block k, which hold step k's row panel, keep their block-k columns).
+// A launch writes only the elements of its part:
+enum SchurPart {
+  kWhole = 0,      // every row outside [s0, s1)
+  kInside = 1,     // only the square [r0, r1) x [r0, r1) (the next pivot block)
+  kOutside = 2,    // all but that square
+  kCrossRows = 3,  // only the rows [r0, r1)
+  kCrossCols = 4,  // only the columns [r0, r1), rows outside [r0, r1)
+};
 
 struct EpiSchurF32 {
   float* X;
   int64_t ldx;
-  int n, o, b;
+  int n;
   const int32_t* status;
+  int s0, s1;          // rows not written
+  int d0, d1;          // columns whose old value is dropped in every written row
+  int g0, g1, e0, e1;  // columns whose old value is dropped in rows outside [e0, e1)
   int part = kWhole;
   int r0 = 0, r1 = 0;
   // The GEMM moves X's 32 x 32 blocks by TMA and asks value() per element.
   static constexpr bool kTmaC = true;
   __device__ bool skip() const { return failed(status); }
+  __device__ bool writes(int row, int col) const {
+    if (row >= n || col >= n || (row >= s0 && row < s1)) return false;
+    const bool rin = row >= r0 && row < r1, cin = col >= r0 && col < r1;
+    switch (part) {
+      case kInside: return rin && cin;
+      case kOutside: return !(rin && cin);
+      case kCrossRows: return rin;
+      case kCrossCols: return cin && !rin;
+      default: return true;
+    }
+  }
   // The new value of X[row][col] from its current value x and the product v
   // (x itself where this launch writes nothing).
   __device__ float value(int row, int col, float x, float v) const {
-    if (col >= n) return x;
-    const bool col_in = col >= r0 && col < r1;
-    if (!writes(row, col_in)) return x;
-    const bool pivot_col = col >= o && col < o + b;
-    return (pivot_col ? 0.f : x) - v;
+    if (!writes(row, col)) return x;
+    const bool drop = (col >= d0 && col < d1) || (col >= g0 && col < g1 && !(row >= e0 && row < e1));
+    return (drop ? 0.f : x) - v;
   }
-  // Whether value() changes any element of the 32 x 32 block at (row0, col0):
-  // blocks of pivot rows only, past the matrix, outside the square (kInside)
-  // or wholly inside it (kOutside) are neither loaded nor stored.
+  // Whether value() may change an element of the 32 x 32 block at (row0,
+  // col0); blocks it leaves alone are neither loaded nor stored.
   __device__ bool block_live(int row0, int col0) const {
     if (row0 >= n || col0 >= n) return false;
     const int rend = min(row0 + 32, n), cend = min(col0 + 32, n);
-    if (row0 >= o && rend <= o + b) return false;
-    if (part == kWhole) return true;
+    if (row0 >= s0 && rend <= s1) return false;
     const bool rows_meet = row0 < r1 && rend > r0, cols_meet = col0 < r1 && cend > r0;
-    if (part == kInside) return rows_meet && cols_meet;
-    return !(row0 >= r0 && rend <= r1 && col0 >= r0 && cend <= r1);
-  }
-  __device__ bool writes(int row, bool col_in) const {
-    if (row >= n || (row >= o && row < o + b)) return false;
-    if (part == kWhole) return true;
-    const bool in = col_in && row >= r0 && row < r1;
-    return part == kInside ? in : !in;
-  }
-  __device__ void apply_cols(int row0, int col, const float (&v)[32], int chunk, int nchunks) const {
-    if (col >= n) return;
-    const bool pivot_col = col >= o && col < o + b;
-    const bool col_in = col >= r0 && col < r1;
-    if (part == kInside && !col_in) return;
-    float* p = X + (int64_t)row0 * ldx + col;
-    // all loads before any store, so the 32 reads are in flight together
-    float cur[32];
-#pragma unroll
-    for (int r = 0; r < 32; ++r) cur[r] = (writes(row0 + r, col_in) && !pivot_col) ? p[(int64_t)r * ldx] : 0.f;
-#pragma unroll
-    for (int r = 0; r < 32; ++r)
-      if (writes(row0 + r, col_in)) p[(int64_t)r * ldx] = cur[r] - v[r];
+    const bool rows_in = row0 >= r0 && rend <= r1, cols_in = col0 >= r0 && cend <= r1;
+    switch (part) {
+      case kInside: return rows_meet && cols_meet;
+      case kOutside: return !(rows_in && cols_in);
+      case kCrossRows: return rows_meet;
+      case kCrossCols: return cols_meet && !rows_in;
+      default: return true;
+    }
   }
 };
 
+// The epilogue of step (o, b) alone.
+EpiSchurF32 one_step_epi(float* X, int64_t ldx, int n, int o, int b, const int32_t* status) {
+  EpiSchurF32 e{};
+  e.X = X;
+  e.ldx = ldx;
+  e.n = n;
+  e.status = status;
+  e.s0 = o;
+  e.s1 = o + b;
+  e.d0 = o;
+  e.d1 = o + b;
+  e.g0 = e.g1 = e.e0 = e.e1 = 0;
+  return e;
+}
+
+// The epilogue of steps (o, b) and (o1, b1) in one sweep.
+EpiSchurF32 two_step_epi(float* X, int64_t ldx, int n, int o, int b, int o1, int b1, const int32_t* status) {
+  EpiSchurF32 e = one_step_epi(X, ldx, n, o1, b1, status);
+  e.g0 = e.e0 = o;
+  e.g1 = e.e1 = o + b;
+  return e;
+}
+
 template <int MAXB, bool kBF16>
 cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
-                         int kpad, int nsl, const int32_t* status, cudaStream_t s) {
+                         int kpad, int nsl, int64_t ldop, const int32_t* status, cudaStream_t s) {
   using T = typename OpType<kBF16>::T;
   const int col_tiles = (n + kCols - 1) / kCols;
   // packing CTAs: about 16 columns of U per thread
@@ -303,52 +337,75 @@ cudaError_t launch_panel(float* X, int64_t ldx, int n, int o, int b, const float
   auto k = row_panel_mixed_kernel<MAXB, kBF16>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, 256, smem, s>>>(X, ldx, n, o, b, Pinv, static_cast<T*>(U), static_cast<T*>(Vt), kpad, nsl, status,
-                            col_tiles);
+  k<<<grid, 256, smem, s>>>(X, ldx, n, o, b, Pinv, static_cast<T*>(U), static_cast<T*>(Vt), kpad, nsl, ldop,
+                            status, col_tiles);
   return cudaGetLastError();
 }
 
 template <bool kBF16>
 cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const float* Pinv, void* U, void* Vt,
-                             int kpad, int nsl, const int32_t* status, cudaStream_t s) {
-  if (b <= 64) return launch_panel<64, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
-  if (b <= 128) return launch_panel<128, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
-  if (b <= 256) return launch_panel<256, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
-  if (b <= 512) return launch_panel<512, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
+                             int kpad, int nsl, int64_t ldop, const int32_t* status, cudaStream_t s) {
+  if (b <= 64) return launch_panel<64, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, ldop, status, s);
+  if (b <= 128) return launch_panel<128, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, ldop, status, s);
+  if (b <= 256) return launch_panel<256, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, ldop, status, s);
+  if (b <= 512) return launch_panel<512, kBF16>(X, ldx, n, o, b, Pinv, U, Vt, kpad, nsl, ldop, status, s);
   return cudaErrorInvalidValue;
 }
 
-// The Schur update of step (o, b): the whole of it (part = kWhole), or the
-// square [o1, o1 + b1)^2 of the next pivot block (kInside: only the tiles
-// that cover it), or everything else (kOutside, on at most max_ctas CTAs,
-// with after_trigger as the programmatic dependent of the kernel before it).
+// The Schur GEMM over the panels of `nsets` elimination steps (slice sets
+// 0 .. nsets - 1 of U and Vt, nsl slices each: hi*hi, and hi*lo + lo*hi with
+// the split), kb k-blocks per slice pair, with the epilogue epi over the
+// tiles of its part: the next pivot block's square (kInside), block row or
+// column (kCrossRows, kCrossCols), or the whole matrix (kWhole, kOutside; the
+// latter on at most max_ctas CTAs, with after_trigger as the programmatic
+// dependent of the kernel before it).
 template <tc::Kind K>
-cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const CUtensorMap& tX, float* X, int64_t ldx,
-                            int n, int o, int b, int kpad, int nsl, int32_t* status, cudaStream_t s, int part = kWhole,
-                            int o1 = 0, int b1 = 0, int max_ctas = 0, bool after_trigger = false) {
-  constexpr int BK = 128 / tc::KindTraits<K>::elem_bytes;
-  const int kb = (b + BK - 1) / BK;
-  tc::KMap km = tc::plain_kmap(kb);
-  if (nsl > 1) {  // hi*hi + hi*lo + lo*hi
-    km.kb_per_pair = kb;
-    km.slice_cols = kpad;
-    km.kblocks = 3 * kb;
-    km.pa[0] = 0; km.pb[0] = 0;
-    km.pa[1] = 0; km.pb[1] = 1;
-    km.pa[2] = 1; km.pb[2] = 0;
+cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const CUtensorMap& tX,
+                            const EpiSchurF32& epi, int nsets, int nsl, int kb, int kpad, int32_t* status,
+                            cudaStream_t s, int max_ctas = 0, bool after_trigger = false) {
+  tc::KMap km{};
+  km.kb_per_pair = kb;
+  km.slice_cols = kpad;
+  int np = 0;
+  for (int t = 0; t < nsets; ++t) {
+    const int h = t * nsl;  // the first slice of set t
+    km.pa[np] = (int8_t)h;
+    km.pb[np] = (int8_t)h;
+    ++np;
+    if (nsl > 1) {
+      km.pa[np] = (int8_t)h;
+      km.pb[np] = (int8_t)(h + 1);
+      ++np;
+      km.pa[np] = (int8_t)(h + 1);
+      km.pb[np] = (int8_t)h;
+      ++np;
+    }
   }
-  EpiSchurF32 epi{X, ldx, n, o, b, status, part, o1, o1 + b1};
+  km.kblocks = np * kb;
   tc::Window win;
   win.c_map = &tX;
-  int M = n, N = n;
-  if (part == kInside) {
-    win.m_base = o1 / tc::kBM * tc::kBM;
-    win.n_base = o1 / tc::kBN * tc::kBN;
-    M = o1 + b1 - win.m_base;
-    N = o1 + b1 - win.n_base;
-  } else if (part == kOutside) {
-    win.max_ctas = max_ctas;
-    win.after_trigger = after_trigger;
+  int M = epi.n, N = epi.n;
+  switch (epi.part) {
+    case kInside:
+      win.m_base = epi.r0 / tc::kBM * tc::kBM;
+      win.n_base = epi.r0 / tc::kBN * tc::kBN;
+      M = epi.r1 - win.m_base;
+      N = epi.r1 - win.n_base;
+      break;
+    case kCrossRows:
+      win.m_base = epi.r0 / tc::kBM * tc::kBM;
+      M = epi.r1 - win.m_base;
+      break;
+    case kCrossCols:
+      win.n_base = epi.r0 / tc::kBN * tc::kBN;
+      N = epi.r1 - win.n_base;
+      break;
+    case kOutside:
+      win.max_ctas = max_ctas;
+      win.after_trigger = after_trigger;
+      break;
+    default:
+      break;
   }
   return tc::launch_gemm<K, EpiSchurF32>(tU, tV, M, N, km, epi, status, s, win);
 }
@@ -369,20 +426,24 @@ int mixed_kpad(int bmax) { return (bmax + 63) / 64 * 64; }
 
 cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, int64_t ld32, float* Pinv, void* U,
                               void* Vt, float pivot_cond_limit, int32_t* piv_words, int32_t* status, cudaStream_t s,
-                              bool lookahead) {
+                              bool lookahead, bool fuse) {
   const int n = mp.n;
   const int p = (int)mp.sizes.size();
   const int kpad = mixed_kpad(mp.bmax);
   const int eb = bf16 ? 2 : 4;
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const uint32_t BK = 128 / eb;
-  const uint64_t w = (uint64_t)nsl * kpad;
+  const int BK = 128 / eb;
+  // U and Vt rows: two slice sets of nsl slices of kpad columns (the panels of
+  // two consecutive steps; one step uses set 0)
+  const int64_t ldop = 2ll * nsl * kpad;
+  unsigned char* Uset[2] = {static_cast<unsigned char*>(U), static_cast<unsigned char*>(U) + (size_t)nsl * kpad * eb};
+  unsigned char* Vset[2] = {static_cast<unsigned char*>(Vt), static_cast<unsigned char*>(Vt) + (size_t)nsl * kpad * eb};
   CUtensorMap tU, tV;
   // X32 itself in 32 x 32 blocks for the update's epilogue (rows of ld32
   // floats, a multiple of 128 bytes)
   CUtensorMap tX;
-  if (!make_tmap_2d(&tU, U, dt, w, n, w * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tV, Vt, dt, w, n, w * eb, BK, tc::kBN) ||
+  if (!make_tmap_2d(&tU, U, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::kBM) ||
+      !make_tmap_2d(&tV, Vt, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::kBN) ||
       !make_tmap_2d(&tX, X32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, n, n, (uint64_t)ld32 * 4, 32, 32))
     return cudaErrorInvalidValue;
   const bool check = pivot_cond_limit != 0.f && piv_words;
@@ -409,57 +470,114 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
     TraceScope t("pivot_f64_if_ill", 0, 8.0 * bd * bd, s);
     return launch_pivot_f64_gated(X32 + (int64_t)o * ld32 + o, ld32, b, Pinv, b, status, k, piv_words, s);
   };
-  auto schur = [&](int k, int part, int k1, int max_ctas, bool after_trigger) -> cudaError_t {
+  auto panel = [&](int k, int set) -> cudaError_t {
     const int o = mp.offs[k], b = mp.sizes[k];
-    const int o1 = k1 >= 0 ? mp.offs[k1] : 0, b1 = k1 >= 0 ? mp.sizes[k1] : 0;
     const double bd = b, nd = n, rest = n - b;
-    const double inside = (double)b1 * b1, elems = part == kWhole ? rest * nd
-                                                   : part == kInside ? inside : rest * nd - inside;
-    const char* name = part == kInside ? (bf16 ? "schur_next_block_bf16_tc" : "schur_next_block_tf32_tc")
-                                       : (bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc");
-    TraceScope t(name, 2.0 * bd * elems * (nsl > 1 ? 3 : 1), 4.0 * 2.0 * elems + eb * 2.0 * nd * bd * nsl, s);
-    return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, tX, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1,
-                                                  b1, max_ctas, after_trigger)
-                : launch_schur_tc<tc::Kind::TF32>(tU, tV, tX, X32, ld32, n, o, b, kpad, nsl, status, s, part, o1,
-                                                  b1, max_ctas, after_trigger);
+    TraceScope t("row_panel_mixed", 2.0 * bd * bd * rest, 4.0 * (2.0 * bd * nd + bd * bd + rest * bd) + eb * 2.0 * nd * kpad, s);
+    return bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, Uset[set], Vset[set], kpad, nsl, ldop, status, s)
+                : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, Uset[set], Vset[set], kpad, nsl, ldop, status, s);
   };
-  // One-step look-ahead: step k's Schur update is split into the next pivot
-  // block's square and the rest. The next FP32 pivot inverse follows the
-  // square and starts its programmatic dependent, the condition estimate,
-  // which starts its own, the rest of the update, at once: they share the GPU
-  // (the update on as many fewer SMs as the other two take). The pivot reads
-  // the square and writes Pinv, the estimate reads both and writes the gate.
-  // The rest of the update neither loads nor stores the 32 x 32 blocks of X
-  // that lie wholly inside the square; a block that straddles its edge (a
-  // block order that is not a multiple of 32) is stored back with the
-  // square's bytes as loaded, so the pivot reads the same values either way.
-  // The gated FP64 inverse and the next row panel (which overwrites U and Vt)
-  // follow.
+  // a Schur GEMM launch: `elems` updated elements, `kdepth` = b summed over its steps
+  auto gemm = [&](const char* name, const EpiSchurF32& epi, int nsets, int kb, double elems, double kdepth,
+                  int max_ctas, bool after_trigger) -> cudaError_t {
+    TraceScope t(name, 2.0 * kdepth * elems * (nsl > 1 ? 3 : 1), 4.0 * 2.0 * elems + eb * 2.0 * n * kdepth * nsl, s);
+    return bf16 ? launch_schur_tc<tc::Kind::BF16>(tU, tV, tX, epi, nsets, nsl, kb, kpad, status, s, max_ctas,
+                                                  after_trigger)
+                : launch_schur_tc<tc::Kind::TF32>(tU, tV, tX, epi, nsets, nsl, kb, kpad, status, s, max_ctas,
+                                                  after_trigger);
+  };
+  auto kblocks = [&](int b) { return (b + BK - 1) / BK; };
+  const char* nm_next = bf16 ? "schur_next_block_bf16_tc" : "schur_next_block_tf32_tc";
+  const char* nm_rest = bf16 ? "schur_update_bf16_tc" : "schur_update_tf32_tc";
+  const char* nm_cross = bf16 ? "schur_cross_bf16_tc" : "schur_cross_tf32_tc";
+  // Step k's update over everything but the pivot rows with set `set`, or,
+  // split around the next pivot block's square (look-ahead), its square, the
+  // next FP32 pivot inverse and its condition estimate by programmatic
+  // dependent launch beside the rest. The pivot reads the square and writes
+  // Pinv, the estimate reads both and writes the gate; the rest of the update
+  // neither loads nor stores the 32 x 32 blocks of X wholly inside the square,
+  // and stores a block straddling its edge (orders not multiples of 32) with
+  // the square's bytes as loaded, so the pivot reads the same values either
+  // way. The gated FP64 inverse follows.
+  auto sweep_then_pivot = [&](EpiSchurF32 epi, int nsets, int kb, double kdepth, int knext,
+                              bool split) -> cudaError_t {
+    const double nd = n, rows = n - (epi.s1 - epi.s0);
+    cudaError_t e;
+    if (!split) {
+      epi.part = kWhole;
+      e = gemm(nm_rest, epi, nsets, kb, rows * nd, kdepth, 0, false);
+      if (e == cudaSuccess && knext < p) e = pivot(knext);
+      if (e == cudaSuccess && knext < p) e = pivot_cond(knext, false);
+    } else {
+      const int o1 = mp.offs[knext], b1 = mp.sizes[knext];
+      const double inside = (double)b1 * b1;
+      epi.r0 = o1;
+      epi.r1 = o1 + b1;
+      epi.part = kInside;
+      e = gemm(nm_next, epi, nsets, kb, inside, kdepth, 0, false);
+      if (e == cudaSuccess) e = pivot(knext);
+      if (e == cudaSuccess) e = pivot_cond(knext, true);
+      const int reserve = pivot_inverse_ctas(b1, 4, false) + (check ? 1 : 0);
+      epi.part = kOutside;
+      if (e == cudaSuccess) e = gemm(nm_rest, epi, nsets, kb, rows * nd - inside, kdepth, tc::num_sms() - reserve, true);
+    }
+    if (e == cudaSuccess && knext < p) e = pivot_gated(knext);
+    return e;
+  };
   const bool ahead = lookahead && p >= 3;
   cudaError_t e = pivot(0);
   if (e == cudaSuccess) e = pivot_cond(0, false);
   if (e == cudaSuccess) e = pivot_gated(0);
-  for (int k = 0; k < p && e == cudaSuccess; ++k) {
+  if (!(fuse && p >= 2)) {
+    // one step per sweep over X
+    for (int k = 0; k < p && e == cudaSuccess; ++k) {
+      const int o = mp.offs[k], b = mp.sizes[k];
+      e = panel(k, 0);
+      if (e != cudaSuccess || n == b) continue;
+      e = sweep_then_pivot(one_step_epi(X32, ld32, n, o, b, status), 1, kblocks(b), b, k + 1,
+                           ahead && k + 1 < p);
+    }
+    return e;
+  }
+  // Two steps per sweep (steps k, k + 1 with K = block k, L = block k + 1):
+  //   row panel k (set 0);
+  //   step k on block row L and block column L only (two windowed launches);
+  //   pivot inverse of L; Vt of set 0 zeroed in the rows of L; row panel
+  //   k + 1 (set 1, from the updated block row and column L);
+  //   one rank-(b_k + b_L) sweep over the rest of X with both sets:
+  //     X <- (drop ? 0 : X) - U_k Vt_k^T - U_L Vt_L^T,
+  //   dropping block columns K and L (only L in the rows of K, which hold
+  //   row panel k) and leaving the rows of L (row panel k + 1) alone.
+  // Every element of the rest gets the same two rank-b products as two
+  // separate steps, summed in one FP32 accumulator instead of rounded to
+  // X32 in between. With an odd block count the last step runs alone.
+  for (int k = 0; k < p && e == cudaSuccess; k += 2) {
     const int o = mp.offs[k], b = mp.sizes[k];
-    const double bd = b, nd = n, rest = n - b;
-    {
-      TraceScope t("row_panel_mixed", 2.0 * bd * bd * rest, 4.0 * (2.0 * bd * nd + bd * bd + rest * bd) + eb * 2.0 * nd * kpad, s);
-      e = bf16 ? launch_panel_any<true>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s)
-               : launch_panel_any<false>(X32, ld32, n, o, b, Pinv, U, Vt, kpad, nsl, status, s);
+    e = panel(k, 0);
+    if (e != cudaSuccess) break;
+    if (k + 1 == p) {
+      if (n != b) e = sweep_then_pivot(one_step_epi(X32, ld32, n, o, b, status), 1, kblocks(b), b, p, false);
+      break;
     }
-    if (e != cudaSuccess || n == b) continue;
-    if (!ahead || k + 1 == p) {
-      e = schur(k, kWhole, -1, 0, false);
-      if (e == cudaSuccess && k + 1 < p) e = pivot(k + 1);
-      if (e == cudaSuccess && k + 1 < p) e = pivot_cond(k + 1, false);
-    } else {
-      e = schur(k, kInside, k + 1, 0, false);
-      if (e == cudaSuccess) e = pivot(k + 1);
-      if (e == cudaSuccess) e = pivot_cond(k + 1, true);
-      const int reserve = pivot_inverse_ctas(mp.sizes[k + 1], 4, false) + (check ? 1 : 0);
-      if (e == cudaSuccess) e = schur(k, kOutside, k + 1, tc::num_sms() - reserve, true);
-    }
-    if (e == cudaSuccess && k + 1 < p) e = pivot_gated(k + 1);
+    const int o1 = mp.offs[k + 1], b1 = mp.sizes[k + 1];
+    const double nd = n, bd = b;
+    EpiSchurF32 cross = one_step_epi(X32, ld32, n, o, b, status);
+    cross.r0 = o1;
+    cross.r1 = o1 + b1;
+    cross.part = kCrossRows;
+    e = gemm(nm_cross, cross, 1, kblocks(b), (double)b1 * nd, bd, 0, false);
+    cross.part = kCrossCols;
+    if (e == cudaSuccess) e = gemm(nm_cross, cross, 1, kblocks(b), (double)b1 * (nd - b1 - bd), bd, 0, false);
+    if (e == cudaSuccess) e = pivot(k + 1);
+    if (e == cudaSuccess) e = pivot_cond(k + 1, false);
+    if (e == cudaSuccess) e = pivot_gated(k + 1);
+    if (e == cudaSuccess)
+      e = cudaMemset2DAsync(Vset[0] + (size_t)o1 * ldop * eb, (size_t)ldop * eb, 0, (size_t)nsl * kpad * eb, b1, s);
+    if (e == cudaSuccess) e = panel(k + 1, 1);
+    if (e != cudaSuccess) break;
+    // (with two blocks only, the sweep still updates the rows of block k)
+    e = sweep_then_pivot(two_step_epi(X32, ld32, n, o, b, o1, b1, status), 2, kblocks(std::max(b, b1)),
+                         (double)b + b1, k + 2, ahead && k + 2 < p);
   }
   return e;
 }

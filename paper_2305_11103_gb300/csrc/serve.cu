@@ -9,9 +9,20 @@
 // what runs beside it: the kernels of one request read and write only that
 // request's matrix and workspace.
 //
+// Small requests (order <= kServeBatchMax) are coalesced: at each admission
+// pass every queued small request that fits in the budget (up to
+// kServeBatchCap of them) goes into one batch job on one slot, inverted by
+// the grouped FP64 batched engine (one launch per kernel and elimination step
+// for the whole batch, partitions and Schur tiles from the batch autotuner's
+// table), whatever mode was asked: at these orders the FP64 path is both
+// faster than the mixed pipeline and exact to FP64 rounding. The result
+// record names the mode that produced it.
+//
 // Per request the context records the time in the queue, the device time
-// (CUDA events on its slot stream) and the end-to-end time, plus the
-// refinement residual for the mixed modes.
+// (CUDA events on its slot stream; for a batch job, the batch's) and the
+// end-to-end time, plus the refinement residual for the mixed modes.
+// Finished requests also enter a completion queue (blockinv_poll_done), so a
+// caller with many requests in flight need not poll each one.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -20,6 +31,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "batched.h"
 #include "internal.h"
 
 using Clock = std::chrono::steady_clock;
@@ -27,13 +39,19 @@ using Clock = std::chrono::steady_clock;
 namespace blockinv {
 namespace {
 
+constexpr int kServeBatchMax = 512;  // orders inverted by the batched FP64 engine
+constexpr int kServeBatchCap = 512;  // requests per batch job
+
 struct Request {
   uint64_t id = 0;
   Plan plan;
   double* A = nullptr;
   int64_t lda = 0;
   int mode = 0;
+  int mode_used = 0;      // the mode that produced the result
   bool host = false;
+  bool batchable = false;
+  bool explicit_sizes = false;
   size_t footprint = 0;
   Clock::time_point t_submit, t_admit, t_done;
   int status = BLOCKINV_PENDING;
@@ -56,6 +74,15 @@ struct Slot {
   Request* req = nullptr;
   int enqueue_status = BLOCKINV_OK;
   float dev_ms = 0.f;              // device time of earlier passes (fallback)
+  // a batch job (req is null then)
+  std::vector<Request*> batch;
+  std::vector<double*> bdbuf;      // device copies of its host requests (or null)
+  BatchPlan* plan = nullptr;
+  int32_t* bstatus_dev = nullptr;  // kServeBatchCap words
+  int32_t* bstatus_host = nullptr; // pinned, kServeBatchCap words
+  void* staging = nullptr;         // pinned descriptor staging of the batch plans
+  size_t staging_cap = 0;
+  bool busy() const { return req != nullptr || !batch.empty(); }
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -78,6 +105,7 @@ struct blockinv_ctx {
   std::thread worker;
   bool stopping = false;
   size_t busy = 0;
+  std::deque<uint64_t> done_ids;  // completion queue (blockinv_poll_done)
 };
 
 namespace blockinv {
@@ -162,13 +190,104 @@ bool finalize_request(blockinv_ctx* c, Slot& sl) {
   r->status = st;
   r->rho = rho;
   r->iters = iters;
+  r->mode_used = r->fell_back ? BLOCKINV_F64 : r->mode;
   r->t_done = Clock::now();
   r->done = true;
   c->used -= r->footprint;
   c->busy -= 1;
+  c->done_ids.push_back(r->id);
   sl.req = nullptr;
   c->cv_done.notify_all();
   return true;
+}
+
+// A batch job: every request's matrix (a pooled device copy for host
+// requests), one pooled batch plan with each request's partition (its own,
+// or the batch tuner's choice for its size class), the grouped FP64 engine,
+// the per-matrix status words back to pinned memory.
+void launch_batch(Slot& sl) {
+  cudaStream_t s = sl.s;
+  const int count = (int)sl.batch.size();
+  cudaEventRecord(sl.ev0, s);
+  std::vector<int32_t> nn(count), pp(count), sizes;
+  std::vector<double*> X(count);
+  std::vector<int64_t> ld(count);
+  sl.bdbuf.assign(count, nullptr);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = workspace_pool(&pool);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    Request* r = sl.batch[i];
+    const int n = r->plan.n;
+    nn[i] = n;
+    X[i] = r->A;
+    ld[i] = r->lda;
+    if (r->host) {
+      e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&sl.bdbuf[i]), sizeof(double) * (size_t)n * n, pool, s);
+      if (e == cudaSuccess) e = copy_matrix(sl.bdbuf[i], n, r->A, r->lda, n, cudaMemcpyHostToDevice, s);
+      X[i] = sl.bdbuf[i];
+      ld[i] = n;
+    }
+    std::vector<int> part;
+    int tile = 0;
+    if (r->explicit_sizes)
+      part = r->plan.sizes;
+    else
+      batch_partition(n, &part, &tile);
+    pp[i] = (int32_t)part.size();
+    sizes.insert(sizes.end(), part.begin(), part.end());
+  }
+  int st = e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  sl.plan = nullptr;
+  if (st == BLOCKINV_OK) {
+    size_t cap = sl.staging_cap;
+    st = batch_plan_create(count, nn.data(), pp.data(), sizes.data(), X.data(), ld.data(), &sl.plan, 0, nullptr, s,
+                           sl.staging, &cap);
+    if (st == BLOCKINV_ERR_NOMEM && cap > sl.staging_cap) {  // grow the staging (the slot is idle)
+      if (sl.staging) cudaFreeHost(sl.staging);
+      sl.staging = nullptr;
+      sl.staging_cap = 0;
+      if (cudaMallocHost(&sl.staging, 2 * cap) == cudaSuccess) sl.staging_cap = 2 * cap;
+      cap = sl.staging_cap;
+      st = batch_plan_create(count, nn.data(), pp.data(), sizes.data(), X.data(), ld.data(), &sl.plan, 0, nullptr,
+                             s, sl.staging, &cap);
+    }
+  }
+  if (st == BLOCKINV_OK && batch_run(*sl.plan, s, sl.bstatus_dev, false) != cudaSuccess) st = BLOCKINV_ERR_CUDA;
+  if (st == BLOCKINV_OK)
+    cudaMemcpyAsync(sl.bstatus_host, sl.bstatus_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
+  for (int i = 0; i < count && st == BLOCKINV_OK; ++i) {
+    Request* r = sl.batch[i];
+    if (r->host) copy_matrix(r->A, r->lda, sl.bdbuf[i], r->plan.n, r->plan.n, cudaMemcpyDeviceToHost, s);
+  }
+  cudaEventRecord(sl.ev1, s);
+  sl.enqueue_status = st;
+}
+
+void finalize_batch(blockinv_ctx* c, Slot& sl) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
+  if (sl.plan) batch_plan_destroy(sl.plan);  // its memory goes back to the pool in stream order
+  sl.plan = nullptr;
+  for (double* d : sl.bdbuf)
+    if (d) cudaFreeAsync(d, sl.s);
+  sl.bdbuf.clear();
+  const auto now = Clock::now();
+  std::lock_guard<std::mutex> g(c->mu);
+  for (size_t i = 0; i < sl.batch.size(); ++i) {
+    Request* r = sl.batch[i];
+    r->status = sl.enqueue_status != BLOCKINV_OK ? sl.enqueue_status : sl.bstatus_host[i];
+    r->dev_ms = ms;
+    r->rho = -1.0;
+    r->iters = 0;
+    r->mode_used = BLOCKINV_F64;
+    r->t_done = now;
+    r->done = true;
+    c->used -= r->footprint;
+    c->busy -= 1;
+    c->done_ids.push_back(r->id);
+  }
+  sl.batch.clear();
+  c->cv_done.notify_all();
 }
 
 void worker_loop(blockinv_ctx* c) {
@@ -177,8 +296,11 @@ void worker_loop(blockinv_ctx* c) {
   for (;;) {
     bool progressed = false;
     for (Slot& sl : c->slots) {
-      if (sl.req && cudaEventQuery(sl.ev1) == cudaSuccess) {
-        finalize_request(c, sl);
+      if (sl.busy() && cudaEventQuery(sl.ev1) == cudaSuccess) {
+        if (sl.req)
+          finalize_request(c, sl);
+        else
+          finalize_batch(c, sl);
         progressed = true;
       }
     }
@@ -186,18 +308,40 @@ void worker_loop(blockinv_ctx* c) {
     {
       std::unique_lock<std::mutex> lk(c->mu);
       if (c->stopping && c->queue.empty() && c->busy == 0) break;
+      bool batched = false;  // at most one new batch job per pass
       for (Slot& sl : c->slots) {
-        if (sl.req) continue;
+        if (sl.busy()) continue;
+        const auto now = Clock::now();
+        if (!batched) {
+          // every queued small request that fits, oldest first, into one batch job
+          for (auto it = c->queue.begin(); it != c->queue.end() && (int)sl.batch.size() < kServeBatchCap;) {
+            Request* r = *it;
+            if (r->batchable && r->footprint <= c->budget - c->used) {
+              it = c->queue.erase(it);
+              c->used += r->footprint;
+              c->busy += 1;
+              r->t_admit = now;
+              sl.batch.push_back(r);
+            } else {
+              ++it;
+            }
+          }
+          if (!sl.batch.empty()) {
+            batched = true;
+            admitted.push_back(&sl);
+            continue;
+          }
+        }
         // first fit: the oldest queued request that fits in the remaining budget
         auto it = c->queue.begin();
         for (; it != c->queue.end(); ++it)
-          if ((*it)->footprint <= c->budget - c->used) break;
+          if (!(*it)->batchable && (*it)->footprint <= c->budget - c->used) break;
         if (it == c->queue.end()) break;
         Request* r = *it;
         c->queue.erase(it);
         c->used += r->footprint;
         c->busy += 1;
-        r->t_admit = Clock::now();
+        r->t_admit = now;
         sl.req = r;
         admitted.push_back(&sl);
       }
@@ -206,7 +350,12 @@ void worker_loop(blockinv_ctx* c) {
         continue;
       }
     }
-    for (Slot* sl : admitted) launch_request(c, *sl);
+    for (Slot* sl : admitted) {
+      if (sl->req)
+        launch_request(c, *sl);
+      else
+        launch_batch(*sl);
+    }
   }
 }
 
@@ -234,6 +383,10 @@ int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, bloc
     if (e == cudaSuccess) e = cudaEventCreate(&sl.ev1);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.status_dev), 2 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.status_host), 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.bstatus_dev), kServeBatchCap * sizeof(int32_t));
+    if (e == cudaSuccess)
+      e = cudaMallocHost(reinterpret_cast<void**>(&sl.bstatus_host), kServeBatchCap * sizeof(int32_t));
+    if (e == cudaSuccess && cudaMallocHost(&sl.staging, 1 << 20) == cudaSuccess) sl.staging_cap = 1 << 20;
   }
   if (e != cudaSuccess) {
     for (Slot& sl : c->slots) {
@@ -242,6 +395,9 @@ int blockinv_ctx_create(int device, size_t hbm_budget_bytes, int max_slots, bloc
       if (sl.ev1) cudaEventDestroy(sl.ev1);
       if (sl.status_dev) cudaFree(sl.status_dev);
       if (sl.status_host) cudaFreeHost(sl.status_host);
+      if (sl.bstatus_dev) cudaFree(sl.bstatus_dev);
+      if (sl.bstatus_host) cudaFreeHost(sl.bstatus_host);
+      if (sl.staging) cudaFreeHost(sl.staging);
     }
     delete c;
     cudaSetDevice(prev);
@@ -265,8 +421,12 @@ int blockinv_submit(blockinv_ctx* c, int64_t n, int32_t p, const int32_t* block_
   r->A = A;
   r->lda = lda;
   r->mode = mode;
+  r->mode_used = mode;
   r->host = (flags & BLOCKINV_SUBMIT_HOST) != 0;
-  r->footprint = serve_footprint(r->plan, mode) + (r->host ? sizeof(double) * (size_t)n * n : 0);
+  r->batchable = n <= kServeBatchMax;
+  r->explicit_sizes = p > 0;
+  r->footprint = serve_footprint(r->plan, r->batchable ? BLOCKINV_F64 : mode) +
+                 (r->host ? sizeof(double) * (size_t)n * n : 0);
   if (r->footprint > c->budget) {
     delete r;
     return BLOCKINV_ERR_BUDGET;
@@ -292,7 +452,7 @@ static int take_result(blockinv_ctx* c, std::unordered_map<uint64_t, Request*>::
   const int st = r->status;
   if (out) {
     out->status = st;
-    out->mode = r->mode;
+    out->mode = r->mode_used;
     out->n = r->plan.n;
     out->refine_iters = r->iters;
     out->used_fallback = r->fell_back ? 1 : 0;
@@ -339,11 +499,24 @@ int blockinv_cancel(blockinv_ctx* c, uint64_t ticket) {
       r->status = BLOCKINV_ERR_CANCELLED;
       r->t_done = Clock::now();
       r->done = true;
+      c->done_ids.push_back(r->id);
       c->cv_done.notify_all();
       return BLOCKINV_OK;
     }
   }
   return BLOCKINV_PENDING;  // already on the GPU: runs to completion
+}
+
+int blockinv_poll_done(blockinv_ctx* c, uint64_t* tickets, int32_t max_tickets, int32_t* count) {
+  if (!c || !count || max_tickets < 0 || (max_tickets > 0 && !tickets)) return BLOCKINV_ERR_INVALID;
+  std::lock_guard<std::mutex> g(c->mu);
+  int32_t k = 0;
+  while (k < max_tickets && !c->done_ids.empty()) {
+    tickets[k++] = c->done_ids.front();
+    c->done_ids.pop_front();
+  }
+  *count = k;
+  return BLOCKINV_OK;
 }
 
 int blockinv_ctx_stats(blockinv_ctx* c, int64_t* queued, int64_t* running, size_t* bytes_in_use) {
@@ -376,6 +549,9 @@ int blockinv_ctx_destroy(blockinv_ctx* c) {
     cudaEventDestroy(sl.ev1);
     cudaFree(sl.status_dev);
     cudaFreeHost(sl.status_host);
+    cudaFree(sl.bstatus_dev);
+    cudaFreeHost(sl.bstatus_host);
+    if (sl.staging) cudaFreeHost(sl.staging);
   }
   for (auto& kv : c->reqs) delete kv.second;
   delete c;

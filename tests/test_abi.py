@@ -173,3 +173,20 @@ def test_diagnostic_argument_errors(lib):
     assert blockinv.blockinv_diag_recip64(None, None, -1, None) == blockinv.ERR_INVALID
     assert blockinv.blockinv_diag_recip64(None, None, 4, None) == blockinv.ERR_INVALID
     assert blockinv.blockinv_diag_recip64(None, None, 0, None) == blockinv.OK
+
+
+def test_block_tuning_table(lib):
+    """The single-matrix block-size table: set / read / clear and argument
+    checks, all on the host."""
+    assert blockinv.blockinv_tuning_clear() == blockinv.OK
+    assert blockinv.blockinv_tuning("tf32", 12) == (blockinv.OK, 0)
+    assert blockinv.blockinv_tuning_set("tf32", 12, 384) == blockinv.OK
+    assert blockinv.blockinv_tuning("tf32", 12) == (blockinv.OK, 384)
+    assert blockinv.blockinv_tuning("f64", 12) == (blockinv.OK, 0)
+    assert blockinv.blockinv_tuning_set("f64", 12, 513) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_tuning_set(3, 12, 256) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_tuning("f64", 21)[0] == blockinv.ERR_INVALID
+    assert blockinv.blockinv_tuning_clear() == blockinv.OK
+    assert blockinv.blockinv_tuning("tf32", 12) == (blockinv.OK, 0)
+    assert blockinv.blockinv_tune([100], "f64", 0) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_tune([16385], "tf32", 1) == blockinv.ERR_INVALID

@@ -184,9 +184,10 @@ def test_full_size_16384_mixed(bi, mode, sigma, seed):
 
 # The mixed look-ahead splits step k's Schur update into the next pivot block's
 # square (its covering tiles) and the rest, and runs the next FP32 pivot inverse
-# beside the rest. Every element is the same tile sum either way, so the
-# unrefined elimination must match the one-step-at-a-time sequence bit for bit,
-# also where block edges cut through tiles (ragged sizes) and in reverse order.
+# beside the rest. Every element is the same tile sum either way, so with one
+# step per sweep (the default, fuse = 0) the unrefined elimination must match the
+# one-step-at-a-time sequence bit for bit, also where block edges cut through
+# tiles (ragged sizes) and in reverse order.
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
 @pytest.mark.parametrize("sizes,order,pf", [([256] * 12, 0, 0), ([200, 312, 256, 300, 212, 200, 300, 316, 300], 0, 0),
                                             ([256] * 12, 1, 0), ([500, 24, 512, 100, 412, 500], 0, 0),
@@ -206,6 +207,43 @@ def test_mixed_look_ahead_same_bits(bi, mode, sizes, order, pf):
         outs.append(d.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
     assert rho_np(A, outs[0]) < 1e-5
+
+
+# Two elimination steps per sweep (option fuse = 1): step k updates block row and
+# column k + 1 alone, then one rank-2b sweep applies both steps to the rest.
+# The products are summed in one FP32 accumulator instead of being rounded to
+# FP32 in between, so the unrefined result differs from one step per sweep by
+# rounding only: its residual must be as small, and the refined result must
+# meet the gate. Sizes cover an odd block count, two blocks only, ragged
+# blocks cut through tiles, the reverse order, n below the look-ahead's 2048
+# and the sizes of the 8192 workload.
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("sizes,order", [([256] * 12, 0), ([256] * 11, 0), ([300, 212], 0),
+                                         ([200, 312, 256, 300, 212, 200, 300, 316, 300], 0),
+                                         ([500, 24, 512, 100, 412, 500], 1), ([100, 60, 140, 37], 0),
+                                         ([256] * 9, 1)])
+def test_fused_two_step_sweep_matches_one_step(bi, mode, sizes, order):
+    n = sum(sizes)
+    A = inputs.gaussian_shifted(n, 11 + n, sigma=1.5)
+    outs = []
+    for fuse in (1, 0):
+        d = torch.from_numpy(A).cuda()
+        st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, mode, None, max_refine=0, pivot_order=order,
+                                         fuse=fuse)
+        assert st == bi.OK
+        outs.append(d.cpu().numpy())
+    r_fused, r_one = rho_np(A, outs[0]), rho_np(A, outs[1])
+    assert r_fused <= 4 * r_one + 1e-9, (r_fused, r_one)
+    # the two unrefined inverses agree to FP32-level rounding of the elimination
+    assert np.linalg.norm(outs[0] - outs[1]) / np.linalg.norm(outs[1]) <= 1e-4
+    d = torch.from_numpy(A).cuda()
+    st, info = bi.blockinv_invert_ex(n, sizes, d.data_ptr(), n, mode, None, tol=1e-12, pivot_order=order, fuse=1)
+    assert st == bi.OK and info.used_fallback == 0
+    X = d.cpu().numpy()
+    assert rho_np(A, X) <= 1e-12
+    Xo = oracle.block_inverse(A, sizes)
+    kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
+    assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 1e-12 * kappa
 
 
 def _ill_block(n, kappa, seed):

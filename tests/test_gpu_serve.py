@@ -1,6 +1,8 @@
 """Serving context (continuous batching) through the C ABI: every result is
-the same alone and in the mix (bit for bit in FP64 mode), admission respects
-the HBM budget, host-buffer requests, cancellation and per-request failures."""
+the same alone and in the mix (bit for bit, in FP64 and in the mixed modes),
+small requests are coalesced into FP64 batch jobs, finished requests come out
+of the completion queue once each, admission respects the HBM budget,
+host-buffer requests, cancellation and per-request failures."""
 import time
 
 import numpy as np
@@ -8,6 +10,7 @@ import pytest
 
 import oracle
 from paper_2305_11103_gb300 import inputs
+from tolerance import eps_max, eps_norm, fwd_bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,8 +86,61 @@ def test_mix_vs_oracle_sample(bi):
         sizes = [n] if n <= 3 else (oracle.paper_partition(n) if n <= 16 else [256] * (n // 256) + ([n % 256] if n % 256 else []))
         Xo = oracle.block_inverse(A, sizes)
         X = d.cpu().numpy()
-        kappa = np.linalg.norm(A) * np.linalg.norm(Xo)
-        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 4 * n * kappa * 2.0 ** -53
+        assert eps_norm(X, Xo) <= fwd_bound(A, Xo) and eps_max(X, Xo) <= fwd_bound(A, Xo)
+    ctx.close()
+
+
+def test_alone_equals_mix_mixed(bi):
+    """Mixed-mode requests (orders above the batching limit): the same bits
+    alone on a one-slot context and all at once on a six-slot one."""
+    mats = [inputs.gaussian_shifted(n, 770 + n, sigma=1.5) for n in (600, 800, 1000, 1400, 2100, 700)]
+    modes = ["tf32", "bf16", "tf32", "bf16", "tf32", "tf32"]
+    ctx1 = bi.Context(0, 8 << 30, 1)
+    alone = []
+    for A, m in zip(mats, modes):
+        d = torch.from_numpy(A).cuda()
+        st, t = ctx1.submit(A.shape[0], None, d.data_ptr(), A.shape[0], m)
+        st, r = ctx1.wait(t)
+        assert st == bi.OK and r.mode == bi.MODES[m] and 0 <= r.rho <= 1e-12
+        alone.append(d.cpu().numpy())
+    ctx1.close()
+    ctx = bi.Context(0, 32 << 30, 6)
+    ds = [torch.from_numpy(A).cuda() for A in mats]
+    tickets = [ctx.submit(A.shape[0], None, d.data_ptr(), A.shape[0], m)[1] for A, d, m in zip(mats, ds, modes)]
+    for t in tickets:
+        assert ctx.wait(t)[0] == bi.OK
+    for A, d, a in zip(mats, ds, alone):
+        X = d.cpu().numpy()
+        assert np.array_equal(X, a)
+        assert rho(A, X) <= 1e-12
+    ctx.close()
+
+
+def test_small_requests_batched_and_completion_queue(bi):
+    """Orders <= 512 in a mixed mode: coalesced into FP64 batch jobs (the
+    record says FP64), each result within the FP64 tolerance of the oracle
+    (with the batched engine's default partition, four near-equal blocks), and
+    every ticket reported once by the completion queue."""
+    mats = request_mix(780, 120, 5, 512)
+    ctx = bi.Context(0, 8 << 30, 4)
+    ds = [torch.from_numpy(A).cuda() for A in mats]
+    tickets = [ctx.submit(A.shape[0], None, d.data_ptr(), A.shape[0], "tf32")[1] for A, d in zip(mats, ds)]
+    seen = []
+    t_end = time.time() + 60
+    while len(seen) < len(tickets) and time.time() < t_end:
+        seen += ctx.poll_done()
+        time.sleep(0.001)
+    assert sorted(seen) == sorted(tickets)
+    assert ctx.poll_done() == []
+    for A, d, t in zip(mats, ds, tickets):
+        st, r = ctx.poll(t)
+        assert st == bi.OK and r.mode == bi.F64 and r.rho == -1.0
+        X = d.cpu().numpy()
+        assert rho(A, X) <= 1e-12
+        n = A.shape[0]
+        sizes = [n] if n < 8 else oracle.quarter_partition(n)
+        Xo = oracle.block_inverse(A, sizes)
+        assert eps_norm(X, Xo) <= fwd_bound(A, Xo) and eps_max(X, Xo) <= fwd_bound(A, Xo)
     ctx.close()
 
 
@@ -173,3 +229,23 @@ def test_cancel_queued(bi):
     for t in ts[:-1]:
         assert ctx.wait(t)[0] == bi.OK
     ctx.close()
+
+
+def test_block_size_autotuner_feeds_default_partition(bi):
+    """blockinv_tune picks a block order per size class; calls with p = 0
+    then use it (the result still meets the gate), and clearing restores 256."""
+    assert bi.blockinv_tuning_clear() == bi.OK
+    assert bi.blockinv_tune([900, 1000, 1100], "f64", 1) == bi.OK
+    st, b = bi.blockinv_tuning("f64", 9)
+    assert st == bi.OK and b in (64, 128, 192, 256, 320, 384, 512)
+    A = inputs.gaussian_shifted(1000, 790, sigma=1.5)
+    d = torch.from_numpy(A).cuda()
+    bi.invert_(d, None)
+    assert rho(A, d.cpu().numpy()) <= 1e-12
+    assert bi.blockinv_tune([3000], "tf32", 1) == bi.OK
+    assert bi.blockinv_tuning("tf32", 11)[1] > 0
+    A = inputs.gaussian_shifted(3000, 791, sigma=1.5)
+    d = torch.from_numpy(A).cuda()
+    bi.invert_(d, None, "tf32")
+    assert rho(A, d.cpu().numpy()) <= 1e-12
+    assert bi.blockinv_tuning_clear() == bi.OK
