@@ -91,6 +91,8 @@ WORKLOADS = {
                     desc="256x256 FP64, 4x4 grid of 64x64 blocks, U[-1,1]+256I, seed 1"),
 }
 CPU_SAMPLE_N = 4096
+SERVE_SLOTS = 32
+SERVE_INFLIGHT = 512  # requests submitted and not finished, at most (device memory of their inputs)
 
 # DRAM traffic per launch of a kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel source
@@ -250,6 +252,36 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+class UtilSampler:
+    """nvidia-smi utilization.gpu every 200 ms (mean and median over the window)."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=utilization.gpu", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        vals = [float(v) for v in open(self.path).read().split() if v.replace(".", "").isdigit()]
+        os.unlink(self.path)
+        if not vals:
+            return None
+        vals.sort()
+        return {"mean": sum(vals) / len(vals), "median": vals[len(vals) // 2], "samples": len(vals)}
 
 
 # -------------------------------------------------------------- oracle -----
@@ -762,7 +794,7 @@ def run_batched(args, bi, torch, stream):
 def run_serving(args, bi, torch):
     """Poisson arrivals at 2000 req/s, sizes log-uniform in [5, 4096] (70%
     U[-1,1] + n I, 30% B B^T + 0.1 I), through a serving context with a
-    120 GB budget and 16 slots: mixed TF32 + refinement over the full window
+    120 GB budget and SERVE_SLOTS slots: mixed TF32 + refinement over the full window
     (60 s by default), and plain FP64 over a shorter one (it cannot keep up).
     Orders <= 512 are coalesced by the context into batch jobs on the FP64
     batched engine; larger ones run the single-matrix path of their mode with
@@ -785,10 +817,33 @@ def run_serving(args, bi, torch):
             pool[key] = M
         return pool[key]
 
+    # block sizes from the autotuners on this stream's orders: the batch tuner
+    # for the orders coalesced into FP64 batch jobs, the single-matrix tuner
+    # per mode for the rest (one matrix per size class, its median order)
+    tune = {}
+    t0 = time.time()
+    small = [int(v) for v in grid if 8 <= v <= 512]
+    mix = np.repeat(small, 8).tolist()
+    st = bi.blockinv_batch_tune(mix, 3, None)
+    tune["batch_tune_status"] = int(st)
+    large = [int(v) for v in grid if v > 512]
+    for mode in ("f64", "tf32"):
+        st = bi.blockinv_tune(large, mode, 2)
+        tune[f"tune_status_{mode}"] = int(st)
+        tune[f"blocks_{mode}"] = {f"{2 ** c}-{2 ** (c + 1) - 1}": bi.blockinv_tuning(mode, c)[1]
+                                  for c in range(9, 13)}
+    tune["batch_table"] = {}
+    for c in range(3, 10):
+        _, pc, tile = bi.blockinv_batch_tuning(c)
+        if pc:
+            tune["batch_table"][f"{2 ** c}-{2 ** (c + 1) - 1}"] = {"blocks": pc, "tile": tile}
+    tune["seconds"] = time.time() - t0
     oracle_x = {}
-    out = {"workload": f"Poisson {rate:.0f} req/s, n log-uniform in [5, 4096] quantised to {len(grid)} orders, "
-                       "70% U[-1,1]+nI / 30% B B^T+0.1I, seed 7; budget 120 GB, 16 slots; orders <= 512 "
-                       "coalesced into FP64 batch jobs"}
+    out = {"autotune": tune,
+           "workload": f"Poisson {rate:.0f} req/s, n log-uniform in [5, 4096] quantised to {len(grid)} orders, "
+                       f"70% U[-1,1]+nI / 30% B B^T+0.1I, seed 7; budget 120 GB, {SERVE_SLOTS} slots; orders <= 512 "
+                       f"coalesced into FP64 batch jobs; at most {SERVE_INFLIGHT} requests in flight, later "
+                       "arrivals wait at the client (latency from arrival)"}
     for mode, window in (("f64", args.serve_seconds_f64), ("tf32", args.serve_seconds)):
         arrivals = inputs.poisson_arrivals(rate, window, 7)
         nreq = len(arrivals)
@@ -800,8 +855,10 @@ def run_serving(args, bi, torch):
             matrix(k)
         torch.cuda.synchronize()
         sample = set(inputs.rng(77).choice(nreq, size=min(nreq, 60), replace=False).tolist())
-        ctx = bi.Context(0, 120 << 30, 16)
+        ctx = bi.Context(0, 120 << 30, SERVE_SLOTS)
         cs = torch.cuda.Stream()
+        util = UtilSampler()
+        util.start()
         pending = {}
         lat, fin, statuses, used_modes = [], [], [], []
         kept = {}
@@ -811,7 +868,11 @@ def run_serving(args, bi, torch):
             now = time.perf_counter() - t0
             new = []
             with torch.cuda.stream(cs):
-                while i < nreq and arrivals[i] <= now:
+                # arrived requests are materialised (their matrix copied into a
+                # buffer of their own) and submitted while fewer than
+                # SERVE_INFLIGHT are in flight; the rest wait at the client as
+                # descriptors, their latency still counted from arrival
+                while i < nreq and arrivals[i] <= now and len(pending) + len(new) < SERVE_INFLIGHT:
                     new.append((i, pool[keys[i]].clone()))
                     i += 1
             if new:
@@ -835,11 +896,12 @@ def run_serving(args, bi, torch):
                     kept[ri] = buf
                 done += 1
             if not new and not finished:
-                if i < nreq and not pending:
+                if i < nreq and not pending and arrivals[i] > time.perf_counter() - t0:
                     time.sleep(max(0.0, arrivals[i] - (time.perf_counter() - t0)))
                 else:
                     time.sleep(0.0002)
         wall = time.perf_counter() - t0
+        gpu_util = util.stop()
         ctx.close()
         flops = sum(2.0 * float(grid[k]) ** 3 for k in idx)
         # latency over the window: the requests arriving in its first and last thirds
@@ -864,6 +926,7 @@ def run_serving(args, bi, torch):
                      "latency_p99_last_third_ms": float(np.percentile(late, 99)),
                      "failed": sum(1 for s in statuses if s != bi.OK),
                      "served_fp64_batched_or_fp64": sum(1 for m in used_modes if m == bi.F64),
+                     "gpu_utilization_pct": gpu_util,
                      "sampled_requests": len(kept),
                      "max_rho_sampled": float(max(rhos)) if rhos else None,
                      "eps_vs_oracle_max_sampled": float(max(eps)) if eps else None,

@@ -546,6 +546,7 @@ struct LaSmem {
   LaKey* key;     // [2][C]
   LaKey* cand;    // [1]: this CTA's candidate of the next column
   double* fbuf;   // [kLaRows]: multipliers of the current step (column c before it)
+  double* win;    // [3]: the current pivot's reciprocal, then (as int32) its CTA, row, failure
   int* perm;      // [b]: pivot row of each column
   int* misc;      // [0] candidate local row (-1 none), [1] flags of this CTA
 };
@@ -557,13 +558,14 @@ __device__ __forceinline__ LaSmem la_layout(unsigned char* raw, int b, int C) {
   m.key = reinterpret_cast<LaKey*>(m.slot + 2 * (size_t)C * b);
   m.cand = m.key + 2 * C;
   m.fbuf = reinterpret_cast<double*>(m.cand + 1);
-  m.perm = reinterpret_cast<int*>(m.fbuf + kLaRows);
+  m.win = m.fbuf + kLaRows;
+  m.perm = reinterpret_cast<int*>(m.win + 3);
   m.misc = m.perm + b;
   return m;
 }
 
 size_t la_smem_bytes(int b, int C) {
-  return sizeof(double) * ((size_t)kLaRows * b + 2 * (size_t)C * b + kLaRows) + sizeof(LaKey) * (2 * C + 1) +
+  return sizeof(double) * ((size_t)kLaRows * b + 2 * (size_t)C * b + kLaRows + 3) + sizeof(LaKey) * (2 * C + 1) +
          sizeof(int) * ((size_t)b + 4) + 16;
 }
 
@@ -622,6 +624,9 @@ __device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, boo
   }
 }
 
+// RT: a compile-time bound on the rows per CTA (4, 8 or 16), so that the
+// bulk update is unrolled with its multipliers in registers.
+template <int RT>
 __global__ void __launch_bounds__(kPivotThreads, 1)
 pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __restrict__ out, int64_t ldo,
                     int32_t* status, int block_index) {
@@ -634,7 +639,7 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
   const int rank = (int)cl.block_rank();
   LaSmem m = la_layout(smem_raw, b, C);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = (b + C - 1) / C;  // rows per CTA (<= kLaRows)
+  const int R = (b + C - 1) / C;  // rows per CTA (<= RT)
   const int r0 = rank * R;
   const int nloc = max(0, min(b, r0 + R) - r0);
   const bool col = tid < b;       // this thread updates column tid
@@ -682,53 +687,83 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
   push(0, m.misc[0]);
   cl.sync();
   int failed = 0;
+  int* wi = reinterpret_cast<int*>(m.win + 1);  // [0] CTA of the pivot row, [1] its row, [2] failure (win[1..2])
   for (int c = 0; c < b; ++c) {
-    // the pivot of column c: the best key in this CTA's slots (integer compares)
     const int par = c & 1;
-    int who = 0;
-    LaKey kb = m.key[par * C];
-    for (int q = 1; q < C; ++q) {
-      const LaKey k = m.key[par * C + q];
-      if (key_better(k, kb)) {
-        kb = k;
-        who = q;
-      }
-    }
-    const unsigned long long vb = kb.vbits;
-    if (kb.row == INT_MAX || vb == 0ull) {
-      failed = BLOCKINV_ERR_SINGULAR;
-      break;
-    }
-    if ((vb >> 52) >= 0x7FFull || nonfinite_bits(kb.inv)) {
-      failed = BLOCKINV_ERR_NONFINITE;
-      break;
-    }
-    const int p = kb.row;
-    const int pl = p - r0;  // local index of the pivot row, if this CTA holds it
-    const bool mine = pl >= 0 && pl < nloc;
-    if (tid == 0) m.perm[c] = p;
-    if (mine) used |= 1u << pl;
-    const double* prow = m.slot + ((size_t)par * C + who) * b;
-    const double inv = kb.inv;
-    // multipliers: column c of the local rows before step c
-    const double fl = (warp == 0 && lane < nloc) ? m.rows[(size_t)lane * b + c] : 0.0;
-    if (warp == 0 && lane < nloc) m.fbuf[lane] = fl;
     const int cn = c + 1;
     const bool ahead = cn < b;
-    if (ahead && warp == 0) {
-      // step c on column cn (lane = row), then this CTA's candidate of column cn
-      double x = 0.0;
-      bool valid = false;
-      if (lane < nloc) {
-        double* e = m.rows + (size_t)lane * b + cn;
-        const double sj = prow[cn] * inv;
-        x = (mine && lane == pl) ? sj : fma(-fl, sj, *e);
-        *e = x;
-        valid = !((used >> lane) & 1u);
+    if (warp == 0) {
+      // the pivot of column c: the best key in this CTA's slots, lane q holding
+      // CTA q's key, reduced by shuffles (integer compares; all lanes agree)
+      // (row, CTA) packed as row * 16 + CTA: rows < 2^20, so the packed
+      // value orders like the row and one shuffle carries both
+      unsigned long long kv = 0ull;
+      unsigned kp = 0xFFFFFFFFu;
+      double kinv = 0.0;
+      if (lane < C) {
+        const LaKey k = m.key[par * C + lane];
+        kv = k.vbits;
+        kp = k.row == INT_MAX ? 0xFFFFFFFFu : (static_cast<unsigned>(k.row) << 4) | static_cast<unsigned>(lane);
+        kinv = k.inv;
       }
-      la_pick(m, lane, x, valid, r0);
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) {  // C <= 16: lanes 0..15 reduce, lane 0 broadcasts
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, kv, off);
+        const unsigned op = __shfl_xor_sync(0xffffffffu, kp, off);
+        if (ov > kv || (ov == kv && op < kp)) {
+          kv = ov;
+          kp = op;
+        }
+      }
+      kv = __shfl_sync(0xffffffffu, kv, 0);
+      kp = __shfl_sync(0xffffffffu, kp, 0);
+      const int kr = kp == 0xFFFFFFFFu ? INT_MAX : static_cast<int>(kp >> 4);
+      const int ks = static_cast<int>(kp & 15u);
+      const double inv = __shfl_sync(0xffffffffu, kinv, ks);
+      int fail = 0;
+      if (kr == INT_MAX || kv == 0ull)
+        fail = BLOCKINV_ERR_SINGULAR;
+      else if ((kv >> 52) >= 0x7FFull || nonfinite_bits(inv))
+        fail = BLOCKINV_ERR_NONFINITE;
+      if (lane == 0) {
+        m.win[0] = inv;
+        wi[0] = ks;
+        wi[1] = kr;
+        wi[2] = fail;
+        if (!fail) m.perm[c] = kr;
+      }
+      if (!fail) {
+        const int pl = kr - r0;
+        const bool mine = pl >= 0 && pl < nloc;
+        if (mine) used |= 1u << pl;
+        const double* prow = m.slot + ((size_t)par * C + ks) * b;
+        // multipliers: column c of the local rows before step c
+        const double fl = lane < nloc ? m.rows[(size_t)lane * b + c] : 0.0;
+        if (lane < nloc) m.fbuf[lane] = fl;
+        if (ahead) {
+          // step c on column cn (lane = row), then this CTA's candidate of column cn
+          double x = 0.0;
+          bool valid = false;
+          if (lane < nloc) {
+            double* e = m.rows + (size_t)lane * b + cn;
+            const double sj = prow[cn] * inv;
+            x = (mine && lane == pl) ? sj : fma(-fl, sj, *e);
+            *e = x;
+            valid = !((used >> lane) & 1u);
+          }
+          la_pick(m, lane, x, valid, r0);
+        }
+      }
     }
-    __syncthreads();  // column cn, the candidate and the multipliers are in shared memory
+    __syncthreads();  // the pivot, column cn, the candidate and the multipliers are in shared memory
+    failed = wi[2];
+    if (failed) break;  // the same in every CTA (the same keys)
+    const int who = wi[0], p = wi[1];
+    const double inv = m.win[0];
+    const int pl = p - r0;
+    const bool mine = pl >= 0 && pl < nloc;
+    if (warp != 0 && mine) used |= 1u << pl;
+    const double* prow = m.slot + ((size_t)par * C + who) * b;
     const int rs = ahead ? m.misc[0] : -1;
     // step c on element (r, tid): the pivot row is scaled, column c takes
     // -f inv, every other element x - f (P[p][tid] inv)
@@ -740,14 +775,22 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
       }
       __syncthreads();  // the candidate row is complete
       push(cn, rs);
-      cluster_arrive();
+      cluster_arrive();  // the bulk below hides the exchange and the other CTAs' skew
     }
     if (col && tid != cn) {
-      for (int r = 0; r < nloc; ++r) {
-        if (r == rs) continue;
-        double* e = m.rows + (size_t)r * b + tid;
-        *e = (mine && r == pl) ? sj : fma(-m.fbuf[r], sj, tid == c ? 0.0 : *e);
+      // every element of the column first (one load each, all in flight), then
+      // the FMAs and stores (row rs was done above; its load is harmless)
+      double f[RT], x[RT];
+#pragma unroll
+      for (int r = 0; r < RT; ++r) {
+        f[r] = m.fbuf[r];
+        x[r] = r < nloc ? m.rows[(size_t)r * b + tid] : 0.0;
       }
+      const bool zc = tid == c;  // column c drops its old value
+#pragma unroll
+      for (int r = 0; r < RT; ++r)
+        if (r < nloc && r != rs)
+          m.rows[(size_t)r * b + tid] = (mine && r == pl) ? sj : fma(-f[r], sj, zc ? 0.0 : x[r]);
     }
     if (ahead) cluster_wait();
     __syncthreads();  // the bulk of step c is in shared memory before column c + 2 is read
@@ -1308,12 +1351,11 @@ int la_ctas(int b) {
   return c;
 }
 
-cudaError_t launch_pivot_la(const double* P, int64_t ldp, int b, double* Pinv, int64_t ldo, int32_t* status,
-                            int block_index, cudaStream_t s) {
-  const int C = la_ctas(b);
-  if (C > 16 || b > kLaMaxB) return cudaErrorInvalidValue;
+template <int RT>
+cudaError_t launch_pivot_la_rt(const double* P, int64_t ldp, int b, int C, double* Pinv, int64_t ldo,
+                               int32_t* status, int block_index, cudaStream_t s) {
   const size_t smem = la_smem_bytes(b, C);
-  cudaError_t e = set_smem_once<pivot_la_f64_kernel>(smem);
+  cudaError_t e = set_smem_once<pivot_la_f64_kernel<RT>>(smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {  // clusters above the portable 8 CTAs, allowed once per device
     static std::mutex mu;
@@ -1323,7 +1365,7 @@ cudaError_t launch_pivot_la(const double* P, int64_t ldp, int b, double* Pinv, i
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(mu);
     if (dev < 0 || dev >= 64 || !done[dev]) {
-      e = cudaFuncSetAttribute(pivot_la_f64_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(pivot_la_f64_kernel<RT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
@@ -1340,7 +1382,17 @@ cudaError_t launch_pivot_la(const double* P, int64_t ldp, int b, double* Pinv, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, pivot_la_f64_kernel, P, ldp, b, Pinv, ldo, status, block_index);
+  return cudaLaunchKernelEx(&cfg, pivot_la_f64_kernel<RT>, P, ldp, b, Pinv, ldo, status, block_index);
+}
+
+cudaError_t launch_pivot_la(const double* P, int64_t ldp, int b, double* Pinv, int64_t ldo, int32_t* status,
+                            int block_index, cudaStream_t s) {
+  const int C = la_ctas(b);
+  if (C > 16 || b > kLaMaxB) return cudaErrorInvalidValue;
+  const int R = (b + C - 1) / C;
+  if (R <= 4) return launch_pivot_la_rt<4>(P, ldp, b, C, Pinv, ldo, status, block_index, s);
+  if (R <= 8) return launch_pivot_la_rt<8>(P, ldp, b, C, Pinv, ldo, status, block_index, s);
+  return launch_pivot_la_rt<16>(P, ldp, b, C, Pinv, ldo, status, block_index, s);
 }
 
 template <typename T>

@@ -145,7 +145,8 @@ def test_small_requests_batched_and_completion_queue(bi):
 
 
 def test_mixed_mode_requests(bi):
-    mats = [inputs.gaussian_shifted(n, 720 + n, sigma=1.5) for n in (300, 700, 1100)]
+    # orders above 512 (smaller ones are coalesced into FP64 batch jobs)
+    mats = [inputs.gaussian_shifted(n, 720 + n, sigma=1.5) for n in (600, 700, 1100)]
     ctx = bi.Context(0, 8 << 30, 3)
     ds = [torch.from_numpy(A).cuda() for A in mats]
     tickets = [ctx.submit(A.shape[0], None, d.data_ptr(), A.shape[0], "tf32")[1] for A, d in zip(mats, ds)]
