@@ -106,6 +106,14 @@ NCU_TRAFFIC = {
     ("schur_update_f64", 8192): {"bytes_per_launch": 532.9e6 / 2 * (7936 * 8192) / (5888 * 6144),
                                  "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
     ("schur_update_f64", 6144): {"bytes_per_launch": 532.9e6 / 2, "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
+    # 16384 mixed TF32 solve: the fresh residual (345.15 + 32.18 GB) and the
+    # incremental one (165.83 + 17.16 GB), averaged over the two launches
+    ("residual_group_gemm_e4m3", 16384): {"bytes_per_launch": (345.15e9 + 32.18e9 + 165.83e9 + 17.16e9) / 2,
+                                          "src": (("k_refine.cu", "tc_gemm.cuh", "tc_common.cuh"),
+                                                  "4a191deefbcaa855")},
+    # the rest of one step's TF32 update (the launch after the next block's square)
+    ("schur_update_tf32_tc", 16384): {"bytes_per_launch": 1.36e9 + 0.996e9,
+                                      "src": (("k_mixed.cu", "tc_gemm.cuh", "tc_common.cuh"), "981a47beb0af9513")},
 }
 
 
@@ -133,7 +141,52 @@ def parse():
                     help="timed inversions of the FP64 GPU path on the 16384 matrix (7 s each)")
     ap.add_argument("--probe-peaks", action="store_true",
                     help="measure library GEMM rates (FP64, FP32, TF32, BF16, FP16, FP8, INT8) and exit")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="for profilers: run this many plain blocking inversions of the workload's first "
+                         "matrix in its first mode (no timing, no other leg) and exit")
+    ap.add_argument("--profile-batch-runs", type=int, default=0,
+                    help="for profilers: run the 2000-matrix uneven batch plan this many times and exit")
     return ap.parse_args()
+
+
+def profile_run(args):
+    """A bare workload for profilers (ncu): no timing, no oracle, no other leg."""
+    import torch
+    from paper_2305_11103_gb300 import blockinv as bi
+    from paper_2305_11103_gb300 import build as libbuild
+    from paper_2305_11103_gb300 import inputs
+    libbuild.build()
+    bi.lib()
+    if args.profile_batch_runs:
+        mats = inputs.uneven_batch(2000, 8, 512, 6)
+        src = [torch.from_numpy(M).cuda() for M in mats]
+        dst = [torch.empty_like(t) for t in src]
+        ns = [t.shape[0] for t in src]
+        st = torch.empty(len(mats), dtype=torch.int32, device="cuda")
+        plan = bi.BatchPlan(ns, None, [t.data_ptr() for t in dst], ns)
+        for _ in range(args.profile_batch_runs):
+            torch._foreach_copy_(dst, src)
+            plan.run(None, st.data_ptr())
+        torch.cuda.synchronize()
+        plan.close()
+        print(json.dumps({"profile": "uneven batch plan", "runs": args.profile_batch_runs,
+                          "failed": int((st != 0).sum().item())}))
+        return
+    w = WORKLOADS[args.workload]
+    n, sizes = w["n"], partition(w["n"], w["block"])
+    if w["kind"] == "mixed":
+        (seed, sigma), mode = w["legs"][0], w["modes"][0]
+    else:
+        seed, sigma, mode = w["seed"], w["sigma"], "f64"
+    dA = torch.from_numpy(make_matrix(n, sigma, seed)).cuda()
+    dX = torch.empty_like(dA)
+    for _ in range(args.profile_solves):
+        dX.copy_(dA)
+        st, info = bi.blockinv_invert_ex(n, sizes, dX.data_ptr(), n, mode, None, tol=RHO_GATE)
+        if st != bi.OK:
+            raise bi.BlockinvError(st, info.failing_block, "blockinv_invert_ex")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": w["desc"], "mode": mode, "solves": args.profile_solves}))
 
 
 def probe_peaks():
@@ -198,9 +251,20 @@ def l2_note(n):
     return "inputs larger than L2 (no flush)" if n * n * 8 > 129 * 2 ** 20 else "fits L2"
 
 
-def src_hash(name):
-    with open(os.path.join(ROOT, "paper_2305_11103_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_hash(names):
+    """Hash of the kernel sources a traffic record was measured on."""
+    h = hashlib.sha256()
+    for name in ((names,) if isinstance(names, str) else names):
+        with open(os.path.join(ROOT, "paper_2305_11103_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n):
+    rec = NCU_TRAFFIC.get((kernel, n))
+    if rec and src_hash(rec["src"][0]) == rec["src"][1]:
+        return rec["bytes_per_launch"]
+    return None
 
 
 def percentiles(xs):
@@ -528,11 +592,16 @@ def mixed_rooflines(n, trace, info, nsteps, mode):
         "peak_source": f"2 x the sustained dense BF16 figure ({peaks['source']}): FP8 / BF16 nominal ratio; "
                        "the kernel runs inside seconds-long loops of solves",
         "algorithmic_flops_per_launch": g["flops"] / g["launches"] if g["launches"] else None,
+        "traffic": ncu_traffic("residual_group_gemm_e4m3", n),
+        "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of the fresh and the "
+                        "incremental residual (profiles/mixed_solve_16384.md)",
         "share_of_kernel_time": g["ms"] / kt_total if kt_total else None}
     hbm = {"bound": "hbm", "kernel": f"schur_update_{mode}_tc (gemm_kernel<{mode.upper()}, EpiSchurF32>)",
            "achieved": ags, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": ags / peaks["hbm_gbs"] if ags else None,
            "algorithmic_bytes_per_launch": schur["bytes"] / schur["launches"] if schur["launches"] else None,
+           "traffic": ncu_traffic(f"schur_update_{mode}_tc", n),
+           "traffic_note": "one launch of the rest of a step (after the next block's square)",
            "share_of_kernel_time": schur["ms"] / kt_total if kt_total else None}
     return tensor, hbm, kt_total
 
@@ -758,6 +827,17 @@ def run_batched(args, bi, torch, stream):
         if pc:
             table[f"{2 ** c}-{2 ** (c + 1) - 1}"] = {"blocks": pc, "tile": tile}
     per, tr = time_plan()
+    # gaps between the graph's nodes: the kernels of one stream-ordered run
+    # (no graph), each with its own event pair, against the graph replay
+    refresh()
+    torch.cuda.synchronize()
+    bi.blockinv_trace_enable(True)
+    st_e = bi.blockinv_invert_batched(ns, None, [t.data_ptr() for t in dst], ns, bi.F64, stream, stt.data_ptr())
+    torch.cuda.synchronize()
+    bi.blockinv_trace_enable(False)
+    tr_e = bi.blockinv_trace_summary()
+    kernel_sum = sum(v["ms"] for k, v in tr_e.items() if k.startswith("batched_step_"))
+    launches_e = sum(v["launches"] for k, v in tr_e.items() if k.startswith("batched_step_"))
     bi.blockinv_batch_tuning_clear()
     ms = sum(per) / len(per)
     ms_default = sum(per_default) / len(per_default)
@@ -782,6 +862,12 @@ def run_batched(args, bi, torch, stream):
         "eps_sample": "50 matrices (seed 66), oracle with four blocks of n/4 (the last n mod 4 one larger)",
         "failed": int((stt != 0).sum().item()),
         "launches_per_batch": tr["launches"] / args.steps,
+        "graph_gap_analysis": {
+            "eager_status": int(st_e), "eager_kernel_groups": launches_e,
+            "sum_of_kernel_ms_eager": kernel_sum,
+            "graph_ms": sum(per) / len(per),
+            "note": "kernels of one stream-ordered run, each timed alone; their sum against one graph replay "
+                    "bounds what removing the graph's inter-node gaps (one persistent launch) could save"},
         "default_partition_ms_per_batch": ms_default,
         "autotune": {"seconds": tune_s, "table": table},
         "roofline": {"bound": "alu", "kernel": "batched_grouped_f64 (graph)", "achieved": tfs,
@@ -950,8 +1036,7 @@ def f64_leg(args, bi, torch, stream, w, world, steps, warmup, orc, key):
     trace = trace_pass(bi, torch, step, min(3, steps))
     kname, kt = max(trace.items(), key=lambda kv: kv[1]["ms"])
     achieved = kt["flops"] / (kt["ms"] / 1e3) / 1e12
-    rec = NCU_TRAFFIC.get((kname, n))
-    traffic = rec["bytes_per_launch"] if rec and src_hash(rec["src"][0]) == rec["src"][1] else None
+    traffic = ncu_traffic(kname, n)
     total = sum(v["ms"] for v in trace.values())
     out = {"workload": w["desc"], "n": n, "block": w["block"], "ms_per_step": ms, "value": value,
            "unit": "TFLOP/s", "inverses_per_s": world * 1e3 / ms, "latency_ms": percentiles(per), "rho": rho,
@@ -1257,6 +1342,8 @@ def main():
     args = parse()
     if args.probe_peaks:
         probe_peaks()
+    elif args.profile_solves or args.profile_batch_runs:
+        profile_run(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

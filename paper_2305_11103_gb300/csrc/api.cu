@@ -555,6 +555,7 @@ int serve_enqueue_fallback(ServeJob* job, const Plan& pl, double* A, int64_t lda
 }
 
 TraceScope::TraceScope(const char* name, double flops, double bytes, cudaStream_t s) : s_(s) {
+  if (!name) return;  // a scope that records nothing
   std::lock_guard<std::mutex> g(g_trace_mu);
   if (!g_trace_on) return;
   if (cudaEventCreate(&a_) != cudaSuccess) return;

@@ -310,21 +310,33 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
 
 cudaError_t batch_enqueue(const BatchPlan& pl, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(pl.status, 0, sizeof(int32_t) * 2 * pl.count, s);
+  // per-kernel tracing only when the launches run now (not into a graph)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool trace = cap == cudaStreamCaptureStatusNone;
   for (int k = 0; k < pl.max_steps && e == cudaSuccess; ++k) {
     const BatchStep& st = pl.steps[k];
     const GroupStep* it = pl.items + st.item_off;
-    e = launch_pivot_grouped(it, st.count, std::min(st.bmax, kGroupedMaxB), s);
-    for (const GroupStep& g : st.big) {
-      if (e != cudaSuccess) break;
-      e = launch_pivot_inverse<double>(g.X + (int64_t)g.o * g.ldx + g.o, g.ldx, g.b, g.Pinv, g.b, g.status, g.k,
-                                       s);
+    {
+      TraceScope t(trace ? "batched_step_pivot" : nullptr, 0, 0, s);
+      e = launch_pivot_grouped(it, st.count, std::min(st.bmax, kGroupedMaxB), s);
+      for (const GroupStep& g : st.big) {
+        if (e != cudaSuccess) break;
+        e = launch_pivot_inverse<double>(g.X + (int64_t)g.o * g.ldx + g.o, g.ldx, g.b, g.Pinv, g.b, g.status, g.k,
+                                         s);
+      }
     }
-    if (e == cudaSuccess) e = launch_row_panel_grouped(it, st.count, pl.starts + st.cs_off, st.cols, st.bmax, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+      TraceScope t(trace ? "batched_step_row_panel" : nullptr, 0, 0, s);
+      e = launch_row_panel_grouped(it, st.count, pl.starts + st.cs_off, st.cols, st.bmax, s);
+    }
+    if (e == cudaSuccess) {
+      TraceScope t(trace ? "batched_step_schur" : nullptr, 0, 0, s);
       e = launch_schur_update_grouped(it, st.count64, pl.starts + st.ts_off64, st.tiles64, 64, s);
-    if (e == cudaSuccess)
-      e = launch_schur_update_grouped(it + st.count64, st.count - st.count64, pl.starts + st.ts_off32, st.tiles32,
-                                      32, s);
+      if (e == cudaSuccess)
+        e = launch_schur_update_grouped(it + st.count64, st.count - st.count64, pl.starts + st.ts_off32,
+                                        st.tiles32, 32, s);
+    }
   }
   return e;
 }
