@@ -389,7 +389,9 @@ int blockinv_invert_ex(int64_t n, int32_t p, const int32_t* block_sizes, double*
 /* Diagnostic: C[M x N] (FP32, row-major, ldc) = A[M x K] B[N x K]^T on the
  * tcgen05 tensor-core GEMM used by the mixed path, with A and B row-major
  * (K contiguous, leading dimensions lda / ldb in elements, rows 16-byte
- * aligned). kind 0: BF16 operands; 1: FP32 storage read as TF32; 2: FP8 E4M3.
+ * aligned). kind 0: BF16 operands; 1: FP32 storage read as TF32; 2: FP8 E4M3;
+ * each on single-CTA 128 x 256 output tiles. kind 3, 4, 5: the same three on
+ * CTA pairs (256 x 256 tiles, the form the library's GEMMs run in).
  * Device pointers; blocking. Not part of the paper's method: it exists to
  * check the tensor-core path in isolation. */
 int blockinv_diag_gemm(int kind, int64_t M, int64_t N, int64_t K, const void* A, int64_t lda,

@@ -354,7 +354,9 @@ cudaError_t launch_panel_any(float* X, int64_t ldx, int n, int o, int b, const f
 
 // The Schur GEMM over the panels of `nsets` elimination steps (slice sets
 // 0 .. nsets - 1 of U and Vt, nsl slices each: hi*hi, and hi*lo + lo*hi with
-// the split), kb k-blocks per slice pair, with the epilogue epi over the
+// the split, all three from split stages that hold both slices of both
+// operands), kb k-blocks per set (64 bytes of K each with the split, else 128;
+// tU and tV boxes to match), with the epilogue epi over the
 // tiles of its part: the next pivot block's square (kInside), block row or
 // column (kCrossRows, kCrossCols), or the whole matrix (kWhole, kOutside; the
 // latter on at most max_ctas CTAs, with after_trigger as the programmatic
@@ -366,22 +368,11 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const 
   tc::KMap km{};
   km.kb_per_pair = kb;
   km.slice_cols = kpad;
-  int np = 0;
   for (int t = 0; t < nsets; ++t) {
-    const int h = t * nsl;  // the first slice of set t
-    km.pa[np] = (int8_t)h;
-    km.pb[np] = (int8_t)h;
-    ++np;
-    if (nsl > 1) {
-      km.pa[np] = (int8_t)h;
-      km.pb[np] = (int8_t)(h + 1);
-      ++np;
-      km.pa[np] = (int8_t)(h + 1);
-      km.pb[np] = (int8_t)h;
-      ++np;
-    }
+    km.pa[t] = (int8_t)(t * nsl);  // the first slice of set t
+    km.pb[t] = (int8_t)(t * nsl);
   }
-  km.kblocks = np * kb;
+  km.kblocks = nsets * kb;
   tc::Window win;
   win.c_map = &tX;
   int M = epi.n, N = epi.n;
@@ -407,7 +398,8 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const 
     default:
       break;
   }
-  return tc::launch_gemm<K, EpiSchurF32>(tU, tV, M, N, km, epi, status, s, win);
+  return nsl > 1 ? tc::launch_gemm<K, EpiSchurF32, true, tc::kPairTiles>(tU, tV, M, N, km, epi, status, s, win)
+                 : tc::launch_gemm<K, EpiSchurF32, false, tc::kPairTiles>(tU, tV, M, N, km, epi, status, s, win);
 }
 
 }  // namespace
@@ -432,7 +424,8 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   const int kpad = mixed_kpad(mp.bmax);
   const int eb = bf16 ? 2 : 4;
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const int BK = 128 / eb;
+  // K elements per k-block of the Schur GEMM: 64 bytes in the split stages
+  const int BK = (nsl > 1 ? 64 : 128) / eb;
   // U and Vt rows: two slice sets of nsl slices of kpad columns (the panels of
   // two consecutive steps; one step uses set 0)
   const int64_t ldop = 2ll * nsl * kpad;
@@ -442,8 +435,9 @@ cudaError_t mixed_elimination(const Plan& mp, bool bf16, int nsl, float* X32, in
   // X32 itself in 32 x 32 blocks for the update's epilogue (rows of ld32
   // floats, a multiple of 128 bytes)
   CUtensorMap tX;
-  if (!make_tmap_2d(&tU, U, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tV, Vt, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::kBN) ||
+  if (!make_tmap_2d(&tU, U, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::kBM, nsl > 1) ||
+      !make_tmap_2d(&tV, Vt, dt, (uint64_t)ldop, n, (uint64_t)ldop * eb, BK, tc::b_rows<tc::kPairTiles>(),
+                    nsl > 1) ||
       !make_tmap_2d(&tX, X32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, n, n, (uint64_t)ld32 * 4, 32, 32))
     return cudaErrorInvalidValue;
   const bool check = pivot_cond_limit != 0.f && piv_words;

@@ -670,9 +670,11 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
 
   CUtensorMap tAs, tXs, tXo, tEo;
   if (!make_tmap_2d(&tAs, Asl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBM) ||
-      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128, tc::kBN) ||
-      !make_tmap_2d(&tXo, Xop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBM) ||
-      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 32, tc::kBN))
+      !make_tmap_2d(&tXs, Xsl, CU_TENSOR_MAP_DATA_TYPE_UINT8, (uint64_t)S * Kp, n, (uint64_t)S * Kp, 128,
+                    tc::b_rows<tc::kPairTiles>()) ||
+      !make_tmap_2d(&tXo, Xop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 16, tc::kBM, true) ||
+      !make_tmap_2d(&tEo, Eop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2ull * Kp, n, 8ull * Kp, 16,
+                    tc::b_rows<tc::kPairTiles>(), true))
     return cudaErrorInvalidValue;
 
   const double nd = n;
@@ -710,7 +712,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
     km.live_groups = incr_groups ? &ctl->groups : nullptr;
     EpiAccumI64 epi{T, ldt, n, groups, km.group_starts, ctl, status, path};
     TraceScope t("residual_group_gemm_e4m3", 2.0 * nd * nd * nd * np, (double)np * 2.0 * nd * Kp + 16.0 * nd * nd, s);
-    return tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64>(tAs, tXs, n, n, km, epi, status, s);
+    return tc::launch_gemm<tc::Kind::E4M3, EpiAccumI64, false, tc::kPairTiles>(tAs, tXs, n, n, km, epi, status, s);
   };
   bool next_inc = false;  // host view of ctl->inc (host_steps)
   for (int it = 0; it <= max_updates && e == cudaSuccess; ++it) {
@@ -773,23 +775,23 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       split_x_kernel<<<8 * tc::num_sms(), 256, 0, s>>>(X, ldx, n, Xop, Kp, ctl, status);
     }
     {
+      // Split stages: each k-block is 16 columns of K of the hi and lo
+      // slices of both operands, with the products hi*hi, hi*lo and lo*hi.
       tc::KMap km{};
-      km.kb_per_pair = Kp / 32;
+      km.kb_per_pair = Kp / 16;
       km.slice_cols = Kp;
-      km.kblocks = 3 * km.kb_per_pair;
-      km.pa[0] = 0; km.pb[0] = 0;
-      km.pa[1] = 0; km.pb[1] = 1;
-      km.pa[2] = 1; km.pb[2] = 0;
+      km.kblocks = km.kb_per_pair;
+      km.pa[0] = 0;
+      km.pb[0] = 0;
       // The tensor-core FP32 accumulator drops bits on every k-step (its
-      // error grows linearly with K, measured), so the hi*hi product's K is
-      // cut into chunks of kUpdateChunkK, each added into the FP64 X on its
-      // own; the hi*lo and lo*hi products (2^-11 smaller) form one more chunk.
-      km.chunk_kb = kUpdateChunkK / 32;
-      km.chunk_end = km.kb_per_pair;
+      // error grows linearly with K, measured, and with the accumulator's
+      // magnitude, which the hi*hi terms set), so K is cut into chunks of
+      // kUpdateChunkK, each added into the FP64 X on its own.
+      km.chunk_kb = kUpdateChunkK / 16;
       EpiAddF64 epi{X, ldx, n, ctl, status, Dbuf, ldt};
-      const double chunks = std::ceil((double)Kp / kUpdateChunkK) + 1.0;
+      const double chunks = std::ceil((double)Kp / kUpdateChunkK);
       TraceScope t("ns_update_tf32x3", 3.0 * 2.0 * nd * nd * nd, 16.0 * nd * nd * chunks + 16.0 * nd * Kp, s);
-      e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64>(tXo, tEo, n, n, km, epi, status, s);
+      e = tc::launch_gemm<tc::Kind::TF32, EpiAddF64, true, tc::kPairTiles>(tXo, tEo, n, n, km, epi, status, s);
     }
   }
   if (e == cudaSuccess && report) {

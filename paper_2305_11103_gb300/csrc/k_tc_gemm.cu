@@ -26,7 +26,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 bool make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, uint64_t inner, uint64_t outer,
-                  uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+                  uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, bool swizzle64) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
@@ -34,7 +34,7 @@ bool make_tmap_2d(CUtensorMap* map, const void* base, CUtensorMapDataType dt, ui
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
   return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -64,7 +64,7 @@ struct EpiStoreF32 {
   }
 };
 
-template <tc::Kind K>
+template <tc::Kind K, bool kPair>
 int diag(int M, int N, int Kdim, const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
          cudaStream_t s) {
   constexpr int eb = tc::KindTraits<K>::elem_bytes;
@@ -74,11 +74,11 @@ int diag(int M, int N, int Kdim, const void* A, int64_t lda, const void* B, int6
                                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   CUtensorMap ta, tb;
   if (!make_tmap_2d(&ta, A, dt, (uint64_t)Kdim, (uint64_t)M, (uint64_t)lda * eb, BK, tc::kBM) ||
-      !make_tmap_2d(&tb, B, dt, (uint64_t)Kdim, (uint64_t)N, (uint64_t)ldb * eb, BK, tc::kBN))
+      !make_tmap_2d(&tb, B, dt, (uint64_t)Kdim, (uint64_t)N, (uint64_t)ldb * eb, BK, tc::b_rows<kPair>()))
     return BLOCKINV_ERR_INVALID;
   tc::KMap km = tc::plain_kmap((Kdim + BK - 1) / BK);
   EpiStoreF32 epi{C, ldc, M, N};
-  cudaError_t e = tc::launch_gemm<K>(ta, tb, M, N, km, epi, nullptr, s);
+  cudaError_t e = tc::launch_gemm<K, EpiStoreF32, false, kPair>(ta, tb, M, N, km, epi, nullptr, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
 }
@@ -94,9 +94,12 @@ extern "C" int blockinv_diag_gemm(int kind, int64_t M, int64_t N, int64_t K, con
     return BLOCKINV_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (kind) {
-    case 0: return diag<tc::Kind::BF16>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
-    case 1: return diag<tc::Kind::TF32>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
-    case 2: return diag<tc::Kind::E4M3>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 0: return diag<tc::Kind::BF16, false>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 1: return diag<tc::Kind::TF32, false>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 2: return diag<tc::Kind::E4M3, false>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 3: return diag<tc::Kind::BF16, true>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 4: return diag<tc::Kind::TF32, true>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
+    case 5: return diag<tc::Kind::E4M3, true>((int)M, (int)N, (int)K, A, lda, B, ldb, C, ldc, s);
     default: return BLOCKINV_ERR_INVALID;
   }
 }

@@ -1,5 +1,6 @@
-"""The tcgen05 tensor-core GEMM (through blockinv_diag_gemm) and the
-unrefined mixed-precision elimination, through the C ABI.
+"""The tcgen05 tensor-core GEMM (through blockinv_diag_gemm, on single-CTA
+128 x 256 tiles and on CTA pairs with 256 x 256 tiles) and the unrefined
+mixed-precision elimination, through the C ABI.
 
 Tolerances: integer-valued operands whose products and sums stay below 2^24
 must come out exact (FP32 accumulation of exact products), which is the
@@ -45,31 +46,37 @@ def padded(t, mult):
     return out[:, :K]
 
 
+PAIR = pytest.mark.parametrize("pair", [0, 3], ids=["cta", "pair"])  # kind offset of the CTA-pair GEMM
+
+
+@PAIR
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (2125, 1100, 512), (77, 3000, 1024)])
-def test_e4m3_integer_exact(bi, M, N, K):
+def test_e4m3_integer_exact(bi, M, N, K, pair):
     g = torch.Generator(device="cpu").manual_seed(M + N + K)
     Ai = torch.randint(-15, 16, (M, K), generator=g)
     Bi = torch.randint(-8, 9, (N, K), generator=g)
     A = padded(Ai.to(torch.float32).to(torch.float8_e4m3fn).cuda(), 16)
     B = padded(Bi.to(torch.float32).to(torch.float8_e4m3fn).cuda(), 16)
-    C = run_gemm(bi, 2, A, B).cpu().double()
+    C = run_gemm(bi, 2 + pair, A, B).cpu().double()
     ref = Ai.double() @ Bi.double().T
     assert torch.equal(C, ref)
 
 
+@PAIR
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (300, 520, 200), (1500, 700, 320)])
-def test_bf16_integer_exact(bi, M, N, K):
+def test_bf16_integer_exact(bi, M, N, K, pair):
     g = torch.Generator(device="cpu").manual_seed(7 + M)
     Ai = torch.randint(-100, 101, (M, K), generator=g)
     Bi = torch.randint(-100, 101, (N, K), generator=g)
     A = padded(Ai.to(torch.bfloat16).cuda(), 8)
     B = padded(Bi.to(torch.bfloat16).cuda(), 8)
-    C = run_gemm(bi, 0, A, B).cpu().double()
+    C = run_gemm(bi, 0 + pair, A, B).cpu().double()
     assert torch.equal(C, Ai.double() @ Bi.double().T)
 
 
+@PAIR
 @pytest.mark.parametrize("M,N,K", [(256, 256, 96), (1000, 1300, 260)])
-def test_tf32_matches_fp64_of_rounded_operands(bi, M, N, K):
+def test_tf32_matches_fp64_of_rounded_operands(bi, M, N, K, pair):
     g = torch.Generator(device="cpu").manual_seed(11 + M)
     A = torch.randn(M, K, generator=g)
     B = torch.randn(N, K, generator=g)
@@ -80,17 +87,18 @@ def test_tf32_matches_fp64_of_rounded_operands(bi, M, N, K):
         u = (u + 0x1000) & ~0x1FFF
         return u.view(torch.float32)
     A, B = tf32(A), tf32(B)
-    C = run_gemm(bi, 1, padded(A.cuda(), 4), padded(B.cuda(), 4)).cpu().double()
+    C = run_gemm(bi, 1 + pair, padded(A.cuda(), 4), padded(B.cuda(), 4)).cpu().double()
     ref = A.double() @ B.double().T
     scale = A.abs().double() @ B.abs().double().T
     assert torch.all((C - ref).abs() <= K * 2.0 ** -23 * scale + 1e-30)
 
 
-def test_tf32_integer_exact(bi):
+@PAIR
+def test_tf32_integer_exact(bi, pair):
     g = torch.Generator(device="cpu").manual_seed(5)
     Ai = torch.randint(-300, 301, (640, 128), generator=g).float()
     Bi = torch.randint(-300, 301, (384, 128), generator=g).float()
-    C = run_gemm(bi, 1, Ai.cuda(), Bi.cuda()).cpu().double()
+    C = run_gemm(bi, 1 + pair, Ai.cuda(), Bi.cuda()).cpu().double()
     assert torch.equal(C, Ai.double() @ Bi.double().T)
 
 
@@ -138,7 +146,8 @@ def test_mixed_tf32_unimodular_exact(bi):
     (0, 128.0, 64.0, 1024),   # BF16: products 2^13, sums near 2^23
     (1, 1024.0, 512.0, 32),   # TF32: products 2^19, sums near 2^24
 ])
-def test_accumulator_exact_near_2_24(bi, kind, big_a, big_b, K):
+@PAIR
+def test_accumulator_exact_near_2_24(bi, kind, big_a, big_b, K, pair):
     M, N = 128, 256
     A = np.full((M, K), big_a)
     B = np.full((N, K), big_b)
@@ -151,7 +160,7 @@ def test_accumulator_exact_near_2_24(bi, kind, big_a, big_b, K):
     dt = {2: torch.float8_e4m3fn, 0: torch.bfloat16, 1: torch.float32}[kind]
     tA = torch.from_numpy(A).float().to(dt).cuda()
     tB = torch.from_numpy(B).float().to(dt).cuda()
-    C = run_gemm(bi, kind, tA, tB).cpu().numpy().astype(np.int64)
+    C = run_gemm(bi, kind + pair, tA, tB).cpu().numpy().astype(np.int64)
     bad = np.count_nonzero(C != expect)
     assert bad == 0, f"{bad} inexact outputs; max error {np.abs(C - expect).max()}"
 
