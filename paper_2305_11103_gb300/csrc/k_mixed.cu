@@ -284,6 +284,23 @@ struct EpiSchurF32 {
     const bool drop = (col >= d0 && col < d1) || (col >= g0 && col < g1 && !(row >= e0 && row < e1));
     return (drop ? 0.f : x) - v;
   }
+  // Whether value() is x - v for every element of the 32 x 32 block at (row0,
+  // col0) that lies inside the matrix (the block meets no row left alone, no
+  // dropped column and no edge of its part); elements outside the matrix are
+  // not stored. The GEMM then skips the per-element tests.
+  __device__ bool block_simple(int row0, int col0) const {
+    const int rend = row0 + 32, cend = col0 + 32;
+    if ((row0 < s1 && rend > s0) || (col0 < d1 && cend > d0) || (col0 < g1 && cend > g0)) return false;
+    const bool rows_in = row0 >= r0 && rend <= r1, rows_out = rend <= r0 || row0 >= r1;
+    const bool cols_in = col0 >= r0 && cend <= r1, cols_out = cend <= r0 || col0 >= r1;
+    switch (part) {
+      case kInside: return rows_in && cols_in;
+      case kOutside: return rows_out || cols_out;
+      case kCrossRows: return rows_in;
+      case kCrossCols: return cols_in && rows_out;
+      default: return true;
+    }
+  }
   // Whether value() may change an element of the 32 x 32 block at (row0,
   // col0); blocks it leaves alone are neither loaded nor stored.
   __device__ bool block_live(int row0, int col0) const {

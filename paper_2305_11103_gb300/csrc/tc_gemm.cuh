@@ -414,6 +414,17 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         bulk_wait_read_all();  // the previous tile's last stores have left both slots
         if (nl > 0) request(0, col_of(0), row0);
         if (nl > 1) request(1, col_of(1), row0);
+        // This warp's blocks of its next tile into L2 now, so that their loads
+        // a tile later wait for L2 instead of DRAM.
+        if (t + stride < ntiles) {
+          int um2, tn2;
+          item_coords(t + stride, tiles_m, tiles_n, group, um2, tn2);
+          const int r2 = m_base + um2 * kTM + rank * kBM + q * 32;
+          const int c2 = n_base + tn2 * kBN + cbeg * 32;
+#pragma unroll
+          for (int c = 0; c < kWarpBlocks; ++c)
+            if (epi.block_live(r2, c2 + c * 32)) tma_prefetch_2d(&tmC, c2 + c * 32, r2);
+        }
       }
       int pending = nl < 2 ? nl : 2;  // requested and not yet waited for, this tile
       int next = 0;                   // the live block waited for next (slot next & 1)
@@ -440,15 +451,28 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         --pending;
         ++next;
         const int row = row0 + lane;
+        if (epi.block_simple(row0, col0)) {  // warp-uniform: x - v throughout
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float4* p = reinterpret_cast<float4*>(cb + lane * 128 + ((j ^ (lane & 7)) << 4));
-          float4 x = *p;
-          x.x = epi.value(row, col0 + 4 * j + 0, x.x, __uint_as_float(v[4 * j + 0]));
-          x.y = epi.value(row, col0 + 4 * j + 1, x.y, __uint_as_float(v[4 * j + 1]));
-          x.z = epi.value(row, col0 + 4 * j + 2, x.z, __uint_as_float(v[4 * j + 2]));
-          x.w = epi.value(row, col0 + 4 * j + 3, x.w, __uint_as_float(v[4 * j + 3]));
-          *p = x;
+          for (int j = 0; j < 8; ++j) {
+            float4* p = reinterpret_cast<float4*>(cb + lane * 128 + ((j ^ (lane & 7)) << 4));
+            float4 x = *p;
+            x.x -= __uint_as_float(v[4 * j + 0]);
+            x.y -= __uint_as_float(v[4 * j + 1]);
+            x.z -= __uint_as_float(v[4 * j + 2]);
+            x.w -= __uint_as_float(v[4 * j + 3]);
+            *p = x;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float4* p = reinterpret_cast<float4*>(cb + lane * 128 + ((j ^ (lane & 7)) << 4));
+            float4 x = *p;
+            x.x = epi.value(row, col0 + 4 * j + 0, x.x, __uint_as_float(v[4 * j + 0]));
+            x.y = epi.value(row, col0 + 4 * j + 1, x.y, __uint_as_float(v[4 * j + 1]));
+            x.z = epi.value(row, col0 + 4 * j + 2, x.z, __uint_as_float(v[4 * j + 2]));
+            x.w = epi.value(row, col0 + 4 * j + 3, x.w, __uint_as_float(v[4 * j + 3]));
+            *p = x;
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
