@@ -67,7 +67,8 @@ def measured_peaks():
     bf = m["bf16_tflops"]
     bfs = m.get("bf16_tflops_sustained", bf)
     return {"hbm_gbs": m["hbm_gbs"], "bf16": bf, "bf16_sustained": bfs, "fp8": 2.0 * bf,
-            "fp8_sustained": 2.0 * bfs, "tf32": bf * 1.1 / 2.25, "source": src}
+            "fp8_sustained": 2.0 * bfs, "tf32": bf * 1.1 / 2.25, "tf32_sustained": bfs * 1.1 / 2.25,
+            "source": src}
 
 
 WORKLOADS = {
@@ -564,8 +565,13 @@ def mixed_report(n, per, info, fp64_rho):
 
 
 def mixed_rooflines(n, trace, info, nsteps, mode):
-    """Rooflines of the two mixed-path kernels that bound it: the FP8 residual
-    GEMM (tensor) and the TF32/BF16 Schur update (HBM), from the trace pass."""
+    """Rooflines of the two mixed-path kernels that bound it, from the trace
+    pass: the FP8 residual GEMM (tensor) and the TF32/BF16 Schur update. The
+    update moves 8 bytes of X per element and does 3 x 2b flops on it (three
+    split products): 192 flop/B at b = 256, above the TF32 ridge (the sustained
+    TF32 peak / HBM, 125 flop/B) and below the BF16 one (250), so its bound is
+    the TF32 tensor pipe in TF32 mode and HBM in BF16 mode; both fractions are
+    given."""
     peaks = measured_peaks()
     g = dict(trace.get("residual_group_gemm_e4m3", {"ms": 0, "flops": 0, "launches": 0}))
     if g["ms"]:
@@ -596,14 +602,28 @@ def mixed_rooflines(n, trace, info, nsteps, mode):
         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, mean of the fresh and the "
                         "incremental residual (profiles/mixed_solve_16384.md)",
         "share_of_kernel_time": g["ms"] / kt_total if kt_total else None}
-    hbm = {"bound": "hbm", "kernel": f"schur_update_{mode}_tc (gemm_kernel<{mode.upper()}, EpiSchurF32>)",
-           "achieved": ags, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-           "frac": ags / peaks["hbm_gbs"] if ags else None,
-           "algorithmic_bytes_per_launch": schur["bytes"] / schur["launches"] if schur["launches"] else None,
-           "traffic": ncu_traffic(f"schur_update_{mode}_tc", n),
-           "traffic_note": "one launch of the rest of a step (after the next block's square)",
-           "share_of_kernel_time": schur["ms"] / kt_total if kt_total else None}
-    return tensor, hbm, kt_total
+    agf = schur["flops"] / (schur["ms"] / 1e3) / 1e12 if schur["ms"] else None
+    tpeak = peaks["tf32_sustained"] if mode == "tf32" else peaks["bf16_sustained"]
+    hbm_frac = ags / peaks["hbm_gbs"] if ags else None
+    tensor_frac = agf / tpeak if agf else None
+    common = {"kernel": f"schur_update_{mode}_tc (gemm_kernel<{mode.upper()}, EpiSchurF32>)",
+              "algorithmic_bytes_per_launch": schur["bytes"] / schur["launches"] if schur["launches"] else None,
+              "algorithmic_flops_per_launch": schur["flops"] / schur["launches"] if schur["launches"] else None,
+              "hbm_achieved_gbs": ags, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_frac,
+              "tensor_achieved_tflops": agf, "tensor_peak_tflops": tpeak, "tensor_frac": tensor_frac,
+              "tensor_peak_source": f"sustained dense {mode.upper()}: " + (
+                  "the sustained BF16 figure x 1.1 / 2.25 (nominal TF32 / BF16 ratio)" if mode == "tf32"
+                  else "the sustained BF16 figure") + f" ({peaks['source']})",
+              "traffic": ncu_traffic(f"schur_update_{mode}_tc", n),
+              "traffic_note": "one launch of the rest of a step (after the next block's square)",
+              "share_of_kernel_time": schur["ms"] / kt_total if kt_total else None}
+    if mode == "tf32":
+        schur_rl = dict({"bound": "tensor", "achieved": agf, "peak": tpeak, "unit": "TFLOP/s",
+                         "frac": tensor_frac}, **common)
+    else:
+        schur_rl = dict({"bound": "hbm", "achieved": ags, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": hbm_frac}, **common)
+    return tensor, schur_rl, kt_total
 
 
 def run_cfg1(args, bi, torch):
@@ -1125,9 +1145,10 @@ def run_ours(args):
             if is_head:
                 nt = 3
                 trace = trace_pass(bi, torch, step, nt)
-                tensor, hbm, kt_total = mixed_rooflines(n, trace, infos[-1], nt, mode)
+                tensor, schur_rl, kt_total = mixed_rooflines(n, trace, infos[-1], nt, mode)
                 launches = sum(v["launches"] for v in trace.values()) / nt
-                head = dict(rep, trace=trace, tensor=tensor, hbm=hbm, kt_total=kt_total, launches=launches, nt=nt)
+                head = dict(rep, trace=trace, tensor=tensor, schur_rl=schur_rl, kt_total=kt_total, launches=launches,
+                            nt=nt)
             if orc:
                 host_X[(seed, mode)] = dX.cpu().numpy()
             legs[f"{mode}_sigma{sig}"] = rep
@@ -1229,7 +1250,7 @@ def run_ours(args):
             "refine_iters": h["refine_iters"],
             "eps_vs_oracle": h.get("eps_vs_oracle"), "eps_max_vs_oracle": h.get("eps_max_vs_oracle"),
             "speedup_vs_fp64_path": h.get("speedup_vs_fp64_path"),
-            "roofline": head["tensor"], "roofline_schur_update": head["hbm"],
+            "roofline": head["tensor"], "roofline_schur_update": head["schur_rl"],
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": int(round(head["launches"] * args.steps)),
             "kernels": head["trace"],

@@ -444,6 +444,13 @@ const char* blockinv_status_str(int status);
  * host thread (-1 if none); also returns that status. */
 int blockinv_last_error_detail(int64_t* failing_block);
 
+/* The cudaError_t value of the most recent CUDA runtime failure that a
+ * library call (on any thread, serving workers included) reported as
+ * BLOCKINV_ERR_CUDA or BLOCKINV_ERR_NOMEM, or 0 if there was none since the
+ * library was loaded or this function was last called (it clears the value).
+ * *name, if name is not NULL, gets the error's name (static string). */
+int blockinv_last_cuda_error(const char** name);
+
 /* ABI version: major * 10000 + minor * 100 + patch. */
 int blockinv_version(void);
 

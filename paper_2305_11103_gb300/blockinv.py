@@ -69,6 +69,7 @@ SIGNATURES = {
                                      _vp]),
     "blockinv_status_str": (ctypes.c_char_p, [_int]),
     "blockinv_last_error_detail": (_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "blockinv_last_cuda_error": (_int, [ctypes.POINTER(ctypes.c_char_p)]),
     "blockinv_version": (_int, []),
     "blockinv_struct_sizes": (_int, [_i32p, _i32p, _i32p]),
     "blockinv_release_memory": (_int, []),
@@ -164,6 +165,14 @@ def blockinv_invert_ex(n, block_sizes, A_ptr, lda, mode=F64, stream=None, tol=0.
     st = lib().blockinv_invert_ex(n, p, arr, A_ptr, lda, _mode(mode), _stream_ptr(stream), ctypes.byref(opt),
                                   ctypes.byref(info))
     return st, info
+
+
+def blockinv_last_cuda_error():
+    """(code, name) of the last CUDA runtime failure the library reported as
+    ERR_CUDA / ERR_NOMEM (0, "cudaSuccess" if none); clears it."""
+    name = ctypes.c_char_p()
+    code = lib().blockinv_last_cuda_error(ctypes.byref(name))
+    return code, (name.value.decode() if name.value else "")
 
 
 def blockinv_diag_gemm(kind, M, N, K, A_ptr, lda, B_ptr, ldb, C_ptr, ldc, stream=None):

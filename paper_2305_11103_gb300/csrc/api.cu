@@ -3,6 +3,7 @@
 // per-step kernel sequence of the blockwise inversion (Eq. (a) applied once
 // per diagonal block, in place).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -190,13 +191,16 @@ cudaError_t workspace_pool(cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
-namespace {
+std::atomic<int> g_last_cuda_error{0};
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return BLOCKINV_OK;
+  g_last_cuda_error.store(static_cast<int>(e), std::memory_order_relaxed);
   if (e == cudaErrorMemoryAllocation) return BLOCKINV_ERR_NOMEM;
   return BLOCKINV_ERR_CUDA;
 }
+
+namespace {
 
 // Side stream per device for the look-ahead (highest priority, created once).
 cudaStream_t side_stream() {
@@ -934,6 +938,12 @@ const char* blockinv_status_str(int status) {
 int blockinv_last_error_detail(int64_t* failing_block) {
   if (failing_block) *failing_block = g_last_block;
   return g_last_status;
+}
+
+int blockinv_last_cuda_error(const char** name) {
+  const int e = blockinv::g_last_cuda_error.exchange(0, std::memory_order_relaxed);
+  if (name) *name = e ? cudaGetErrorName(static_cast<cudaError_t>(e)) : "cudaSuccess";
+  return e;
 }
 
 int blockinv_version(void) { return 100; }

@@ -258,13 +258,15 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
     if (staging_bytes) *staging_bytes = need;
     if (!staging || cap < need) return BLOCKINV_ERR_NOMEM;
   }
-  if (cudaGetDevice(&tmp.device) != cudaSuccess) return BLOCKINV_ERR_CUDA;
+  const cudaError_t ed = cudaGetDevice(&tmp.device);
+  if (ed != cudaSuccess) return cuda_status(ed);
   void* dev = nullptr;
   if (pool_stream) {
     // stream-ordered, from the library's pool (no device-wide synchronisation)
     cudaMemPool_t pool = nullptr;
-    if (workspace_pool(&pool) != cudaSuccess) return BLOCKINV_ERR_CUDA;
-    if (cudaMallocFromPoolAsync(&dev, total, pool, pool_stream) != cudaSuccess) return BLOCKINV_ERR_NOMEM;
+    cudaError_t ep = workspace_pool(&pool);
+    if (ep == cudaSuccess) ep = cudaMallocFromPoolAsync(&dev, total, pool, pool_stream);
+    if (ep != cudaSuccess) return cuda_status(ep);
     tmp.pool_stream = pool_stream;
   } else if (cudaMalloc(&dev, total) != cudaSuccess) {
     return BLOCKINV_ERR_NOMEM;
@@ -293,7 +295,7 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
       e = cudaMemcpyAsync(base + o_starts, static_cast<char*>(staging) + tb, sb, cudaMemcpyHostToDevice, pool_stream);
     if (e != cudaSuccess) {
       cudaFreeAsync(dev, pool_stream);
-      return BLOCKINV_ERR_CUDA;
+      return cuda_status(e);
     }
   } else {
     e = cudaMemcpy(base + o_items, items.data(), sizeof(GroupStep) * items.size(), cudaMemcpyHostToDevice);
@@ -301,7 +303,7 @@ int batch_plan_create(int32_t count, const int32_t* n, const int32_t* p, const i
       e = cudaMemcpy(base + o_starts, starts.data(), sizeof(int32_t) * starts.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       cudaFree(dev);
-      return BLOCKINV_ERR_CUDA;
+      return cuda_status(e);
     }
   }
   *out = new BatchPlan(std::move(tmp));
@@ -416,7 +418,7 @@ struct TuneBatch {
     for (size_t m = 0; m < n.size(); ++m) hA[m] = reinterpret_cast<double*>(base + off[m]);
     cudaError_t e = cudaMemcpy(base + o_ptr, hA.data(), sizeof(double*) * n.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + o_n, n.data(), sizeof(int32_t) * n.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     dA = reinterpret_cast<double* const*>(base + o_ptr);
     dn = reinterpret_cast<const int32_t*>(base + o_n);
     return BLOCKINV_OK;
@@ -470,7 +472,7 @@ int time_table(TuneBatch& tb, const Tuned* table, int reps, cudaStream_t s, floa
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   batch_plan_destroy(pl);
-  return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  return cuda_status(e);
 }
 
 }  // namespace
@@ -560,7 +562,7 @@ int blockinv_batch_plan_run(blockinv_batch_plan* plan, void* stream, int32_t* st
     TraceScope t("batched_grouped_f64", pl->flops, pl->bytes, s);
     e = batch_run(*pl, s, status_dev, true);
   }
-  return e == cudaSuccess ? BLOCKINV_OK : (e == cudaErrorMemoryAllocation ? BLOCKINV_ERR_NOMEM : BLOCKINV_ERR_CUDA);
+  return cuda_status(e);
 }
 
 int blockinv_batch_plan_destroy(blockinv_batch_plan* plan) {
@@ -582,7 +584,7 @@ int blockinv_invert_batched(int32_t count, const int32_t* n, const int32_t* p, c
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   batch_plan_destroy(pl);
-  return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  return cuda_status(e);
 }
 
 int blockinv_batch_tune(int32_t count, const int32_t* n, int32_t reps, void* stream) {

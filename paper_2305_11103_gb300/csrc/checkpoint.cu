@@ -56,7 +56,7 @@ int blockinv_checkpoint_write(const char* path, int64_t n, int32_t p, const int3
   const size_t row = sizeof(double) * (size_t)n;
   cudaError_t e = copy_matrix(host.data(), n, A, lda, n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_status(e);
   const int32_t np = (int32_t)pl.sizes.size();
   const uint64_t h = fnv1a(host.data(), row * (size_t)n);
   File out(path, "wb");
@@ -97,7 +97,7 @@ int blockinv_checkpoint_read(const char* path, int64_t n, int32_t p, const int32
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = copy_matrix(A, lda, host.data(), n, n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_status(e);
   *k_done = fk;
   return BLOCKINV_OK;
 }

@@ -45,7 +45,7 @@ extern "C" int blockinv_diag_recip64(const double* v, double* out, int64_t count
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 8 * 152);
   recip64_kernel<<<(int)blocks, 256, 0, s>>>(v, out, count);
   const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  return cuda_status(e);
 }
 
 extern "C" int blockinv_diag_wait_timeout(int64_t limit_ns, void* stream) {
@@ -53,7 +53,7 @@ extern "C" int blockinv_diag_wait_timeout(int64_t limit_ns, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int32_t* status = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&status), 2 * sizeof(int32_t), s);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? BLOCKINV_ERR_NOMEM : BLOCKINV_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_status(e);
   int32_t host[2] = {0, 0};
   e = cudaMemsetAsync(status, 0, 2 * sizeof(int32_t), s);
   if (e == cudaSuccess) {
@@ -63,6 +63,6 @@ extern "C" int blockinv_diag_wait_timeout(int64_t limit_ns, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(status, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return BLOCKINV_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_status(e);
   return host[0];
 }

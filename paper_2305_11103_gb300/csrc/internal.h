@@ -166,6 +166,11 @@ struct ServeJob;
 // The library's device memory pool for workspace on the current device.
 cudaError_t workspace_pool(cudaMemPool_t* out);
 
+// Status of a CUDA runtime result: OK, NOMEM for an allocation failure, else
+// ERR_CUDA. A failure is also kept as the library's last CUDA error (any
+// thread), which blockinv_last_cuda_error reports.
+int cuda_status(cudaError_t e);
+
 // The paper's partition rule (Table 2) for any order (blocks of order 2..4).
 void paper_partition(int n, std::vector<int>* out);
 

@@ -34,6 +34,7 @@
 
 #include "fp64_ops.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -509,27 +510,40 @@ pivot_warp_grouped_kernel(const GroupStep* __restrict__ items, int count) {
 // microsecond). The 256-block (b^3 = 16.8 M DFMA) therefore spreads its rows
 // over a cluster of up to 16 CTAs (at most kLaRows rows each, in shared
 // memory), and the per-column critical path is built from few FP64
-// instructions, every one of them with all its lanes busy:
+// instructions, every one of them with all its lanes busy, and from shared
+// memory of the CTA itself:
 //
-//   1. warp 0 applies step c to column c + 1 (lane = local row, one FMA),
-//      takes each lane's reciprocal, and picks the local candidate of column
-//      c + 1 (largest magnitude among rows not yet used as pivots, lowest
-//      row on ties) on the integer pipe from the value's bit pattern;
-//   2. every thread applies step c to the candidate row's element of its
-//      column (one FMA) and stores it into this CTA's slot in every CTA of
-//      the cluster (distributed shared memory); thread 0 adds the key
-//      (|value| bits, row) and the candidate's reciprocal;
-//   3. barrier.cluster.arrive, step c on every other local row (the bulk of
-//      the FP64 work, b x rows FMAs), then barrier.cluster.wait: the
-//      exchange of the next pivot row overlaps the bulk of the update;
-//   4. every CTA reduces the keys in its own slots (integer compares) to the
-//      same pivot row and finds that row, unscaled, in the winner's slot.
+//   1. every CTA waits on its own mbarrier until the records of column c of
+//      all C CTAs have arrived in its slots (record = the CTA's candidate
+//      key: |value| bits, row, reciprocal; and the candidate row);
+//   2. warp 0 reduces the C keys (integer compares) to the pivot row, which
+//      every CTA finds, unscaled, in the winner's slot; applies step c to
+//      column c + 1 (lane = local row, one FMA), takes each lane's
+//      reciprocal, and picks the local candidate of column c + 1 (largest
+//      magnitude among rows not yet used as pivots, lowest row on ties) on
+//      the integer pipe from the value's bit pattern;
+//   3. every thread applies step c to the candidate row's element of its
+//      column (one FMA); one warp packs the record of column c + 1 and sends
+//      it to every CTA of the cluster as one bulk copy each (cp.async.bulk,
+//      shared::cta to shared::cluster), completing on the receiver's
+//      mbarrier;
+//   4. step c on every other local row (the bulk of the FP64 work, b x rows
+//      FMAs), started by the other warps at once, while the copies are in
+//      flight.
 //
-// Slots alternate by column parity: a slot is rewritten only after every CTA
-// has passed the barrier that follows its last use. Each element gets
-// x - f * (P[p][j] r) with r the pivot's reciprocal (3 FMAs from the hardware
-// estimate, within an ulp; exact for powers of two), the same arithmetic as
-// the row-split kernel except for that reciprocal.
+// A record travels by DMA, so no thread waits for a remote store and no
+// cluster barrier runs per column (a phase probe of the earlier form, with
+// a cluster barrier and remote row loads, spent 3700 of 5970 clocks per
+// column outside the bulk at b = 256). Slots, outgoing records and mbarriers
+// alternate by column parity. A CTA sends the records of column c + 2 only
+// after all records of column c + 1 have reached it, and each CTA sends
+// those after it has finished reading its slots of column c: so a slot is
+// rewritten only after its last reader is done with it.
+//
+// Each element gets x - f * (P[p][j] r) with r the pivot's reciprocal
+// (3 FMAs from the hardware estimate, within an ulp; exact for powers of
+// two), the same arithmetic as the row-split kernel except for that
+// reciprocal.
 constexpr int kLaRows = 16;             // local rows per CTA
 constexpr int kLaMaxB = kPivotThreads;  // one column per thread
 
@@ -538,49 +552,65 @@ struct LaKey {
   int row;                   // global row (INT_MAX with no candidate)
   int pad;
   double inv;                // reciprocal of the candidate
+  double pad2;               // the record header is 32 bytes
 };
+static_assert(sizeof(LaKey) == 32, "record header");
+
+// Bytes of one record (key, then the candidate row of b doubles), a multiple
+// of 16 for the bulk copy.
+__host__ __device__ __forceinline__ int la_rec_bytes(int b) { return (32 + 8 * b + 15) / 16 * 16; }
 
 struct LaSmem {
-  double* rows;   // [kLaRows][b]: this CTA's rows
-  double* slot;   // [2][C][b]: candidate rows by column parity and CTA
-  LaKey* key;     // [2][C]
-  LaKey* cand;    // [1]: this CTA's candidate of the next column
-  double* fbuf;   // [kLaRows]: multipliers of the current step (column c before it)
-  double* win;    // [3]: the current pivot's reciprocal, then (as int32) its CTA, row, failure
-  int* perm;      // [b]: pivot row of each column
-  int* misc;      // [0] candidate local row (-1 none), [1] flags of this CTA
+  double* rows;            // [kLaRows][b]: this CTA's rows
+  unsigned char* slot;     // [2][C] records by column parity and sending CTA
+  unsigned char* out;      // [2] records this CTA sends, by column parity
+  uint64_t* bar;           // [2] mbarriers: all C records of a column have arrived
+  double* fbuf;            // [kLaRows]: multipliers of the current step (column c before it)
+  double* win;             // [3]: the current pivot's reciprocal, then (as int32) its CTA, row, failure
+  int* perm;               // [b]: pivot row of each column
+  int* misc;               // [0] candidate local row (-1 none), [1] flags of this CTA, [2] wait failed
+  int rec;                 // record bytes
+  __device__ LaKey* key(int par, int q) const {
+    return reinterpret_cast<LaKey*>(slot + ((size_t)par * 16 + q) * rec);
+  }
+  __device__ double* row_of(int par, int q) const {
+    return reinterpret_cast<double*>(slot + ((size_t)par * 16 + q) * rec + 32);
+  }
 };
 
-__device__ __forceinline__ LaSmem la_layout(unsigned char* raw, int b, int C) {
+__device__ __forceinline__ LaSmem la_layout(unsigned char* raw, int b) {
   LaSmem m;
+  m.rec = la_rec_bytes(b);
   m.rows = reinterpret_cast<double*>(raw);
-  m.slot = m.rows + (size_t)kLaRows * b;
-  m.key = reinterpret_cast<LaKey*>(m.slot + 2 * (size_t)C * b);
-  m.cand = m.key + 2 * C;
-  m.fbuf = reinterpret_cast<double*>(m.cand + 1);
+  m.slot = reinterpret_cast<unsigned char*>(m.rows + (size_t)kLaRows * b);  // 16-byte aligned: 128 b bytes of rows
+  m.out = m.slot + (size_t)2 * 16 * m.rec;
+  m.bar = reinterpret_cast<uint64_t*>(m.out + (size_t)2 * m.rec);
+  m.fbuf = reinterpret_cast<double*>(m.bar + 2);
   m.win = m.fbuf + kLaRows;
   m.perm = reinterpret_cast<int*>(m.win + 3);
   m.misc = m.perm + b;
   return m;
 }
 
-size_t la_smem_bytes(int b, int C) {
-  return sizeof(double) * ((size_t)kLaRows * b + 2 * (size_t)C * b + kLaRows + 3) + sizeof(LaKey) * (2 * C + 1) +
-         sizeof(int) * ((size_t)b + 4) + 16;
+size_t la_smem_bytes(int b) {
+  return sizeof(double) * (size_t)kLaRows * b + (size_t)(2 * 16 + 2) * la_rec_bytes(b) + 2 * sizeof(uint64_t) +
+         sizeof(double) * (kLaRows + 3) + sizeof(int) * ((size_t)b + 4) + 16;
+}
+
+// Send this CTA's outgoing record of parity `par` into slot [par][rank] of
+// CTA q, completing on q's mbarrier of that parity.
+__device__ __forceinline__ void la_send(const LaSmem& m, int par, int rank, int q) {
+  const uint32_t src = tc::smem_u32(m.out + (size_t)par * m.rec);
+  const uint32_t dst = tc::mapa_u32(tc::smem_u32(m.slot + ((size_t)par * 16 + rank) * m.rec), (uint32_t)q);
+  const uint32_t bar = tc::mapa_u32(tc::smem_u32(&m.bar[par]), (uint32_t)q);
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst),
+               "r"(src), "r"(m.rec), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ bool key_better(const LaKey& a, const LaKey& b) {
   return a.vbits > b.vbits || (a.vbits == b.vbits && a.row < b.row);
-}
-
-// Split cluster barrier (every thread of every CTA; the warp reconverges first).
-__device__ __forceinline__ void cluster_arrive() {
-  __syncwarp();
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  __syncwarp();
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // The reciprocal without the range check of recip64 (the caller checks the
@@ -593,9 +623,10 @@ __device__ __forceinline__ double recip_core(double v) {
 }
 
 // Local candidate of column cn from warp 0 (lane = local row): key and
-// reciprocal into m.cand, local row into m.misc[0]. x = the lane's updated
-// value, valid = the lane holds a row not yet used as a pivot.
-__device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, bool valid, int r0) {
+// reciprocal, and the candidate's value x, into this CTA's outgoing record
+// of column cn; local row into m.misc[0]. x = the lane's updated value,
+// valid = the lane holds a row not yet used as a pivot.
+__device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, bool valid, int r0, int cn) {
   const unsigned long long ab =
       valid ? (static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
   const unsigned hi = static_cast<unsigned>(ab >> 32), lo = static_cast<unsigned>(ab);
@@ -603,13 +634,16 @@ __device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, boo
   const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
   const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
   const unsigned win = __reduce_min_sync(0xffffffffu, (valid && hi == mhi && lo == mlo) ? (unsigned)lane : 64u);
+  unsigned char* o = m.out + (size_t)(cn & 1) * m.rec;
+  LaKey* key = reinterpret_cast<LaKey*>(o);
   if (lane == 0 && win == 64u) {
     LaKey k;
     k.vbits = 0ull;
     k.row = INT_MAX;
     k.pad = 0;
     k.inv = 0.0;
-    *m.cand = k;
+    k.pad2 = 0.0;
+    *key = k;
     m.misc[0] = -1;
   }
   if ((unsigned)lane == win) {
@@ -619,7 +653,9 @@ __device__ __forceinline__ void la_pick(const LaSmem& m, int lane, double x, boo
     k.pad = 0;
     const int ef = exp_field(x);
     k.inv = (ef >= 1 && ef <= 2044) ? rr : 1.0 / x;  // outside the normal range: the division
-    *m.cand = k;
+    k.pad2 = 0.0;
+    *key = k;
+    reinterpret_cast<double*>(o + 32)[cn] = x;  // the candidate row's element of column cn
     m.misc[0] = lane;
   }
 }
@@ -637,7 +673,7 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  LaSmem m = la_layout(smem_raw, b, C);
+  LaSmem m = la_layout(smem_raw, b);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int R = (b + C - 1) / C;  // rows per CTA (<= RT)
   const int r0 = rank * R;
@@ -651,11 +687,17 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
       if (nonfinite_bits(v)) bad = 1;
       m.rows[(size_t)r * b + tid] = v;
     }
-  if (tid == 0) m.misc[1] = (*(volatile const int32_t*)&status[0] != 0) ? 2 : 0;
+  if (tid == 0) {
+    m.misc[1] = (*(volatile const int32_t*)&status[0] != 0) ? 2 : 0;
+    m.misc[2] = 0;
+    tc::mbar_init(&m.bar[0], 1);
+    tc::mbar_init(&m.bar[1], 1);
+    tc::fence_mbar_init();
+  }
   __syncthreads();
   if (bad) atomicOr(&m.misc[1], 1);
-  // every CTA of the cluster is running (peers' shared memory may be
-  // written from here on) and every CTA's flags are set
+  // every CTA of the cluster is running, its mbarriers are initialised (peers
+  // may send from here on) and its flags are set
   cl.sync();
   int flags = 0;
   for (int q = 0; q < C; ++q) flags |= *cl.map_shared_rank(&m.misc[1], q);
@@ -668,55 +710,62 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
   }
 
   uint32_t used = 0;  // local rows already used as pivots (the same in every thread)
-  // this CTA's candidate of column cn (already up to date in m.rows) to every CTA
-  auto push = [&](int cn, int rs) {
-    const int par = cn & 1;
-    if (col && rs >= 0) {
-      const double v = m.rows[(size_t)rs * b + tid];
-      for (int q = 0; q < C; ++q) cl.map_shared_rank(m.slot, q)[((size_t)par * C + rank) * b + tid] = v;
-    }
-    if (tid < C) cl.map_shared_rank(m.key, tid)[par * C + rank] = *m.cand;
+  // this CTA's record of column cn to every CTA, one bulk copy each from the
+  // last warp (the other warps go on with the bulk of the step). The record
+  // (key, candidate row) is complete: every thread has written its part and
+  // ordered it for the async proxy before the CTA barrier that precedes this.
+  constexpr int kSendWarp = kPivotThreads / 32 - 1;
+  auto send = [&](int cn) {
+    if (warp == kSendWarp && lane < C) la_send(m, cn & 1, rank, lane);
   };
 
   // column 0: candidates from the input itself
+  if (tid == 0) tc::mbar_arrive_expect_tx(&m.bar[0], (uint32_t)(C * m.rec));
   if (warp == 0) {
     const double x = lane < nloc ? m.rows[(size_t)lane * b] : 0.0;
-    la_pick(m, lane, x, lane < nloc, r0);
+    la_pick(m, lane, x, lane < nloc, r0, 0);
   }
   __syncthreads();
-  push(0, m.misc[0]);
-  cl.sync();
+  {
+    const int rs = m.misc[0];
+    if (col && tid != 0 && rs >= 0) reinterpret_cast<double*>(m.out + 32)[tid] = m.rows[(size_t)rs * b + tid];
+  }
+  tc::fence_proxy_async_smem();
+  __syncthreads();
+  send(0);
   int failed = 0;
   int* wi = reinterpret_cast<int*>(m.win + 1);  // [0] CTA of the pivot row, [1] its row, [2] failure (win[1..2])
   for (int c = 0; c < b; ++c) {
     const int par = c & 1;
     const int cn = c + 1;
     const bool ahead = cn < b;
+    // the records of column c from every CTA (bounded wait; the same outcome
+    // in every thread of the CTA)
+    const bool arrived = tc::mbar_wait_for(&m.bar[par], (uint32_t)((c >> 1) & 1), tc::kWaitLimitNs);
+    if (__syncthreads_or(!arrived)) {
+      failed = BLOCKINV_ERR_TIMEOUT;
+      break;
+    }
+    if (tid == 0 && ahead) tc::mbar_arrive_expect_tx(&m.bar[cn & 1], (uint32_t)(C * m.rec));
     if (warp == 0) {
-      // the pivot of column c: the best key in this CTA's slots, lane q holding
-      // CTA q's key, reduced by shuffles (integer compares; all lanes agree)
-      // (row, CTA) packed as row * 16 + CTA: rows < 2^20, so the packed
-      // value orders like the row and one shuffle carries both
+      // the pivot of column c: the best key in this CTA's slots (lane q holds
+      // CTA q's), by three warp reductions on the integer pipe: the largest
+      // |value| bits (high word, then low word), then among those the lowest
+      // row, with (row, CTA) packed as row * 16 + CTA (rows < 2^20)
       unsigned long long kv = 0ull;
       unsigned kp = 0xFFFFFFFFu;
       double kinv = 0.0;
       if (lane < C) {
-        const LaKey k = m.key[par * C + lane];
+        const LaKey k = *m.key(par, lane);
         kv = k.vbits;
         kp = k.row == INT_MAX ? 0xFFFFFFFFu : (static_cast<unsigned>(k.row) << 4) | static_cast<unsigned>(lane);
         kinv = k.inv;
       }
-#pragma unroll
-      for (int off = 8; off > 0; off >>= 1) {  // C <= 16: lanes 0..15 reduce, lane 0 broadcasts
-        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, kv, off);
-        const unsigned op = __shfl_xor_sync(0xffffffffu, kp, off);
-        if (ov > kv || (ov == kv && op < kp)) {
-          kv = ov;
-          kp = op;
-        }
-      }
-      kv = __shfl_sync(0xffffffffu, kv, 0);
-      kp = __shfl_sync(0xffffffffu, kp, 0);
+      const unsigned vhi = static_cast<unsigned>(kv >> 32), vlo = static_cast<unsigned>(kv);
+      const unsigned mhi = __reduce_max_sync(0xffffffffu, vhi);
+      const unsigned mlo = __reduce_max_sync(0xffffffffu, vhi == mhi ? vlo : 0u);
+      kp = __reduce_min_sync(0xffffffffu, (vhi == mhi && vlo == mlo) ? kp : 0xFFFFFFFFu);
+      kv = (static_cast<unsigned long long>(mhi) << 32) | mlo;
       const int kr = kp == 0xFFFFFFFFu ? INT_MAX : static_cast<int>(kp >> 4);
       const int ks = static_cast<int>(kp & 15u);
       const double inv = __shfl_sync(0xffffffffu, kinv, ks);
@@ -736,7 +785,7 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
         const int pl = kr - r0;
         const bool mine = pl >= 0 && pl < nloc;
         if (mine) used |= 1u << pl;
-        const double* prow = m.slot + ((size_t)par * C + ks) * b;
+        const double* prow = m.row_of(par, ks);
         // multipliers: column c of the local rows before step c
         const double fl = lane < nloc ? m.rows[(size_t)lane * b + c] : 0.0;
         if (lane < nloc) m.fbuf[lane] = fl;
@@ -751,19 +800,19 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
             *e = x;
             valid = !((used >> lane) & 1u);
           }
-          la_pick(m, lane, x, valid, r0);
+          la_pick(m, lane, x, valid, r0, cn);
         }
       }
     }
     __syncthreads();  // the pivot, column cn, the candidate and the multipliers are in shared memory
     failed = wi[2];
-    if (failed) break;  // the same in every CTA (the same keys)
+    if (failed) break;  // the same in every CTA (the same keys); no copies in flight
     const int who = wi[0], p = wi[1];
     const double inv = m.win[0];
     const int pl = p - r0;
     const bool mine = pl >= 0 && pl < nloc;
     if (warp != 0 && mine) used |= 1u << pl;
-    const double* prow = m.slot + ((size_t)par * C + who) * b;
+    const double* prow = m.row_of(par, who);
     const int rs = ahead ? m.misc[0] : -1;
     // step c on element (r, tid): the pivot row is scaled, column c takes
     // -f inv, every other element x - f (P[p][tid] inv)
@@ -771,11 +820,13 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
     if (ahead) {
       if (col && tid != cn && rs >= 0) {
         double* e = m.rows + (size_t)rs * b + tid;
-        *e = fma(-m.fbuf[rs], sj, tid == c ? 0.0 : *e);  // rs is never the pivot row
+        const double v = fma(-m.fbuf[rs], sj, tid == c ? 0.0 : *e);  // rs is never the pivot row
+        *e = v;
+        reinterpret_cast<double*>(m.out + (size_t)(cn & 1) * m.rec + 32)[tid] = v;
       }
-      __syncthreads();  // the candidate row is complete
-      push(cn, rs);
-      cluster_arrive();  // the bulk below hides the exchange and the other CTAs' skew
+      tc::fence_proxy_async_smem();
+      __syncthreads();  // the record of column cn is complete
+      send(cn);         // the copies fly while the bulk below runs
     }
     if (col && tid != cn) {
       // every element of the column first (one load each, all in flight), then
@@ -792,13 +843,13 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
         if (r < nloc && r != rs)
           m.rows[(size_t)r * b + tid] = (mine && r == pl) ? sj : fma(-f[r], sj, zc ? 0.0 : x[r]);
     }
-    if (ahead) cluster_wait();
     __syncthreads();  // the bulk of step c is in shared memory before column c + 2 is read
   }
-  // no CTA writes another CTA's shared memory after this barrier
+  // every CTA is done with every slot and no copy is in flight (a timed-out
+  // CTA may leave copies in flight only after a failure)
   cl.sync();
-  if (failed) {
-    if (rank == 0 && tid == 0) set_status(status, failed, block_index);
+  if (failed) {  // the same code in every CTA, or a timeout in some (the first report wins)
+    if (tid == 0) set_status(status, failed, block_index);
     return;
   }
   // unscramble: inverse[c][p_j] = a[p_c][j] for the step c at which row p_c was pivot
@@ -1354,7 +1405,7 @@ int la_ctas(int b) {
 template <int RT>
 cudaError_t launch_pivot_la_rt(const double* P, int64_t ldp, int b, int C, double* Pinv, int64_t ldo,
                                int32_t* status, int block_index, cudaStream_t s) {
-  const size_t smem = la_smem_bytes(b, C);
+  const size_t smem = la_smem_bytes(b);
   cudaError_t e = set_smem_once<pivot_la_f64_kernel<RT>>(smem);
   if (e != cudaSuccess) return e;
   if (C > 8) {  // clusters above the portable 8 CTAs, allowed once per device

@@ -80,7 +80,7 @@ int diag(int M, int N, int Kdim, const void* A, int64_t lda, const void* B, int6
   EpiStoreF32 epi{C, ldc, M, N};
   cudaError_t e = tc::launch_gemm<K, EpiStoreF32, false, kPair>(ta, tb, M, N, km, epi, nullptr, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  return cuda_status(e);
 }
 
 }  // namespace

@@ -93,7 +93,7 @@ extern "C" int blockinv_invert_noalloc(int64_t n, int32_t p, const int32_t* bloc
   int32_t host[2] = {0, -1};
   if (e == cudaSuccess) e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? BLOCKINV_ERR_NOMEM : BLOCKINV_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_status(e);
   if (host[0] != BLOCKINV_OK && failing_block) *failing_block = host[1];
   return host[0];
 }

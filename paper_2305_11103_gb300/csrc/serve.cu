@@ -147,7 +147,7 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
     ld = n;
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(sl.status_dev, 0, 2 * sizeof(int32_t), s);
-  int st = (e == cudaSuccess) ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  int st = cuda_status(e);
   if (st == BLOCKINV_OK)
     st = serve_enqueue(r->plan, X, ld, r->mode, sl.status_dev, s, c->tol, -1, &sl.job);
   sl.X = X;
@@ -157,7 +157,7 @@ void launch_request(blockinv_ctx* c, Slot& sl) {
     e = copy_matrix(r->A, r->lda, sl.dbuf, n, n, cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(sl.status_host, sl.status_dev, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaEventRecord(sl.ev1, s);
-  sl.enqueue_status = (st == BLOCKINV_OK && e != cudaSuccess) ? BLOCKINV_ERR_CUDA : st;
+  sl.enqueue_status = st == BLOCKINV_OK ? cuda_status(e) : st;
 }
 
 // A mixed request whose refinement failed is rerun in FP64 on its slot, from
@@ -253,7 +253,7 @@ void launch_batch(Slot& sl) {
     pp[i] = (int32_t)part.size();
     sizes.insert(sizes.end(), part.begin(), part.end());
   }
-  int st = e == cudaSuccess ? BLOCKINV_OK : BLOCKINV_ERR_CUDA;
+  int st = cuda_status(e);
   sl.plan = nullptr;
   if (st == BLOCKINV_OK) {
     size_t cap = sl.staging_cap;
@@ -269,7 +269,7 @@ void launch_batch(Slot& sl) {
                              s, sl.staging, &cap);
     }
   }
-  if (st == BLOCKINV_OK && batch_run(*sl.plan, s, sl.bstatus_dev, false) != cudaSuccess) st = BLOCKINV_ERR_CUDA;
+  if (st == BLOCKINV_OK) st = cuda_status(batch_run(*sl.plan, s, sl.bstatus_dev, false));
   if (st == BLOCKINV_OK)
     cudaMemcpyAsync(sl.bstatus_host, sl.bstatus_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s);
   for (int i = 0; i < count && st == BLOCKINV_OK; ++i) {

@@ -132,9 +132,11 @@ def test_small_requests_batched_and_completion_queue(bi):
         time.sleep(0.001)
     assert sorted(seen) == sorted(tickets)
     assert ctx.poll_done() == []
-    for A, d, t in zip(mats, ds, tickets):
-        st, r = ctx.poll(t)
-        assert st == bi.OK and r.mode == bi.F64 and r.rho == -1.0
+    res = [ctx.poll(t) for t in tickets]
+    bad = [(A.shape[0], st) for A, (st, r) in zip(mats, res) if st != bi.OK]
+    assert not bad, (bad, bi.blockinv_last_cuda_error())
+    for A, d, (st, r) in zip(mats, ds, res):
+        assert r.mode == bi.F64 and r.rho == -1.0
         X = d.cpu().numpy()
         assert rho(A, X) <= 1e-12
         n = A.shape[0]
