@@ -843,7 +843,8 @@ pivot_la_f64_kernel(const double* __restrict__ P, int64_t ldp, int b, double* __
         if (r < nloc && r != rs)
           m.rows[(size_t)r * b + tid] = (mine && r == pl) ? sj : fma(-f[r], sj, zc ? 0.0 : x[r]);
     }
-    __syncthreads();  // the bulk of step c is in shared memory before column c + 2 is read
+    // the CTA barrier after the next wait orders the bulk of step c before
+    // warp 0 reads column c + 2
   }
   // every CTA is done with every slot and no copy is in flight (a timed-out
   // CTA may leave copies in flight only after a failure)
