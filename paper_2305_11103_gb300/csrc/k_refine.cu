@@ -449,21 +449,41 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int j = j0 + tx;
   float s2 = 0.f;  // ||E||^2 needs a few digits only: FP32 keeps the FP64 pipe for E itself
-  for (int ii = ty; ii < 32; ii += 8) {
+  // all loads of this thread's four elements first (Eout may be Ebase, so a
+  // store would otherwise hold back the next element's loads)
+  constexpr int kR = 4;
+  long long tv[kR];
+  double aii[kR], aij[kR], xij[kR], bv[kR];
+  int exv[kR];
+  const bool jin = j < n;
+  const double xjj = jin ? X[(int64_t)j * ldx + j] : 0.0;
+  const int cj = jin ? cexp[j] : 0;
+#pragma unroll
+  for (int q = 0; q < kR; ++q) {
+    const int i = i0 + ty + 8 * q;
+    const bool in = i < n && jin;
+    tv[q] = in ? T[(int64_t)i * ldt + j] : 0;
+    aii[q] = in ? A[(int64_t)i * lda + i] : 0.0;
+    aij[q] = in ? A[(int64_t)i * lda + j] : 0.0;
+    xij[q] = in ? X[(int64_t)i * ldx + j] : 0.0;
+    bv[q] = (in && Ebase) ? Ebase[(int64_t)i * ldb + j] : 0.0;
+    exv[q] = in ? rexp[i] : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < kR; ++q) {
+    const int ii = ty + 8 * q;
     const int i = i0 + ii;
     double e = 0.0;
-    if (i < n && j < n) {
-      const int ex = rexp[i] + cexp[j] + 2 * kHeadroom - kLog2Digit * (S + 1);
-      const long long t = T[(int64_t)i * ldt + j];
-      const double r = scaled_i64(t, ex);
-      const double dx = A[(int64_t)i * lda + i] * X[(int64_t)i * ldx + j];   // (D_A X)_ij
+    if (i < n && jin) {
+      const int ex = exv[q] + cj + 2 * kHeadroom - kLog2Digit * (S + 1);
+      const double r = scaled_i64(tv[q], ex);
+      const double dx = aii[q] * xij[q];  // (D_A X)_ij
       if (Ebase) {
-        const double base = Ebase[(int64_t)i * ldb + j];
-        e = (i == j) ? (base - dx) - r : (base - fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx)) - r;
+        e = (i == j) ? (bv[q] - dx) - r : (bv[q] - fma(aij[q], xjj, dx)) - r;
       } else if (i == j) {
         e = (1.0 - dx) - r;
       } else {
-        e = -fma(A[(int64_t)i * lda + j], X[(int64_t)j * ldx + j], dx) - r;   // (O_A D_X)_ij
+        e = -fma(aij[q], xjj, dx) - r;  // (O_A D_X)_ij
       }
       const float ef = f32_trunc(e);
       s2 = fmaf(ef, ef, s2);
