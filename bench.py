@@ -107,14 +107,14 @@ NCU_TRAFFIC = {
     ("schur_update_f64", 8192): {"bytes_per_launch": 532.9e6 / 2 * (7936 * 8192) / (5888 * 6144),
                                  "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
     ("schur_update_f64", 6144): {"bytes_per_launch": 532.9e6 / 2, "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
-    # 16384 mixed TF32 solve: the fresh residual (440.28 + 32.20 GB) and the
-    # incremental one (246.41 + 17.17 GB), averaged over the two launches
-    ("residual_group_gemm_e4m3", 16384): {"bytes_per_launch": (440.28e9 + 32.20e9 + 246.41e9 + 17.17e9) / 2,
+    # 16384 mixed TF32 solve: the fresh residual (772.83 + 32.21 GB) and the
+    # incremental one (236.46 + 17.17 GB), averaged over the two launches
+    ("residual_group_gemm_e4m3", 16384): {"bytes_per_launch": (772.83e9 + 32.21e9 + 236.46e9 + 17.17e9) / 2,
                                           "src": (("k_refine.cu", "tc_gemm.cuh", "tc_common.cuh"),
-                                                  "01f72e84b08dfa82")},
+                                                  "e4ac66a494595a59")},
     # the rest of one step's TF32 update (the launch after the next block's square)
     ("schur_update_tf32_tc", 16384): {"bytes_per_launch": 1.33e9 + 0.999e9,
-                                      "src": (("k_mixed.cu", "tc_gemm.cuh", "tc_common.cuh"), "3ff8d95acd470c2c")},
+                                      "src": (("k_mixed.cu", "tc_gemm.cuh", "tc_common.cuh"), "dd4ffd6395993da7")},
 }
 
 

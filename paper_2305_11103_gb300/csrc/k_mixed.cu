@@ -45,24 +45,64 @@ struct OpType<true> {
 
 // ------------------------------------------------------------- casts ------
 // Row by row (a CTA per row at a time), so no element index is divided.
+// kVec: A's rows start 16-byte aligned (aligned A, even lda), so four
+// elements move per 2 x 16-byte load and one 16-byte store (X32 rows are
+// multiples of 32 floats); otherwise one element at a time.
+template <bool kVec>
 __global__ void cast_f64_to_f32_kernel(const double* __restrict__ A, int64_t lda, float* __restrict__ X,
                                        int64_t ldx, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const double* a = A + (int64_t)i * lda;
     float* x = X + (int64_t)i * ldx;
+    if constexpr (kVec) {
+#pragma unroll 2
+      for (int j = 4 * threadIdx.x; j < ldx; j += 4 * blockDim.x) {
+        float4 v;
+        if (j + 3 < n) {
+          const double2 p = *reinterpret_cast<const double2*>(a + j);
+          const double2 q = *reinterpret_cast<const double2*>(a + j + 2);
+          v = make_float4((float)p.x, (float)p.y, (float)q.x, (float)q.y);
+        } else {
+          v = make_float4(j < n ? (float)a[j] : 0.f, j + 1 < n ? (float)a[j + 1] : 0.f,
+                          j + 2 < n ? (float)a[j + 2] : 0.f, 0.f);
+        }
+        *reinterpret_cast<float4*>(x + j) = v;
+      }
+    } else {
 #pragma unroll 4
-    for (int j = threadIdx.x; j < ldx; j += blockDim.x) x[j] = (j < n) ? (float)a[j] : 0.f;
+      for (int j = threadIdx.x; j < ldx; j += blockDim.x) x[j] = (j < n) ? (float)a[j] : 0.f;
+    }
   }
 }
 
+template <bool kVec>
 __global__ void cast_f32_to_f64_kernel(const float* __restrict__ X, int64_t ldx, double* __restrict__ A,
                                        int64_t lda, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const float* x = X + (int64_t)i * ldx;
     double* a = A + (int64_t)i * lda;
+    if constexpr (kVec) {
+#pragma unroll 2
+      for (int j = 4 * threadIdx.x; j < n; j += 4 * blockDim.x) {
+        const float4 v = *reinterpret_cast<const float4*>(x + j);
+        if (j + 3 < n) {
+          *reinterpret_cast<double2*>(a + j) = make_double2((double)v.x, (double)v.y);
+          *reinterpret_cast<double2*>(a + j + 2) = make_double2((double)v.z, (double)v.w);
+        } else {
+          a[j] = (double)v.x;
+          if (j + 1 < n) a[j + 1] = (double)v.y;
+          if (j + 2 < n) a[j + 2] = (double)v.z;
+        }
+      }
+    } else {
 #pragma unroll 4
-    for (int j = threadIdx.x; j < n; j += blockDim.x) a[j] = (double)x[j];
+      for (int j = threadIdx.x; j < n; j += blockDim.x) a[j] = (double)x[j];
+    }
   }
+}
+
+bool rows_16b_aligned(const void* p, int64_t ld, int elem) {
+  return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && (ld * elem) % 16 == 0;
 }
 
 // --------------------------------------------------------- row panel ------
@@ -422,12 +462,18 @@ cudaError_t launch_schur_tc(const CUtensorMap& tU, const CUtensorMap& tV, const 
 }  // namespace
 
 cudaError_t launch_cast_f64_to_f32(const double* A, int64_t lda, float* X, int64_t ldx, int n, cudaStream_t s) {
-  cast_f64_to_f32_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(A, lda, X, ldx, n);
+  if (rows_16b_aligned(A, lda, 8) && rows_16b_aligned(X, ldx, 4))
+    cast_f64_to_f32_kernel<true><<<8 * tc::num_sms(), 256, 0, s>>>(A, lda, X, ldx, n);
+  else
+    cast_f64_to_f32_kernel<false><<<4 * tc::num_sms(), 256, 0, s>>>(A, lda, X, ldx, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_f32_to_f64(const float* X, int64_t ldx, double* A, int64_t lda, int n, cudaStream_t s) {
-  cast_f32_to_f64_kernel<<<4 * tc::num_sms(), 256, 0, s>>>(X, ldx, A, lda, n);
+  if (rows_16b_aligned(A, lda, 8) && rows_16b_aligned(X, ldx, 4))
+    cast_f32_to_f64_kernel<true><<<8 * tc::num_sms(), 256, 0, s>>>(X, ldx, A, lda, n);
+  else
+    cast_f32_to_f64_kernel<false><<<4 * tc::num_sms(), 256, 0, s>>>(X, ldx, A, lda, n);
   return cudaGetLastError();
 }
 
