@@ -374,10 +374,14 @@ __global__ void incr_groups_kernel(const int32_t* __restrict__ cx, const int32_t
   }
 }
 
+// x rounded to TF32 (10 explicit mantissa bits), nearest with ties away from
+// zero, on the integer pipe: half a unit added at bit 12 of the magnitude and
+// the 13 bits below cleared (a carry into the exponent is the round-up).
+// Inf and NaN are returned as they are.
 __device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7F800000u) == 0x7F800000u) return x;
+  return __uint_as_float((u + 0x1000u) & ~0x1FFFu);
 }
 
 // 2^e for -1022 <= e <= 1023 from its bit pattern (exact); 0 below.
@@ -392,6 +396,11 @@ __device__ __forceinline__ double pow2(int e) {
 // the 11 bits below decide the rounding. The same value as the FP64
 // conversion times 2^ex; that product is the fallback where the result
 // would leave the normal range.
+// The out-of-range case of scaled_i64, kept out of line so that the compiler
+// does not evaluate it (an int64 conversion and a multiply on the FP64 pipe)
+// for every element.
+__device__ __noinline__ double scaled_i64_slow(long long t, int ex) { return static_cast<double>(t) * pow2(ex); }
+
 __device__ __forceinline__ double scaled_i64(long long t, int ex) {
   if (t == 0) return 0.0;
   const unsigned long long sign = t < 0 ? (1ull << 63) : 0ull;
@@ -409,7 +418,7 @@ __device__ __forceinline__ double scaled_i64(long long t, int ex) {
     }
   }
   const int be = e + 1023;
-  if (be <= 0 || be >= 2047) return static_cast<double>(t) * pow2(ex);
+  if (be <= 0 || be >= 2047) return scaled_i64_slow(t, ex);
   return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(be) << 52) |
                                                      (m & 0xFFFFFFFFFFFFFull)));
 }
@@ -434,13 +443,16 @@ __device__ __forceinline__ float f32_trunc(double v) {
 // (S = the digit groups summed in T: 2^(-2F) 32^(2S' - 1 - S) with F = 5S' - 1);
 // ||E||^2; E^T split into TF32 hi/lo (rows j of Eop, columns i and Kp + i);
 // optionally E itself in FP64.
+// kBase: Ebase is given (the incremental residual); a template argument so
+// that the compiler does not evaluate both forms for every element.
+template <bool kBase>
 __global__ void __launch_bounds__(256)
 finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const double* __restrict__ A,
                 int64_t lda, const double* __restrict__ X, int64_t ldx, const int32_t* __restrict__ rexp,
                 const int32_t* __restrict__ cexp, int S, double* __restrict__ e2sum, float* __restrict__ Eop,
                 int Kp, double* Eout, int64_t lde, const double* Ebase, int64_t ldb, const Ctl* ctl,
                 const int32_t* status, int path) {
-  // Ebase null: E = I - A X. Otherwise (incremental residual, X = the change
+  // Without kBase: E = I - A X. With it (incremental residual, X = the change
   // of the iterate): E = Ebase - A X; Ebase and Eout may be the same matrix.
   if (halted(ctl, status, path)) return;
   __shared__ double tile[32][33];
@@ -466,9 +478,13 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
     aii[q] = in ? A[(int64_t)i * lda + i] : 0.0;
     aij[q] = in ? A[(int64_t)i * lda + j] : 0.0;
     xij[q] = in ? X[(int64_t)i * ldx + j] : 0.0;
-    bv[q] = (in && Ebase) ? Ebase[(int64_t)i * ldb + j] : 0.0;
+    bv[q] = (kBase && in) ? Ebase[(int64_t)i * ldb + j] : 0.0;
     exv[q] = in ? rexp[i] : 0;
   }
+  // Tiles off the diagonal (all but one in 32 of them) take the
+  // off-diagonal formula alone: a select between the two would have the
+  // FP64 pipe evaluate both for every element.
+  const bool diag_tile = i0 == j0;
 #pragma unroll
   for (int q = 0; q < kR; ++q) {
     const int ii = ty + 8 * q;
@@ -478,12 +494,15 @@ finalize_kernel(const long long* __restrict__ T, int64_t ldt, int n, const doubl
       const int ex = exv[q] + cj + 2 * kHeadroom - kLog2Digit * (S + 1);
       const double r = scaled_i64(tv[q], ex);
       const double dx = aii[q] * xij[q];  // (D_A X)_ij
-      if (Ebase) {
+      if (!diag_tile) {
+        if constexpr (kBase) e = (bv[q] - fma(aij[q], xjj, dx)) - r;
+        else e = -fma(aij[q], xjj, dx) - r;  // (O_A D_X)_ij
+      } else if (kBase) {
         e = (i == j) ? (bv[q] - dx) - r : (bv[q] - fma(aij[q], xjj, dx)) - r;
       } else if (i == j) {
         e = (1.0 - dx) - r;
       } else {
-        e = -fma(aij[q], xjj, dx) - r;  // (O_A D_X)_ij
+        e = -fma(aij[q], xjj, dx) - r;
       }
       const float ef = f32_trunc(e);
       s2 = fmaf(ef, ef, s2);
@@ -767,7 +786,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       if (e == cudaSuccess) e = group_gemms(S, incr ? kFresh : kAny, false);
       if (e != cudaSuccess) break;
       TraceScope t("residual_finalize", 0, 8.0 * nd * nd + (max_updates > 0 ? 16.0 * nd * nd : 0.0), s);
-      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
+      finalize_kernel<false><<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, X, ldx, rexp, cx, S, &sums[1 + 2 * it],
                                          it < max_updates ? Eop : nullptr, Kp,
                                          (max_updates == 0) ? Eout : (it < max_updates ? Ebuf : nullptr),
                                          (max_updates == 0) ? lde : ldt, nullptr, 0, ctl, status,
@@ -788,7 +807,7 @@ cudaError_t enqueue_refine(const double* A0, int64_t ld0, double* X, int64_t ldx
       if (e == cudaSuccess) e = group_gemms(S, fresh ? kIncr : kAny, true);
       if (e != cudaSuccess) break;
       TraceScope t("residual_finalize", 0, 24.0 * nd * nd, s);
-      finalize_kernel<<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, Dbuf, ldt, rexp, cx, S, &sums[1 + 2 * it],
+      finalize_kernel<true><<<fg, 256, 0, s>>>(T, ldt, n, A0, ld0, Dbuf, ldt, rexp, cx, S, &sums[1 + 2 * it],
                                          it < max_updates ? Eop : nullptr, Kp, Ebuf, ldt, Ebuf, ldt, ctl, status,
                                          fresh ? kIncr : kAny);
     }
