@@ -94,6 +94,8 @@ WORKLOADS = {
 CPU_SAMPLE_N = 4096
 SERVE_SLOTS = 32
 SERVE_INFLIGHT = 512  # requests submitted and not finished, at most (device memory of their inputs)
+SERVE_DRAIN_S = 240.0  # after a serving window, how long unfinished requests are waited for
+stuck_contexts = []  # serving contexts with requests that never completed (not closed)
 
 # DRAM traffic per launch of a kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel source
@@ -116,6 +118,14 @@ NCU_TRAFFIC = {
     ("schur_update_tf32_tc", 16384): {"bytes_per_launch": 1.33e9 + 0.999e9,
                                       "src": (("k_mixed.cu", "tc_gemm.cuh", "tc_common.cuh"), "dd4ffd6395993da7")},
 }
+
+
+_T0 = time.time()
+
+
+def progress(msg):
+    """One line per leg on stderr (the JSON result goes to stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def parse():
@@ -394,11 +404,16 @@ class OracleRuns:
         self.proc.start()
         self.done = False
 
-    def get(self, key):
+    def get(self, key, limit_s=1800.0):
         """Block until the oracle's X for `key` is ready: (seconds, threads,
-        X as a read-only memory map) or None if the worker failed."""
+        X as a read-only memory map) or None if the worker failed or did not
+        deliver within limit_s."""
         import queue
+        t_end = time.time() + limit_s
         while key not in self.results and not self.done:
+            if time.time() > t_end:
+                self.error = self.error or f"no result for {key} within {limit_s:.0f} s"
+                break
             try:
                 item = self.q.get(timeout=5)
             except queue.Empty:
@@ -431,6 +446,8 @@ class OracleRuns:
             self.drop(k)
         if self.proc.is_alive():
             self.proc.join(timeout=1)
+        if self.proc.is_alive():
+            self.proc.terminate()
         try:
             os.rmdir(self.dir)
         except OSError:
@@ -969,8 +986,16 @@ def run_serving(args, bi, torch):
         lat, fin, statuses, used_modes = [], [], [], []
         kept = {}
         done = i = 0
+        progress(f"serving {mode}: {nreq} requests over {window} s")
         t0 = time.perf_counter()
+        # a request that never completes must not stall the benchmark: after
+        # the window and a generous drain, the rest is reported as incomplete
+        deadline = window + SERVE_DRAIN_S
+        incomplete = 0
         while done < nreq:
+            if time.perf_counter() - t0 > deadline:
+                incomplete = nreq - done
+                break
             now = time.perf_counter() - t0
             new = []
             with torch.cuda.stream(cs):
@@ -1008,7 +1033,11 @@ def run_serving(args, bi, torch):
                     time.sleep(0.0002)
         wall = time.perf_counter() - t0
         gpu_util = util.stop()
-        ctx.close()
+        if incomplete:
+            progress(f"serving {mode}: {incomplete} requests incomplete at the deadline; context left open")
+            stuck_contexts.append(ctx)  # closing it would wait for them
+        else:
+            ctx.close()
         flops = sum(2.0 * float(grid[k]) ** 3 for k in idx)
         # latency over the window: the requests arriving in its first and last thirds
         order = np.argsort(fin)
@@ -1025,7 +1054,7 @@ def run_serving(args, bi, torch):
             e = eps_vs_oracle(b.cpu().numpy(), oracle_x[keys[r]])
             eps.append(e["eps_vs_oracle"])
             epsm.append(e["eps_max_vs_oracle"])
-        out[mode] = {"window_s": window, "requests": nreq, "completed": done, "wall_s": wall,
+        out[mode] = {"window_s": window, "requests": nreq, "completed": done, "incomplete": incomplete, "wall_s": wall,
                      "throughput_req_s": done / wall, "offered_req_s": rate, "effective_tflops": flops / wall / 1e12,
                      "latency_ms": percentiles(lat),
                      "latency_p99_first_third_ms": float(np.percentile(early, 99)),
@@ -1114,6 +1143,7 @@ def run_ours(args):
     flops = 2.0 * n ** 3
     # serving first: its host loop must not share the cores with the oracle
     serving = {} if args.no_serve else run_serving(args, bi, torch)
+    progress("mixed legs")
     jobs = [(f"x{n}_s{seed}", n, w["block"], sig, seed) for seed, sig in w["legs"]]
     side = not args.no_side and n != 8192
     if side:
@@ -1190,12 +1220,15 @@ def run_ours(args):
 
     side_legs = {}
     if side:
+        progress("side legs: FP64 8192 and 256")
         f64_steps, f64_warm = min(args.steps, 5), min(args.warmup, 2)
         res, _, X8 = f64_leg(args, bi, torch, stream, WORKLOADS["f64_8192"], world, f64_steps, f64_warm, orc,
                              "x8192_s2")
         side_legs["f64_8192"] = (res, X8)
         side_legs["f64_256"] = (run_cfg1(args, bi, torch), None)
+    progress("batched legs")
     batched = {} if args.no_batched else run_batched(args, bi, torch, stream)
+    progress("waiting for the oracle")
 
     # eps against the oracle for every large result, as its inverses arrive
     cpu = None
@@ -1369,6 +1402,10 @@ def main():
         run_reference(args)
     else:
         run_ours(args)
+    if stuck_contexts:  # their worker threads may never finish: leave without waiting for them
+        sys.stdout.flush()
+        sys.stderr.flush()
+        os._exit(0)
 
 
 if __name__ == "__main__":

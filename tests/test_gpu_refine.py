@@ -119,6 +119,26 @@ def test_poorly_conditioned_sigma_105(bi):
     assert rho_np(A, X) <= 1e-12
 
 
+def test_ill_conditioned_spd_converges_without_fallback(bi):
+    """B B^T + 0.1 I (kappa ~ 4e4 at n = 1024): the update maps E to E^2, so
+    from ||E||_F < 1 it converges, over several updates, without the FP64 rerun."""
+    n = 1024
+    A = inputs.spd_covariance(n, 1924)
+    st, info, X = refine(bi, A, [256] * 4, "tf32", fallback=0)
+    assert st == bi.OK and info.used_fallback == 0 and info.refine_iters >= 2
+    assert rho_np(A, X) <= 1e-12
+
+
+def test_stall_at_the_rounding_floor_stops(bi):
+    """A target below the rounding floor: the residual stops falling, and the
+    refinement ends with NOT_CONVERGED before the iteration cap."""
+    n = 512
+    A = inputs.gaussian_shifted(n, 19, sigma=1.5)
+    st, info, _ = refine(bi, A, [128] * 4, "tf32", tol=1e-30, max_refine=8, fallback=0)
+    assert st == bi.ERR_NOT_CONVERGED and info.used_fallback == 0
+    assert 1 <= info.refine_iters < 8
+
+
 def test_not_converged_then_fallback(bi):
     n = 512
     A = inputs.gaussian_shifted(n, 9, sigma=1.5)

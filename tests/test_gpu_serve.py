@@ -160,8 +160,8 @@ def test_mixed_mode_requests(bi):
 
 
 def test_mixed_fallback_for_ill_conditioned(bi):
-    """B B^T + 0.1 I at n = 1500 (kappa ~ 1e5): BF16 refinement does not
-    contract, so the request is rerun in FP64 and still meets the gate."""
+    """B B^T + 0.1 I at n = 1500 (kappa ~ 1e5) in BF16: the refinement either
+    brings it down or the request is rerun in FP64; either way it meets the gate."""
     n = 1500
     A = inputs.spd_covariance(n, 760)
     ctx = bi.Context(0, 8 << 30, 2)
