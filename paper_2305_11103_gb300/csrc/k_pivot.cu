@@ -130,14 +130,15 @@ __device__ __forceinline__ void pivot_gj_body(const TIO* __restrict__ P, int64_t
     }
   }
   if (bad) atomicOr(&flags[0], 1);
-  // Skip everything if an earlier kernel of this inversion already failed.
-  const int prior = *(volatile int32_t*)&status[0];
+  // Skip everything if an earlier kernel of this inversion already failed:
+  // bit 2, OR-ed over the cluster with the rest, so that every CTA leaves
+  // here or none does (each CTA reads the status word at its own time).
+  if (tid == 0 && *(volatile int32_t*)&status[0] != 0) atomicOr(&flags[0], 2);
   cluster_or_block_sync<kCluster>();
   int anybad = 0;
   for (int q = 0; q < nranks; ++q) anybad |= *peer<kCluster>(&flags[0], q);
-  if (anybad || prior != 0) {
-    if (anybad && prior == 0 && rank == 0 && tid == 0)
-      set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
+  if (anybad) {
+    if (anybad == 1 && rank == 0 && tid == 0) set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
     cluster_or_block_sync<kCluster>();
     return;
   }
@@ -337,10 +338,13 @@ pivot_gj_grouped_kernel(const GroupStep* __restrict__ items, int count, int bmin
     rows[e] = v;
   }
   if (bad) atomicOr(flag, 1);
-  const int prior = *(volatile const int32_t*)it.status;  // an earlier kernel of this inversion failed
+  // an earlier kernel of this inversion failed: bit 2, read once for the
+  // whole CTA, so that all threads leave here or none does
+  if (tid == 0 && *(volatile const int32_t*)it.status != 0) atomicOr(flag, 2);
   __syncthreads();
-  if (flag[0] || prior != 0) {
-    if (flag[0] && prior == 0 && tid == 0) set_status(it.status, BLOCKINV_ERR_NONFINITE, it.k);
+  const int any = flag[0];
+  if (any) {
+    if (any == 1 && tid == 0) set_status(it.status, BLOCKINV_ERR_NONFINITE, it.k);
     return;
   }
   // flat walk e = tid + 256 i over the block, (r, j) stepped without division
@@ -945,12 +949,15 @@ pivot_blocked_kernel(const T* __restrict__ P, int64_t ldp, int b, int ncl, T* __
   if (tid < 4) m.flags[tid] = 0;
   __syncthreads();
   if (bad) atomicOr(&m.flags[0], 1);
-  const int prior = *(volatile int32_t*)&status[0];
+  // an earlier kernel failed: bit 2, OR-ed over the cluster with the rest, so
+  // that every CTA leaves here or none does (each CTA reads the status word
+  // at its own time)
+  if (tid == 0 && *(volatile int32_t*)&status[0] != 0) atomicOr(&m.flags[0], 2);
   cluster_or_block_sync<kCluster>();
   int anybad = 0;
   for (int q = 0; q < nranks; ++q) anybad |= *peer<kCluster>(&m.flags[0], q);
-  if (anybad || prior != 0) {
-    if (anybad && prior == 0 && rank == 0 && tid == 0) set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
+  if (anybad) {
+    if (anybad == 1 && rank == 0 && tid == 0) set_status(status, BLOCKINV_ERR_NONFINITE, block_index);
     cluster_or_block_sync<kCluster>();
     return;
   }

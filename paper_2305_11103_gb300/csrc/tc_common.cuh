@@ -168,6 +168,14 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
       : "memory");
 }
 
+// 32-bit load from the shared memory of a CTA of this cluster (an address
+// from mapa_u32).
+__device__ __forceinline__ uint32_t ld_shared_cluster_u32(uint32_t caddr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(caddr) : "memory");
+  return v;
+}
+
 // Every thread of both CTAs: all earlier shared-memory accesses of the
 // cluster (remote arrivals, copies) are done before any thread goes on.
 __device__ __forceinline__ void cluster_sync_all() {

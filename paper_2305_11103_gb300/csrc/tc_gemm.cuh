@@ -119,6 +119,7 @@ struct GemmShared {
   uint64_t tempty[2];
   uint64_t cbar[2 * kEpiWarps];  // kTmaC epilogues: per warp, the TMA loads of its two C-block slots
   uint32_t tmem_base;
+  uint32_t skip;  // pair: rank 0's reading of epi.skip(), taken by both CTAs
 };
 
 // Epilogue staging: each epilogue warp turns its 32 x 32 accumulator block
@@ -225,10 +226,15 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   // An earlier kernel of this computation failed: the status word it wrote is
   // the same for every CTA. A programmatic dependent runs to the end instead:
   // its predecessor may still be writing that word, and the dependent's
-  // griddepcontrol.wait at the end is what keeps the stream order.
-  if (!dep_wait && epi.skip()) return;
+  // griddepcontrol.wait at the end is what keeps the stream order. The two
+  // CTAs of a pair both take rank 0's reading (below): a timeout elsewhere in
+  // this launch may set the word between their reads, and a CTA that left
+  // alone would keep the other waiting at the cluster barrier.
+  const bool skip_me = !dep_wait && epi.skip();
+  if (!kPair && skip_me) return;
 
   if (threadIdx.x == 0) {
+    sh->skip = skip_me ? 1u : 0u;
     for (int s = 0; s < kS; ++s) {
       mbar_init(&sh->full[s], 1);
       mbar_init(&sh->empty[s], 1);
@@ -255,8 +261,12 @@ gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if constexpr (kPair) cluster_sync_all();
   fence_after_sync();
   const uint32_t tmem = sh->tmem_base;
+  bool skip_all = false;
+  if constexpr (kPair) skip_all = ld_shared_cluster_u32(mapa_u32(smem_u32(&sh->skip), 0)) != 0;
 
-  if (warp == 0 && lane == 0) {
+  if (skip_all) {
+    // the pair does no work and leaves through the common end below
+  } else if (warp == 0 && lane == 0) {
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
     uint32_t it = 0;
