@@ -109,11 +109,11 @@ NCU_TRAFFIC = {
     ("schur_update_f64", 8192): {"bytes_per_launch": 532.9e6 / 2 * (7936 * 8192) / (5888 * 6144),
                                  "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
     ("schur_update_f64", 6144): {"bytes_per_launch": 532.9e6 / 2, "src": ("k_update_f64.cu", "1910ef6dd2b79f18")},
-    # 16384 mixed TF32 solve: the fresh residual (580.77 + 32.21 GB) and the
-    # incremental one (239.28 + 17.17 GB), averaged over the two launches
-    ("residual_group_gemm_e4m3", 16384): {"bytes_per_launch": (580.77e9 + 32.21e9 + 239.28e9 + 17.17e9) / 2,
+    # 16384 mixed TF32 solve: the fresh residual (444.15 + 32.20 GB) and the
+    # incremental one (187.43 + 17.16 GB), averaged over the two launches
+    ("residual_group_gemm_e4m3", 16384): {"bytes_per_launch": (444.15e9 + 32.20e9 + 187.43e9 + 17.16e9) / 2,
                                           "src": (("k_refine.cu", "tc_gemm.cuh", "tc_common.cuh"),
-                                                  "5c52461be1e4f429")},
+                                                  "2bc8f9508a2b6ac1")},
     # the rest of one step's TF32 update (the launch after the next block's square)
     ("schur_update_tf32_tc", 16384): {"bytes_per_launch": 1.33e9 + 0.999e9,
                                       "src": (("k_mixed.cu", "tc_gemm.cuh", "tc_common.cuh"), "dd4ffd6395993da7")},
