@@ -192,9 +192,16 @@ int oracle_small_inverse(int m, const double* M, long ldm, double* out, long ldo
     double c22 = E(0, 0) * E(1, 1) - E(0, 1) * E(1, 0);
     double det = E(0, 0) * c00 + E(0, 1) * c01 + E(0, 2) * c02;
     if (det == 0.0 || !isfinite(det)) return OR_SINGULAR;
+#if ORACLE_MUTANT == 6
+    /* planted mistake: the cofactor matrix used without its transpose */
+    O(0, 0) = c00 / det; O(0, 1) = c01 / det; O(0, 2) = c02 / det;
+    O(1, 0) = c10 / det; O(1, 1) = c11 / det; O(1, 2) = c12 / det;
+    O(2, 0) = c20 / det; O(2, 1) = c21 / det; O(2, 2) = c22 / det;
+#else
     O(0, 0) = c00 / det; O(0, 1) = c10 / det; O(0, 2) = c20 / det;
     O(1, 0) = c01 / det; O(1, 1) = c11 / det; O(1, 2) = c21 / det;
     O(2, 0) = c02 / det; O(2, 1) = c12 / det; O(2, 2) = c22 / det;
+#endif
     return OR_OK;
   }
 #undef E
@@ -320,12 +327,22 @@ int oracle_paper_partition(int m, int* sizes, int cap) {
   if (nk > cap) return OR_INVALID;
   for (int i = 0; i < nk; ++i) sizes[i] = 2;
   int r = m - 2 * nk;
+#if ORACLE_MUTANT == 9
+  /* planted mistake: the remainder handed out from the first block */
+  int pos = 0;
+  while (r > 0) {
+    sizes[pos] += 1;
+    r -= 1;
+    pos = (pos == nk - 1) ? 0 : pos + 1;
+  }
+#else
   int pos = nk - 1;
   while (r > 0) {                         /* hand out one unit per block from the end */
     sizes[pos] += 1;
     r -= 1;
     pos = (pos == 0) ? nk - 1 : pos - 1;
   }
+#endif
   return nk;
 }
 
@@ -353,7 +370,12 @@ double oracle_residual(int n, const double* A, long lda, const double* X, long l
       x2 += x * x;
     }
   free(R);
+#if ORACLE_MUTANT == 7
+  /* planted mistake: the square root of the numerator dropped */
+  return r2 / (sqrt(a2) * sqrt(x2));
+#else
   return sqrt(r2) / (sqrt(a2) * sqrt(x2));
+#endif
 }
 
 /* One Newton-Schulz step: Xn = X + X (I - A X). */
@@ -365,7 +387,12 @@ int oracle_ns_step(int n, const double* A, long lda, const double* X, long ldx,
   matmul(n, n, n, A, lda, X, ldx, E, n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) E[(long)i * n + j] = (i == j ? 1.0 : 0.0) - E[(long)i * n + j];
+#if ORACLE_MUTANT == 8
+  /* planted mistake: the correction multiplied on the wrong side, E X */
+  matmul(n, n, n, E, n, X, ldx, F, n);
+#else
   matmul(n, n, n, X, ldx, E, n, F, n);
+#endif
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) Xn[(long)i * ldn + j] = X[(long)i * ldx + j] + F[(long)i * n + j];
   free(E);

@@ -124,9 +124,9 @@ def block_inverse(A, sizes, mutant=0):
     return X
 
 
-def paper_partition(m):
+def paper_partition(m, mutant=0):
     buf = np.zeros(max(1, m), dtype=np.int32)
-    k = load().oracle_paper_partition(int(m), buf.ctypes.data_as(_IP), len(buf))
+    k = load(mutant).oracle_paper_partition(int(m), buf.ctypes.data_as(_IP), len(buf))
     if k < 0:
         raise OracleError(k)
     return [int(v) for v in buf[:k]]

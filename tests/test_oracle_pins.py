@@ -294,6 +294,35 @@ def _pin_suite(mutant):
             fails.append(("lapack", "swap"))
     except OracleError:
         fails.append(("lapack-raise", "swap"))
+    # closed forms of orders 2 and 3 against exact rationals
+    g = inputs.rng(5)
+    for m in (2, 3):
+        A = g.integers(-9, 10, size=(m, m)).astype(np.float64)
+        while round(np.linalg.det(A)) == 0:
+            A = g.integers(-9, 10, size=(m, m)).astype(np.float64)
+        exact = np.array([[float(v) for v in row] for row in rational_inverse(A)])
+        if not np.allclose(oracle.small_inverse(A, mutant=mutant), exact, rtol=4e-16 * 8, atol=0):
+            fails.append(("closed form", m))
+    # the paper's partition table
+    for m, sizes in read_table("paper_partition_table.txt").items():
+        if oracle.paper_partition(m, mutant=mutant) != sizes:
+            fails.append(("table 2", m))
+            break
+    # rho of the exact inverse and of twice it
+    A, _, _ = inputs.unimodular_block_lu([4, 4, 4], 7)
+    X = np.array([[float(v) for v in row] for row in rational_inverse(A)])
+    expect = np.sqrt(12) / (np.linalg.norm(A) * np.linalg.norm(2 * X))
+    if oracle.residual(A, X, mutant=mutant) != 0.0 or \
+            abs(oracle.residual(A, 2 * X, mutant=mutant) - expect) > 1e-14 * expect:
+        fails.append(("rho", "closed form"))
+    # one Newton-Schulz step squares the right residual
+    n = 24
+    A = inputs.gaussian_shifted(n, 51, sigma=1.5)
+    X0 = np.linalg.inv(A) @ (np.eye(n) + 1e-3 * inputs.rng(52).standard_normal((n, n)))
+    e0 = np.linalg.norm(np.eye(n) - A @ X0, 2)
+    e1 = np.linalg.norm(np.eye(n) - A @ oracle.ns_step(A, X0, mutant=mutant), 2)
+    if e1 > 1.01 * e0 ** 2 + 1e-14:
+        fails.append(("newton-schulz", "quadratic"))
     return fails
 
 
@@ -301,7 +330,7 @@ def test_pins_pass_on_real_oracle():
     assert _pin_suite(0) == []
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_pins_catch_planted_mistakes(mutant):
     oracle.build_oracle(mutant=mutant)
     assert _pin_suite(mutant), f"mutant {mutant} passed every pin"
