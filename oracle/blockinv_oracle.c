@@ -351,7 +351,12 @@ int oracle_paper_partition(int m, int* sizes, int cap) {
 int oracle_quarter_partition(int m, int* sizes) {
   if (m < 4) return OR_INVALID;
   int q = m / 4, r = m % 4;
+#if ORACLE_MUTANT == 10
+  /* planted mistake: the larger blocks placed first */
+  for (int i = 0; i < 4; ++i) sizes[i] = q + ((i < r) ? 1 : 0);
+#else
   for (int i = 0; i < 4; ++i) sizes[i] = q + ((i >= 4 - r) ? 1 : 0);
+#endif
   return 4;
 }
 

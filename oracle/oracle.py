@@ -132,9 +132,9 @@ def paper_partition(m, mutant=0):
     return [int(v) for v in buf[:k]]
 
 
-def quarter_partition(m):
+def quarter_partition(m, mutant=0):
     buf = np.zeros(4, dtype=np.int32)
-    k = load().oracle_quarter_partition(int(m), buf.ctypes.data_as(_IP))
+    k = load(mutant).oracle_quarter_partition(int(m), buf.ctypes.data_as(_IP))
     if k < 0:
         raise OracleError(k)
     return [int(v) for v in buf[:k]]

@@ -308,6 +308,12 @@ def _pin_suite(mutant):
         if oracle.paper_partition(m, mutant=mutant) != sizes:
             fails.append(("table 2", m))
             break
+    # four near-equal blocks, the larger ones last
+    for m in (9, 10, 11):
+        q = oracle.quarter_partition(m, mutant=mutant)
+        if sum(q) != m or q != sorted(q) or q[0] != m // 4:
+            fails.append(("quarters", m))
+            break
     # rho of the exact inverse and of twice it
     A, _, _ = inputs.unimodular_block_lu([4, 4, 4], 7)
     X = np.array([[float(v) for v in row] for row in rational_inverse(A)])
@@ -330,7 +336,7 @@ def test_pins_pass_on_real_oracle():
     assert _pin_suite(0) == []
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 def test_pins_catch_planted_mistakes(mutant):
     oracle.build_oracle(mutant=mutant)
     assert _pin_suite(mutant), f"mutant {mutant} passed every pin"
