@@ -75,6 +75,16 @@ def test_argument_errors_are_synchronous(lib, n, sizes, lda):
     assert blockinv.blockinv_last_error_detail() == (blockinv.ERR_INVALID, -1)
 
 
+def test_argument_errors_leave_no_cuda_error(lib):
+    # argument errors return before any CUDA call, so no runtime failure is
+    # recorded; reading the record clears it
+    blockinv.blockinv_last_cuda_error()
+    assert blockinv.blockinv_invert(4, [2, 1], 0x1000, 4, 0, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_invert(8, [8], 0x1000, 8, 7, None) == blockinv.ERR_INVALID
+    assert blockinv.blockinv_last_cuda_error() == (0, "cudaSuccess")
+    assert blockinv.blockinv_last_cuda_error() == (0, "cudaSuccess")
+
+
 def test_null_pointer_rejected(lib):
     assert blockinv.blockinv_invert(8, None, None, 8, 0, None) == blockinv.ERR_INVALID
 
